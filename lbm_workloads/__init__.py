@@ -1,0 +1,211 @@
+"""Seeded synthetic inputs for the double-MRT phase-change LBM.
+
+Both the FP64 oracle and the CUDA library are fed from here.  This module
+holds none of the method's arithmetic: it only draws random fields, smooths
+them, and writes down the dimensionless parameter sets of the workloads.  The
+one formula it applies is the Kozeny-Carman form of Eq. (6) to turn a
+porosity field into the *input* permeability field, as the workload recipe
+asks; the lattice code evaluates Eq. (6) again, separately, at every step.
+
+Every workload is a ``Workload``: lattice size, a parameter dict whose keys
+are the parameter names shared by ``oracle.Oracle`` and
+``paper_1503_08406_gb300.Lattice``, and float64 fields ``phi`` (porosity),
+``K`` (fully liquid permeability, lattice units), ``T0`` (initial
+temperature) and ``fl0`` (initial liquid fraction), row-major [ny][nx].
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    params: dict
+    phi: np.ndarray
+    K: np.ndarray
+    T0: np.ndarray
+    fl0: np.ndarray
+    wall_T_left: np.ndarray | None = None
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny
+
+
+def smoothed_gaussian(n: int, sigma_cells: float, seed: int, shape=None) -> np.ndarray:
+    """Unit-variance, zero-mean Gaussian noise smoothed with a periodic Gaussian kernel.
+
+    i.i.d. N(0,1) noise on an n x n (or ``shape``) grid, convolved (FFT,
+    periodic) with a Gaussian of standard deviation ``sigma_cells`` cells and
+    renormalised to zero mean and unit variance.
+    """
+    ny, nx = shape if shape is not None else (n, n)
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal((ny, nx))
+    ky = np.fft.fftfreq(ny)[:, None]
+    kx = np.fft.fftfreq(nx)[None, :]
+    kern = np.exp(-2.0 * np.pi ** 2 * sigma_cells ** 2 * (kx ** 2 + ky ** 2))
+    s = np.real(np.fft.ifft2(np.fft.fft2(g) * kern))
+    s -= s.mean()
+    sd = s.std()
+    return s / sd if sd > 0 else s
+
+
+def kozeny_carman_K(phi: np.ndarray, mean_K: float) -> np.ndarray:
+    """Input permeability K = phi^3 d^2 / (175 (1 - phi)^2), Eq. (6), with the
+    particle diameter d chosen so that mean(K) = mean_K."""
+    shape = phi ** 3 / (175.0 * (1.0 - phi) ** 2)
+    d2 = mean_K / shape.mean()
+    return shape * d2
+
+
+def heterogeneous_porosity(n: int, seed: int, sigma_cells: float = 16.0) -> np.ndarray:
+    """phi = clip(0.45 + 0.15 g, 0.3, 0.6), g unit-variance smoothed noise."""
+    g = smoothed_gaussian(n, sigma_cells, seed)
+    return np.clip(0.45 + 0.15 * g, 0.3, 0.6)
+
+
+def block_average(a: np.ndarray, b: int) -> np.ndarray:
+    ny, nx = a.shape
+    return a.reshape(ny // b, b, nx // b, b).mean(axis=(1, 3))
+
+
+def _cavity_fields(n: int, phi, K, hot_wall: bool = True):
+    T0 = np.zeros((n, n))
+    fl0 = np.zeros((n, n))
+    if hot_wall:
+        T0[:, 0] = 1.0
+        fl0[:, 0] = 1.0
+    phi = np.broadcast_to(np.asarray(phi, dtype=np.float64), (n, n)).copy()
+    K = np.broadcast_to(np.asarray(K, dtype=np.float64), (n, n)).copy()
+    return phi, K, T0, fl0
+
+
+def conduction_slab(nx: int = 256, ny: int = 4, phi: float = 0.5, St: float = 1.0,
+                    sigma: float = 1.0, alpha: float = 0.02, Da: float = 1e-2) -> Workload:
+    """Conduction melting of a semi-infinite porous slab.
+
+    256 x 4 lattice periodic in y, porosity 0.5, Ste = 1, sigma = 1, solid at
+    T = T_m = 0, wall node x = 0 held at 1 and x = nx-1 at 0, no flow.
+    alpha = 0.02 gives tau_T = 0.6 (Sec. 4.1 uses the same alpha_s).
+    """
+    csT2 = 0.2  # (4 + varpi)/10 with varpi = -2, Sec. 4 preamble
+    params = dict(bc=("dirichlet", "dirichlet", "periodic", "periodic"),
+                  T_bc=(1.0, 0.0, 0.0, 0.0), flow=0, St=St, sigma=sigma, dT=1.0,
+                  T_s=0.0, T_l=0.0, tau_T=0.5 + alpha / (sigma * csT2), H=float(nx))
+    T0 = np.zeros((ny, nx))
+    fl0 = np.zeros((ny, nx))
+    T0[:, 0] = 1.0
+    fl0[:, 0] = 1.0
+    return Workload("conduction_slab_%dx%d" % (nx, ny), nx, ny, params,
+                    np.full((ny, nx), phi), np.full((ny, nx), Da * nx * nx), T0, fl0,
+                    meta=dict(alpha=alpha))
+
+
+def convection_cavity(n: int = 256, phi: float = 0.4, Da: float = 1e-4, Ra: float = 1e5,
+                      Pr: float = 1.0, St: float = 1.0, sigma: float = 1.0) -> Workload:
+    """Convection melting in a square porous cavity.
+
+    Hot left wall T = 1, cold right wall T = 0 = T_m, adiabatic top and
+    bottom, uniform porosity, K = Da H^2 with H = n, solid at T = 0 initially.
+    """
+    params = dict(bc=("dirichlet", "dirichlet", "adiabatic", "adiabatic"),
+                  T_bc=(1.0, 0.0, 0.0, 0.0), flow=1, Ra=Ra, Pr=Pr, Ma=0.1, J=1.0,
+                  lambda_=1.0, sigma=sigma, St=St, dT=1.0, H=float(n), T_ref=0.0,
+                  T_s=0.0, T_l=0.0)
+    phi_f, K, T0, fl0 = _cavity_fields(n, phi, Da * n * n)
+    return Workload("convection_cavity_%d" % n, n, n, params, phi_f, K, T0, fl0)
+
+
+def heterogeneous_cavity(n: int = 2048, seed: int = 3, Da: float = 1e-4, Ra: float = 1e6,
+                         Pr: float = 1.0, St: float = 1.0, sigma: float = 1.0,
+                         source_n: int | None = None) -> Workload:
+    """Heterogeneous large cavity.
+
+    Porosity phi = clip(0.45 + 0.15 g, 0.3, 0.6) with g seeded unit-variance
+    noise smoothed by a 16-cell Gaussian; K from Kozeny-Carman with the
+    particle diameter giving mean(K) = Da H^2.  With ``source_n`` > n the
+    field is drawn at source_n^2 and block-averaged down to n^2 (the
+    downsampled copy used for the precision study); Ra and Da are kept.
+    """
+    if source_n is not None and source_n != n:
+        phi = block_average(heterogeneous_porosity(source_n, seed), source_n // n)
+    else:
+        phi = heterogeneous_porosity(n, seed)
+    K = kozeny_carman_K(phi, Da * n * n)
+    params = dict(bc=("dirichlet", "dirichlet", "adiabatic", "adiabatic"),
+                  T_bc=(1.0, 0.0, 0.0, 0.0), flow=1, Ra=Ra, Pr=Pr, Ma=0.1, J=1.0,
+                  lambda_=1.0, sigma=sigma, St=St, dT=1.0, H=float(n), T_ref=0.0,
+                  T_s=0.0, T_l=0.0)
+    phi_f, K_f, T0, fl0 = _cavity_fields(n, phi, K)
+    return Workload("heterogeneous_cavity_%d_seed%d" % (n, seed), n, n, params,
+                    phi_f, K_f, T0, fl0, meta=dict(seed=seed, Da=Da))
+
+
+def parity_cavity(n: int = 256, seed: int = 1, Ra: float = 1e5) -> Workload:
+    """The convection cavity with the heterogeneous porosity recipe (seed 1)."""
+    w = heterogeneous_cavity(n=n, seed=seed, Ra=Ra)
+    w.name = "parity_cavity_%d_seed%d" % (n, seed)
+    return w
+
+
+def melted_cavity(n: int = 64, seed: int = 7, Ra: float = 1e5, melted_cols: int | None = None,
+                  Da: float = 1e-3) -> Workload:
+    """Small cavity whose left part starts liquid and warm, so that flow, the
+    moving front and the flow mask are all exercised within a few hundred steps."""
+    w = heterogeneous_cavity(n=n, seed=seed, Ra=Ra, Da=Da)
+    m = melted_cols if melted_cols is not None else n // 3
+    x = np.arange(n)[None, :]
+    w.fl0[:, :m] = 1.0
+    w.T0[:, :] = np.where(x < m, 1.0 - x / (2.0 * m), 0.0)
+    w.T0[:, 0] = 1.0
+    w.name = "melted_cavity_%d_seed%d" % (n, seed)
+    return w
+
+
+def periodic_box(n: int = 32, seed: int = 11, flow: int = 1, Ra: float = 1e4,
+                 St: float = 0.5, T_s: float = 0.0, T_l: float = 0.0) -> Workload:
+    """Fully periodic box (no walls): a warm liquid blob, a solid block, random
+    porosity.  Closed, so total mass and total enthalpy are invariants."""
+    rng = np.random.default_rng(seed)
+    phi = np.clip(0.45 + 0.1 * smoothed_gaussian(n, 3.0, seed), 0.3, 0.6)
+    K = kozeny_carman_K(phi, 1e-2 * n * n)
+    yy, xx = np.mgrid[0:n, 0:n]
+    r2 = (xx - n / 3) ** 2 + (yy - n / 2) ** 2
+    T0 = np.where(r2 < (n / 5) ** 2, 0.8, -0.2) + 0.05 * rng.standard_normal((n, n))
+    fl0 = np.where(T0 > 0, 1.0, 0.0)
+    fl0[(xx > 2 * n // 3) & (yy > n // 4) & (yy < 3 * n // 4)] = 0.0
+    params = dict(bc=("periodic",) * 4, T_bc=(0.0,) * 4, flow=flow, Ra=Ra, Pr=1.0,
+                  Ma=0.1, J=1.0, lambda_=1.0, sigma=1.0, St=St, dT=1.0, H=float(n),
+                  T_ref=0.0, T_s=T_s, T_l=T_l)
+    if not flow:
+        params["tau_T"] = 0.8
+    return Workload("periodic_box_%d_seed%d" % (n, seed), n, n, params, phi, K, T0, fl0)
+
+
+def corner_solidification(n: int = 100, St: float = 4.0, T_i: float = 0.3, T_c: float = -1.0,
+                          T_s: float = -0.02, T_l: float = 0.02, alpha: float = 0.02) -> Workload:
+    """Solidification in a semi-infinite corner (Sec. 4.2 parameters).
+
+    Liquid at T_i, left and bottom walls lowered to T_c, phi = 1, sigma = 1,
+    St = 4 with dT = T_m - T_c = 1, mushy band [T_s, T_l].  The far (right,
+    top) walls are adiabatic so the far field is one-dimensional.  No flow.
+    """
+    csT2 = 0.2
+    params = dict(bc=("dirichlet", "adiabatic", "dirichlet", "adiabatic"),
+                  T_bc=(T_c, 0.0, T_c, 0.0), flow=0, St=St, sigma=1.0, dT=1.0,
+                  T_s=T_s, T_l=T_l, tau_T=0.5 + alpha / csT2, H=n / 2.0)
+    T0 = np.full((n, n), T_i)
+    fl0 = np.ones((n, n))
+    T0[0, :] = T_c
+    T0[:, 0] = T_c
+    fl0[0, :] = 0.0
+    fl0[:, 0] = 0.0
+    return Workload("corner_solidification_%d" % n, n, n, params, np.ones((n, n)),
+                    np.full((n, n), 1e3), T0, fl0, meta=dict(alpha=alpha, T_i=T_i, T_c=T_c))
