@@ -1,0 +1,166 @@
+/*
+ * liblbm: GB300 (sm_103a) implementation of one time step of the double
+ * multiple-relaxation-time lattice Boltzmann model for solid-liquid phase
+ * change with natural convection in porous media at the REV scale
+ * (Liu & He, arXiv:1503.08406).
+ *
+ * One step advances two coupled lattices and the liquid fraction:
+ *   - D2Q9 MRT flow lattice with the generalized non-Darcy body force,
+ *     Eq. (4)-(6), (13)-(29), on liquid nodes, halfway bounce-back on links
+ *     into solid or wall nodes;
+ *   - D2Q5 MRT temperature lattice with the latent-heat source, Eq. (30)-(39),
+ *     non-equilibrium extrapolation on thermal wall nodes (Sec. 4 preamble);
+ *   - the iterative enthalpy method for the liquid fraction, Eq. (40)-(42)
+ *     with the inner iteration of Sec. 3.2.
+ *
+ * Conventions (all entry points):
+ *   - fields are row-major [ny][nx] float32 arrays, x fastest;
+ *   - the caller owns every pointer it passes; the library copies from or
+ *     into it during the call (or, for device pointers, on the context's
+ *     stream) and never keeps it;
+ *   - the context owns its device state (populations, liquid fraction,
+ *     material fields, scratch), either in memory it allocated itself or in
+ *     a caller-provided workspace (see lbm_create);
+ *   - every int-returning call returns LBM_OK (0) or a negative LBM_ERR_*;
+ *     nothing aborts, throws or exits across this boundary;
+ *   - work is queued on the stream given to lbm_create; calls that return
+ *     host data synchronise that stream.
+ */
+#ifndef LBM_H
+#define LBM_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_ERR_INVALID_ARG (-1)  /* bad size, bad parameter, NULL where data is needed */
+#define LBM_ERR_CUDA (-2)         /* a CUDA call failed; the context may be unusable */
+#define LBM_ERR_NONFINITE (-3)    /* a reduction found NaN or Inf in the state */
+#define LBM_ERR_NOT_CONVERGED (-4)/* an inner enthalpy iteration hit max_inner_iters */
+#define LBM_ERR_OOM (-5)          /* allocation failed or workspace too small */
+#define LBM_ERR_NO_DEVICE (-6)    /* no usable sm_103a device */
+
+/* Boundary condition of one side. Periodic sides come in pairs (left/right,
+ * bottom/top). A non-periodic side's outer row or column is a wall node:
+ * no flow, fixed liquid fraction, halfway bounce-back for the flow lattice,
+ * non-equilibrium extrapolation for the temperature lattice (Sec. 4). */
+enum { LBM_BC_PERIODIC = 0, LBM_BC_DIRICHLET = 1, LBM_BC_ADIABATIC = 2 };
+enum { LBM_SIDE_LEFT = 0, LBM_SIDE_RIGHT = 1, LBM_SIDE_BOTTOM = 2, LBM_SIDE_TOP = 3 };
+
+/* Inputs. Dimensionless groups as in Eq. (9). A negative tau_nu, tau_T or
+ * g_beta is derived (Sec. 4.3): tau_nu = 1/2 + Ma J H sqrt(3 Pr)/sqrt(Ra),
+ * tau_T = 1/2 + lambda c_s^2 (tau_nu - 1/2)/(J sigma c_sT^2 Pr),
+ * g_beta = Ra nu_l alpha_l/(dT H^3). Zero relaxation rates take the Sec. 4
+ * values s_e = s_eps = 1.1, s_q = 1.2, zeta_e = zeta_nu = 1.5. Zero H means
+ * H = ny; zero dT, rho0, J or lambda_ mean 1. With flow = 0 (vartheta = 0,
+ * pure conduction) tau_T must be given. */
+typedef struct {
+  int32_t nx, ny;                 /* lattice nodes, >= 3 each */
+  int32_t bc[4];                  /* LBM_BC_* for left, right, bottom, top */
+  double  T_bc[4];                /* Dirichlet wall temperatures, same order */
+  int32_t flow;                   /* 1: flow lattice on (vartheta = 1); 0: conduction */
+  double  Ra, Pr, Ma, J, lambda_, sigma, St, dT, H;
+  double  T_ref;                  /* T_0 of the Boussinesq term, Eq. (5) */
+  double  T_s, T_l;               /* solidus, liquidus, Eq. (41)-(42); T_s == T_l allowed */
+  double  varpi;                  /* D2Q5 parameter, -4 < varpi < 1 (paper: -2) */
+  double  rho0;
+  double  tau_nu, tau_T, g_beta;
+  double  s_e, s_eps, s_q, zeta_e, zeta_nu;
+  double  f_act;                  /* a node carries flow when f_l >= f_act (default 1e-3) */
+  int32_t max_inner_iters;        /* cap of one inner enthalpy solve (default 1000) */
+  double  inner_tol;              /* inner iteration stop: max |f(k+1) - f(k)| (FP32 path: >= 1e-6) */
+  double  screen_tol;             /* phase-change screen margin in temperature: 0 = 1e-7 of the
+                                     temperature scale; < 0 = no screen, every tile is solved */
+} lbm_params;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Bytes of device workspace a context with these parameters needs; lets a
+ * caller (e.g. a framework's caching allocator) provide the memory itself. */
+int lbm_workspace_bytes(const lbm_params* p, size_t* bytes);
+
+/* Validate p, derive the lattice parameters and set up device state on the
+ * current CUDA device. `stream` is a cudaStream_t (NULL: the legacy default
+ * stream); all device work of the context is queued on it. `workspace` is a
+ * device pointer of at least lbm_workspace_bytes() bytes, 256-byte aligned,
+ * that the context uses for all its device state and keeps using until
+ * lbm_destroy; the caller keeps ownership and must not free it before then.
+ * Pass NULL to have the library allocate (and later free) the memory.
+ * On error *out is NULL. */
+int lbm_create(const lbm_params* p, void* stream, void* workspace, size_t workspace_bytes,
+               lbm_ctx** out);
+
+/* Release the context (and the memory the library allocated). NULL is a no-op. */
+void lbm_destroy(lbm_ctx* c);
+
+/* Derived lattice quantities: tau_nu, tau_T, nu_e, nu_l, alpha_e, g_beta,
+ * c_sT^2, latent coefficient dT/(sigma St). */
+int lbm_derived(const lbm_ctx* c, double out[8]);
+
+/* Load the material and initial fields (nx*ny floats each) and reset the
+ * populations to the rest equilibria f = f^eq(rho0, 0), Eq. (29), and
+ * g = g^eq(T0, 0), Eq. (39). phi: porosity in (0,1] (flow needs < 1);
+ * K: fully liquid permeability in lattice units, > 0, +inf = no porous drag;
+ * T0: initial temperature; fl0: initial liquid fraction in [0,1] (kept fixed
+ * on wall nodes). wall_T_left: NULL or ny floats replacing T_bc[LEFT] row by
+ * row on a Dirichlet left wall. device_ptrs != 0: the pointers are device
+ * memory (copies are queued on the context stream); 0: host memory (the call
+ * synchronises). Validation of host inputs returns LBM_ERR_INVALID_ARG. */
+int lbm_set_fields(lbm_ctx* c, const float* phi, const float* K, const float* T0,
+                   const float* fl0, const float* wall_T_left, int device_ptrs);
+
+/* Queue nsteps >= 0 time steps on the context stream. Returns launch and
+ * argument errors only; device-side conditions (an inner iteration that hit
+ * its cap) are reported by lbm_status. */
+int lbm_step(lbm_ctx* c, int64_t nsteps);
+
+/* Synchronise the stream and report deferred device-side conditions:
+ * LBM_ERR_NOT_CONVERGED if any inner enthalpy iteration hit max_inner_iters
+ * since the last call (the flag is then cleared), else LBM_OK. */
+int lbm_status(lbm_ctx* c);
+
+/* Steps taken since the last lbm_set_fields / lbm_set_state. */
+int64_t lbm_steps_done(const lbm_ctx* c);
+
+/* Macroscopic fields at the current time (each nx*ny floats, NULL to skip):
+ * velocity from Eq. (26)-(28) (zero on nodes without flow), rho from
+ * Eq. (24), T from Eq. (33) (wall nodes: the temperature the wall imposes),
+ * and f_l. device_ptrs as in lbm_set_fields; host outputs synchronise. */
+int lbm_get_macros(lbm_ctx* c, float* ux, float* uy, float* rho, float* T, float* fl,
+                   int device_ptrs);
+
+/* FP64 sums over non-wall nodes: out[0] total mass sum f_i, out[1] total
+ * enthalpy sum (T + a f_l) with a = phi dT/(sigma St) (Eq. 38), out[2] mean
+ * f_l, out[3] mean Nusselt number on the left wall (second-order one-sided
+ * gradient times H/dT). Synchronises. LBM_ERR_NONFINITE if a sum is not finite. */
+int lbm_reduce(lbm_ctx* c, double out[4]);
+
+/* Checkpoint: populations in natural layout, f[9][ny][nx] as deviations
+ * f_i - w_i rho0 from the rest equilibrium (the stored form), g[5][ny][nx],
+ * and f_l[ny][nx] (NULL to skip). lbm_set_state restores them and resets the
+ * step parity, so a state saved and restored continues bit for bit. */
+int lbm_get_state(lbm_ctx* c, float* f, float* g, float* fl, int device_ptrs);
+int lbm_set_state(lbm_ctx* c, const float* f, const float* g, const float* fl, int device_ptrs);
+
+/* Per-kernel timing with CUDA events on the context stream. enable != 0
+ * starts recording (and clears earlier records and counters); while it is on,
+ * lbm_step launches kernel by kernel (no CUDA graph) with events between the
+ * kernels. lbm_timing_read synchronises and returns, over the recorded steps,
+ * the summed milliseconds of the fused stream-collide kernel, of the enthalpy
+ * solve kernel and of the enthalpy commit kernel, the number of steps timed,
+ * the number of enthalpy tiles solved and the largest number of inner sweeps
+ * one tile needed (NULL outputs are skipped). */
+int lbm_timing(lbm_ctx* c, int enable);
+int lbm_timing_read(lbm_ctx* c, double* fused_ms, double* solve_ms, double* commit_ms,
+                    int64_t* steps_timed, int64_t* tiles_solved, int32_t* max_sweeps);
+
+/* Static text for an LBM_* code. */
+const char* lbm_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

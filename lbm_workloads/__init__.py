@@ -170,23 +170,26 @@ def melted_cavity(n: int = 64, seed: int = 7, Ra: float = 1e5, melted_cols: int 
 
 
 def periodic_box(n: int = 32, seed: int = 11, flow: int = 1, Ra: float = 1e4,
-                 St: float = 0.5, T_s: float = 0.0, T_l: float = 0.0) -> Workload:
-    """Fully periodic box (no walls): a warm liquid blob, a solid block, random
-    porosity.  Closed, so total mass and total enthalpy are invariants."""
+                 St: float = 0.5, T_s: float = 0.0, T_l: float = 0.0,
+                 ny: int | None = None) -> Workload:
+    """Fully periodic n x ny box (no walls): a warm liquid blob, a solid block,
+    random porosity.  Closed, so total mass and total enthalpy are invariants."""
+    nx = n
+    ny = n if ny is None else ny
     rng = np.random.default_rng(seed)
-    phi = np.clip(0.45 + 0.1 * smoothed_gaussian(n, 3.0, seed), 0.3, 0.6)
-    K = kozeny_carman_K(phi, 1e-2 * n * n)
-    yy, xx = np.mgrid[0:n, 0:n]
-    r2 = (xx - n / 3) ** 2 + (yy - n / 2) ** 2
-    T0 = np.where(r2 < (n / 5) ** 2, 0.8, -0.2) + 0.05 * rng.standard_normal((n, n))
+    phi = np.clip(0.45 + 0.1 * smoothed_gaussian(0, 3.0, seed, shape=(ny, nx)), 0.3, 0.6)
+    K = kozeny_carman_K(phi, 1e-2 * ny * ny)
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    r2 = (xx - nx / 3) ** 2 + (yy - ny / 2) ** 2
+    T0 = np.where(r2 < (min(nx, ny) / 5) ** 2, 0.8, -0.2) + 0.05 * rng.standard_normal((ny, nx))
     fl0 = np.where(T0 > 0, 1.0, 0.0)
-    fl0[(xx > 2 * n // 3) & (yy > n // 4) & (yy < 3 * n // 4)] = 0.0
+    fl0[(xx > 2 * nx // 3) & (yy > ny // 4) & (yy < 3 * ny // 4)] = 0.0
     params = dict(bc=("periodic",) * 4, T_bc=(0.0,) * 4, flow=flow, Ra=Ra, Pr=1.0,
-                  Ma=0.1, J=1.0, lambda_=1.0, sigma=1.0, St=St, dT=1.0, H=float(n),
+                  Ma=0.1, J=1.0, lambda_=1.0, sigma=1.0, St=St, dT=1.0, H=float(ny),
                   T_ref=0.0, T_s=T_s, T_l=T_l)
     if not flow:
         params["tau_T"] = 0.8
-    return Workload("periodic_box_%d_seed%d" % (n, seed), n, n, params, phi, K, T0, fl0)
+    return Workload("periodic_box_%dx%d_seed%d" % (nx, ny, seed), nx, ny, params, phi, K, T0, fl0)
 
 
 def corner_solidification(n: int = 100, St: float = 4.0, T_i: float = 0.3, T_c: float = -1.0,
@@ -209,3 +212,21 @@ def corner_solidification(n: int = 100, St: float = 4.0, T_i: float = 0.3, T_c: 
     fl0[:, 0] = 0.0
     return Workload("corner_solidification_%d" % n, n, n, params, np.ones((n, n)),
                     np.full((n, n), 1e3), T0, fl0, meta=dict(alpha=alpha, T_i=T_i, T_c=T_c))
+
+
+def bench_cavity(n: int = 2048, seed: int = 3, melted: float = 0.875, Ra: float = 1e6,
+                 Da: float = 1e-4) -> Workload:
+    """The heterogeneous cavity part-way through melting: the left ``melted``
+    fraction of the columns is liquid with T falling linearly from the hot
+    wall (1) to the front (0); the rest is solid at T_m = 0.  The flow lattice
+    then runs on most nodes and a full-height front exercises the enthalpy
+    solve."""
+    w = heterogeneous_cavity(n=n, seed=seed, Ra=Ra, Da=Da)
+    m = int(round(melted * n))
+    x = np.arange(n)[None, :]
+    w.fl0[:, :m] = 1.0
+    w.T0[:, :] = np.where(x < m, 1.0 - x / float(m), 0.0)
+    w.T0[:, 0] = 1.0
+    w.name = "heterogeneous_cavity_%d_seed%d_melted%g" % (n, seed, melted)
+    w.meta.update(melted=melted)
+    return w

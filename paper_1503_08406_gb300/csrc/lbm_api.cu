@@ -1,0 +1,610 @@
+// C ABI of liblbm (declared in include/lbm.h): context, parameter derivation,
+// workspace layout, step sequencing, outputs.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.cuh"
+
+using lbm::Dev;
+
+struct lbm_ctx {
+  lbm_params p;
+  Dev d;
+  cudaStream_t stream;
+  void* ws;
+  size_t ws_bytes;
+  bool own_ws;
+  int64_t steps;
+  int parity;          // layout before the next step: 0 natural (next step even), 1 swapped
+  double derived[8];
+  float* tmp;          // staging for host inputs/outputs, 9 n floats
+  double* partials;
+  double* sums;        // 8 doubles
+  int* bad;            // validation flag
+  int nred;
+  bool timing;
+  std::vector<cudaEvent_t> ev;   // per step: start, after fused, after enthalpy
+  // CUDA graphs of GRAPH_STEPS and 2 steps starting at parity 0, captured on a
+  // private stream and replayed on the context stream
+  cudaStream_t cap;
+  cudaGraphExec_t g_long, g_pair;
+  bool graphs_off;
+};
+
+static const int GRAPH_STEPS = 32;
+
+namespace {
+
+const double CS2 = 1.0 / 3.0;
+
+int derive(lbm_params* p, double out[8]) {
+  if (p->H <= 0) p->H = p->ny;
+  if (p->dT <= 0) p->dT = 1;
+  if (p->rho0 <= 0) p->rho0 = 1;
+  if (p->s_e <= 0) p->s_e = 1.1;
+  if (p->s_eps <= 0) p->s_eps = 1.1;
+  if (p->s_q <= 0) p->s_q = 1.2;
+  if (p->zeta_e <= 0) p->zeta_e = 1.5;
+  if (p->zeta_nu <= 0) p->zeta_nu = 1.5;
+  if (p->J <= 0) p->J = 1;
+  if (p->lambda_ <= 0) p->lambda_ = 1;
+  if (p->f_act <= 0) p->f_act = 1e-3;
+  if (p->max_inner_iters <= 0) p->max_inner_iters = 1000;
+  if (!(p->sigma > 0) || !(p->St > 0)) return LBM_ERR_INVALID_ARG;
+  if (!(p->varpi > -4 && p->varpi < 1)) return LBM_ERR_INVALID_ARG;
+  if (!(p->T_l >= p->T_s)) return LBM_ERR_INVALID_ARG;
+  const double csT2 = (4 + p->varpi) / 10.0;  // Eq. (39)
+  double tau_nu = 0, tau_T, nu_e = 0, nu_l = 0, g_beta = 0;
+  if (p->flow) {
+    if (p->tau_nu > 0) tau_nu = p->tau_nu;
+    else if (p->Ra > 0 && p->Pr > 0 && p->Ma > 0)
+      tau_nu = 0.5 + p->Ma * p->J * p->H * sqrt(3 * p->Pr) / sqrt(p->Ra);  // Sec. 4.3
+    else return LBM_ERR_INVALID_ARG;
+    nu_e = CS2 * (tau_nu - 0.5);
+    nu_l = nu_e / p->J;
+    if (p->tau_T > 0) {
+      tau_T = p->tau_T;
+    } else {
+      if (!(p->Pr > 0)) return LBM_ERR_INVALID_ARG;
+      tau_T = 0.5 + p->lambda_ * CS2 * (tau_nu - 0.5) / (p->J * p->sigma * csT2 * p->Pr);
+    }
+    if (p->g_beta >= 0) {
+      g_beta = p->g_beta;
+    } else {
+      if (!(p->Ra > 0) || !(p->Pr > 0)) return LBM_ERR_INVALID_ARG;
+      g_beta = p->Ra * nu_l * (nu_l / p->Pr) / (p->dT * p->H * p->H * p->H);  // Eq. (9)
+    }
+    if (!(tau_nu > 0.5)) return LBM_ERR_INVALID_ARG;
+  } else {
+    if (!(p->tau_T > 0)) return LBM_ERR_INVALID_ARG;
+    tau_T = p->tau_T;
+  }
+  if (!(tau_T > 0.5)) return LBM_ERR_INVALID_ARG;
+  out[0] = tau_nu;
+  out[1] = tau_T;
+  out[2] = nu_e;
+  out[3] = nu_l;
+  out[4] = p->sigma * csT2 * (tau_T - 0.5);  // alpha_e, Eq. (39)
+  out[5] = g_beta;
+  out[6] = csT2;
+  out[7] = p->dT / (p->sigma * p->St);
+  return LBM_OK;
+}
+
+int check_params(const lbm_params* p) {
+  if (!p) return LBM_ERR_INVALID_ARG;
+  if (p->nx < 3 || p->ny < 3) return LBM_ERR_INVALID_ARG;
+  // 32-bit node offsets address all 14 population planes
+  if ((long long)p->nx * p->ny * 14 >= (1LL << 31)) return LBM_ERR_INVALID_ARG;
+  for (int k = 0; k < 4; ++k)
+    if (p->bc[k] < LBM_BC_PERIODIC || p->bc[k] > LBM_BC_ADIABATIC) return LBM_ERR_INVALID_ARG;
+  if ((p->bc[0] == LBM_BC_PERIODIC) != (p->bc[1] == LBM_BC_PERIODIC)) return LBM_ERR_INVALID_ARG;
+  if ((p->bc[2] == LBM_BC_PERIODIC) != (p->bc[3] == LBM_BC_PERIODIC)) return LBM_ERR_INVALID_ARG;
+  return LBM_OK;
+}
+
+struct Layout {
+  size_t f, g, fl, phi, K, wallTl, flags, list, lcount, ctr, proc, scr, stats, tmp, partials, sums,
+      bad, total;
+};
+
+size_t up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+Layout layout_of(const lbm_params* p, int nred) {
+  const size_t n = (size_t)p->nx * p->ny;
+  const size_t tiles = (size_t)((p->nx + lbm::TE - 1) / lbm::TE) * ((p->ny + lbm::TE - 1) / lbm::TE);
+  Layout L;
+  size_t o = 0;
+  L.f = o; o += up(9 * n * sizeof(float));
+  L.g = o; o += up(5 * n * sizeof(float));
+  L.fl = o; o += up(n * sizeof(float));
+  L.phi = o; o += up(n * sizeof(float));
+  L.K = o; o += up(n * sizeof(float));
+  L.wallTl = o; o += up((size_t)p->ny * sizeof(float));
+  L.flags = o; o += up(tiles * sizeof(int));
+  L.list = o; o += up(2 * tiles * sizeof(int));
+  L.lcount = o; o += up(2 * sizeof(int));
+  L.ctr = o; o += up(sizeof(int));
+  L.proc = o; o += up(tiles * sizeof(int));
+  L.scr = o; o += up(n * sizeof(float2));
+  L.stats = o; o += up(4 * sizeof(int));
+  L.tmp = o; o += up(9 * n * sizeof(float));
+  L.partials = o; o += up((size_t)nred * 6 * sizeof(double));
+  L.sums = o; o += up(8 * sizeof(double));
+  L.bad = o; o += up(sizeof(int));
+  L.total = o;
+  return L;
+}
+
+int nred_of(const lbm_params* p) {
+  long long n = (long long)p->nx * p->ny;
+  long long b = (n + lbm::RB - 1) / lbm::RB;
+  return (int)(b < 1024 ? b : 1024);
+}
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA; }
+
+#define LBM_TRY(call)                     \
+  do {                                    \
+    int _r = (call);                      \
+    if (_r != LBM_OK) return _r;          \
+  } while (0)
+#define LBM_CUDA(call) LBM_TRY(cuda_err(call))
+
+int layout_now(const lbm_ctx* c) { return c->parity; }
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_error_string(int code) {
+  switch (code) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_INVALID_ARG: return "invalid argument";
+    case LBM_ERR_CUDA: return "CUDA error";
+    case LBM_ERR_NONFINITE: return "non-finite value in the state";
+    case LBM_ERR_NOT_CONVERGED: return "inner enthalpy iteration hit its cap";
+    case LBM_ERR_OOM: return "out of device memory or workspace too small";
+    case LBM_ERR_NO_DEVICE: return "no usable CUDA device";
+    default: return "unknown error";
+  }
+}
+
+int lbm_workspace_bytes(const lbm_params* p, size_t* bytes) {
+  if (!bytes) return LBM_ERR_INVALID_ARG;
+  LBM_TRY(check_params(p));
+  *bytes = layout_of(p, nred_of(p)).total;
+  return LBM_OK;
+}
+
+int lbm_create(const lbm_params* pin, void* stream, void* workspace, size_t workspace_bytes,
+               lbm_ctx** out) {
+  if (!out) return LBM_ERR_INVALID_ARG;
+  *out = nullptr;
+  LBM_TRY(check_params(pin));
+  lbm_params p = *pin;
+  double der[8];
+  LBM_TRY(derive(&p, der));
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return LBM_ERR_NO_DEVICE;
+  }
+  const int nred = nred_of(&p);
+  const Layout L = layout_of(&p, nred);
+  lbm_ctx* c = new (std::nothrow) lbm_ctx();
+  if (!c) return LBM_ERR_OOM;
+  c->p = p;
+  memcpy(c->derived, der, sizeof der);
+  c->stream = (cudaStream_t)stream;
+  c->nred = nred;
+  if (workspace) {
+    if (workspace_bytes < L.total || ((uintptr_t)workspace & 255)) {
+      delete c;
+      return workspace_bytes < L.total ? LBM_ERR_OOM : LBM_ERR_INVALID_ARG;
+    }
+    c->ws = workspace;
+    c->own_ws = false;
+  } else {
+    if (cudaMalloc(&c->ws, L.total) != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return LBM_ERR_OOM;
+    }
+    c->own_ws = true;
+  }
+  c->ws_bytes = L.total;
+  char* b = (char*)c->ws;
+  Dev& d = c->d;
+  memset(&d, 0, sizeof d);
+  d.nx = p.nx;
+  d.ny = p.ny;
+  d.n = (long long)p.nx * p.ny;
+  d.per_x = p.bc[0] == LBM_BC_PERIODIC;
+  d.per_y = p.bc[2] == LBM_BC_PERIODIC;
+  d.wall_l = !d.per_x;
+  d.wall_r = !d.per_x;
+  d.wall_b = !d.per_y;
+  d.wall_t = !d.per_y;
+  for (int k = 0; k < 4; ++k) {
+    d.bc[k] = p.bc[k];
+    d.Tbc[k] = (float)p.T_bc[k];
+  }
+  d.flow = p.flow ? 1 : 0;
+  d.rho0 = (float)p.rho0;
+  d.inv_rho0 = (float)(1.0 / p.rho0);
+  d.nu_l = (float)der[3];
+  d.g_beta = (float)der[5];
+  d.T_ref = (float)p.T_ref;
+  d.s_e = (float)p.s_e;
+  d.s_eps = (float)p.s_eps;
+  d.s_q = (float)p.s_q;
+  d.s_nu = p.flow ? (float)(1.0 / der[0]) : 0.f;
+  d.z_a = (float)(1.0 / der[1]);
+  d.z_e = (float)p.zeta_e;
+  d.z_nu = (float)p.zeta_nu;
+  d.varpi = (float)p.varpi;
+  d.csT2 = (float)der[6];
+  d.sigma = (float)p.sigma;
+  d.conv = p.flow ? (float)(1.0 / (p.sigma * der[6])) : 0.f;
+  d.wt0 = (float)((1 - p.varpi) / 5.0);
+  d.wt1 = (float)((4 + p.varpi) / 20.0);
+  d.lat = (float)der[7];
+  d.T_s = (float)p.T_s;
+  d.T_l = (float)p.T_l;
+  d.dTt = (float)(p.T_l - p.T_s);
+  d.f_act = (float)p.f_act;
+  {
+    double scale = fabs(p.T_s) > fabs(p.T_l) ? fabs(p.T_s) : fabs(p.T_l);
+    if (p.dT > scale) scale = p.dT;
+    if (scale < 1.0) scale = 1.0;
+    d.scr_T = (float)(p.screen_tol > 0 ? p.screen_tol : 1e-7 * scale);
+    d.scr_f = 1e-7f;
+    d.screen_off = p.screen_tol < 0 ? 1 : 0;
+  }
+  d.H_over_dT = (float)(p.H / p.dT);
+  d.etx = (p.nx + lbm::TE - 1) / lbm::TE;
+  d.ety = (p.ny + lbm::TE - 1) / lbm::TE;
+  d.ntiles = d.etx * d.ety;
+  {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+      sms = 1;
+    d.egrid = d.ntiles < 4 * sms ? d.ntiles : 4 * sms;
+    lbm::enthalpy_setup();
+  }
+  d.max_inner = p.max_inner_iters;
+  d.tol = (float)(p.inner_tol > 1e-6 ? p.inner_tol : 1e-6);
+  d.f = (float*)(b + L.f);
+  d.g = (float*)(b + L.g);
+  d.fl = (float*)(b + L.fl);
+  d.phi = (const float*)(b + L.phi);
+  d.K = (const float*)(b + L.K);
+  d.wallTl = (const float*)(b + L.wallTl);
+  d.flags = (int*)(b + L.flags);
+  d.list = (int*)(b + L.list);
+  d.lcount = (int*)(b + L.lcount);
+  d.ctr = (int*)(b + L.ctr);
+  d.proc = (int*)(b + L.proc);
+  d.scr = (float2*)(b + L.scr);
+  d.stats = (int*)(b + L.stats);
+  c->tmp = (float*)(b + L.tmp);
+  c->partials = (double*)(b + L.partials);
+  c->sums = (double*)(b + L.sums);
+  c->bad = (int*)(b + L.bad);
+  if (cudaMemsetAsync(c->ws, 0, L.total, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    lbm_destroy(c);
+    return LBM_ERR_CUDA;
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  if (c->g_long) cudaGraphExecDestroy(c->g_long);
+  if (c->g_pair) cudaGraphExecDestroy(c->g_pair);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  if (c->own_ws && c->ws) cudaFree(c->ws);
+  delete c;
+}
+
+int lbm_derived(const lbm_ctx* c, double out[8]) {
+  if (!c || !out) return LBM_ERR_INVALID_ARG;
+  memcpy(out, c->derived, sizeof c->derived);
+  return LBM_OK;
+}
+
+int64_t lbm_steps_done(const lbm_ctx* c) { return c ? c->steps : -1; }
+
+// empty work lists and tile flags; tile status words keep old stamps, which
+// never equal a later step's stamp
+static int reset_lists(lbm_ctx* c) {
+  const Dev& d = c->d;
+  LBM_CUDA(cudaMemsetAsync(d.flags, 0, sizeof(int) * d.ntiles, c->stream));
+  LBM_CUDA(cudaMemsetAsync(d.lcount, 0, 2 * sizeof(int), c->stream));
+  return LBM_OK;
+}
+
+static int copy_in(lbm_ctx* c, float* dst, const float* src, size_t count, int device_ptrs) {
+  return cuda_err(cudaMemcpyAsync(dst, src, count * sizeof(float),
+                                  device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  c->stream));
+}
+
+int lbm_set_fields(lbm_ctx* c, const float* phi, const float* K, const float* T0,
+                   const float* fl0, const float* wall_T_left, int device_ptrs) {
+  if (!c || !phi || !K || !T0 || !fl0) return LBM_ERR_INVALID_ARG;
+  const size_t n = (size_t)c->d.n;
+  Dev& d = c->d;
+  if (!device_ptrs) {
+    for (size_t s = 0; s < n; ++s) {
+      const float p = phi[s], k = K[s], t = T0[s], l = fl0[s];
+      if (!(p > 0.f && p <= 1.f) || (d.flow && !(p < 1.f)) || !(k > 0.f) || !isfinite(t) ||
+          !(l >= 0.f && l <= 1.f))
+        return LBM_ERR_INVALID_ARG;
+    }
+    if (wall_T_left)
+      for (int y = 0; y < c->p.ny; ++y)
+        if (!isfinite(wall_T_left[y])) return LBM_ERR_INVALID_ARG;
+  } else {
+    LBM_CUDA(cudaMemsetAsync(c->bad, 0, sizeof(int), c->stream));
+    lbm::launch_validate(d, phi, K, T0, fl0, c->bad, c->stream);
+    int bad = 0;
+    LBM_CUDA(cudaMemcpyAsync(&bad, c->bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    if (bad) return LBM_ERR_INVALID_ARG;
+  }
+  LBM_TRY(copy_in(c, (float*)d.phi, phi, n, device_ptrs));
+  LBM_TRY(copy_in(c, (float*)d.K, K, n, device_ptrs));
+  LBM_TRY(copy_in(c, d.fl, fl0, n, device_ptrs));
+  LBM_TRY(copy_in(c, c->tmp, T0, n, device_ptrs));
+  if (wall_T_left) {
+    LBM_TRY(copy_in(c, (float*)d.wallTl, wall_T_left, (size_t)c->p.ny, device_ptrs));
+  } else {
+    std::vector<float> w((size_t)c->p.ny, (float)c->p.T_bc[LBM_SIDE_LEFT]);
+    LBM_CUDA(cudaMemcpyAsync((float*)d.wallTl, w.data(), w.size() * sizeof(float),
+                             cudaMemcpyHostToDevice, c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  lbm::launch_init(d, c->tmp, c->stream);
+  LBM_CUDA(cudaGetLastError());
+  LBM_TRY(reset_lists(c));
+  c->steps = 0;
+  c->parity = 0;
+  if (!device_ptrs) LBM_CUDA(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+static void launch_one_step(lbm_ctx* c, int parity, cudaStream_t st) {
+  lbm::launch_fused(c->d, parity, st);
+  lbm::launch_enthalpy_solve(c->d, parity, st);
+  lbm::launch_enthalpy_commit(c->d, parity, st);
+}
+
+// Capture `steps` (even) steps starting at parity 0 into an executable graph.
+static cudaGraphExec_t capture(lbm_ctx* c, int steps) {
+  if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    c->cap = nullptr;
+    return nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  for (int k = 0; k < steps; ++k) launch_one_step(c, k & 1, c->cap);
+  if (cudaStreamEndCapture(c->cap, &g) != cudaSuccess || !g) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaGraphExec_t ex = nullptr;
+  if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    ex = nullptr;
+  }
+  cudaGraphDestroy(g);
+  return ex;
+}
+
+static int step_direct(lbm_ctx* c) {
+  cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (c->timing) {
+    for (int k = 0; k < 4; ++k) {
+      if (cudaEventCreate(&e[k]) != cudaSuccess) return LBM_ERR_CUDA;
+      c->ev.push_back(e[k]);
+    }
+    cudaEventRecord(e[0], c->stream);
+  }
+  lbm::launch_fused(c->d, c->parity, c->stream);
+  if (c->timing) cudaEventRecord(e[1], c->stream);
+  lbm::launch_enthalpy_solve(c->d, c->parity, c->stream);
+  if (c->timing) cudaEventRecord(e[2], c->stream);
+  lbm::launch_enthalpy_commit(c->d, c->parity, c->stream);
+  if (c->timing) cudaEventRecord(e[3], c->stream);
+  c->parity ^= 1;
+  c->steps++;
+  return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* c, int64_t nsteps) {
+  if (!c || nsteps < 0) return LBM_ERR_INVALID_ARG;
+  // timed runs launch kernel by kernel so events can bracket each kernel
+  const bool graphs = !c->timing && !c->graphs_off;
+  while (nsteps > 0 && (c->parity != 0 || !graphs || nsteps < 2)) {
+    LBM_TRY(step_direct(c));
+    --nsteps;
+  }
+  if (nsteps >= GRAPH_STEPS && !c->g_long) c->g_long = capture(c, GRAPH_STEPS);
+  if (nsteps >= 2 && !c->g_pair) c->g_pair = capture(c, 2);
+  while (nsteps >= GRAPH_STEPS && c->g_long) {
+    LBM_CUDA(cudaGraphLaunch(c->g_long, c->stream));
+    nsteps -= GRAPH_STEPS;
+    c->steps += GRAPH_STEPS;
+  }
+  while (nsteps >= 2 && c->g_pair) {
+    LBM_CUDA(cudaGraphLaunch(c->g_pair, c->stream));
+    nsteps -= 2;
+    c->steps += 2;
+  }
+  while (nsteps > 0) {
+    LBM_TRY(step_direct(c));
+    --nsteps;
+  }
+  return cuda_err(cudaGetLastError());
+}
+
+int lbm_status(lbm_ctx* c) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  int st[4];
+  LBM_CUDA(cudaMemcpyAsync(st, c->d.stats, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(cudaStreamSynchronize(c->stream));
+  if (st[0]) {
+    LBM_CUDA(cudaMemsetAsync(c->d.stats, 0, sizeof(int), c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    return LBM_ERR_NOT_CONVERGED;
+  }
+  return LBM_OK;
+}
+
+int lbm_get_macros(lbm_ctx* c, float* ux, float* uy, float* rho, float* T, float* fl,
+                   int device_ptrs) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  const size_t n = (size_t)c->d.n;
+  float* outs[5] = {ux, uy, rho, T, fl};
+  float* dst[5];
+  for (int k = 0; k < 5; ++k)
+    dst[k] = outs[k] ? (device_ptrs ? outs[k] : c->tmp + k * n) : nullptr;
+  lbm::launch_macros(c->d, layout_now(c), dst[0], dst[1], dst[2], dst[3], dst[4], c->stream);
+  LBM_CUDA(cudaGetLastError());
+  if (!device_ptrs) {
+    for (int k = 0; k < 5; ++k)
+      if (outs[k])
+        LBM_CUDA(cudaMemcpyAsync(outs[k], dst[k], n * sizeof(float), cudaMemcpyDeviceToHost,
+                                 c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  return LBM_OK;
+}
+
+int lbm_reduce(lbm_ctx* c, double out[4]) {
+  if (!c || !out) return LBM_ERR_INVALID_ARG;
+  lbm::launch_reduce(c->d, layout_now(c), c->partials, c->sums, c->nred, c->stream);
+  LBM_CUDA(cudaGetLastError());
+  double s[4];
+  LBM_CUDA(cudaMemcpyAsync(s, c->sums, sizeof s, cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(cudaStreamSynchronize(c->stream));
+  memcpy(out, s, sizeof s);
+  for (int k = 0; k < 4; ++k)
+    if (!isfinite(s[k])) return LBM_ERR_NONFINITE;
+  return LBM_OK;
+}
+
+int lbm_get_state(lbm_ctx* c, float* f, float* g, float* fl, int device_ptrs) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  const size_t n = (size_t)c->d.n;
+  float* df = f ? (device_ptrs ? f : c->tmp) : nullptr;
+  float* dg = g ? (device_ptrs ? g : c->tmp) : nullptr;
+  if (f) {
+    lbm::launch_get_state(c->d, layout_now(c), df, nullptr, c->stream);
+    LBM_CUDA(cudaGetLastError());
+    if (!device_ptrs) {
+      LBM_CUDA(cudaMemcpyAsync(f, df, 9 * n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+      LBM_CUDA(cudaStreamSynchronize(c->stream));
+    }
+  }
+  if (g) {
+    lbm::launch_get_state(c->d, layout_now(c), nullptr, dg, c->stream);
+    LBM_CUDA(cudaGetLastError());
+    if (!device_ptrs) {
+      LBM_CUDA(cudaMemcpyAsync(g, dg, 5 * n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+      LBM_CUDA(cudaStreamSynchronize(c->stream));
+    }
+  }
+  if (fl) {
+    LBM_CUDA(cudaMemcpyAsync(fl, c->d.fl, n * sizeof(float),
+                             device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             c->stream));
+    if (!device_ptrs) LBM_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  return LBM_OK;
+}
+
+int lbm_set_state(lbm_ctx* c, const float* f, const float* g, const float* fl, int device_ptrs) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  const size_t n = (size_t)c->d.n;
+  const float* sf = f;
+  const float* sg = g;
+  if (f && !device_ptrs) {
+    LBM_CUDA(cudaMemcpyAsync(c->tmp, f, 9 * n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    sf = c->tmp;
+  }
+  if (f) {
+    lbm::launch_set_state(c->d, sf, nullptr, c->stream);
+    LBM_CUDA(cudaGetLastError());
+  }
+  if (g && !device_ptrs) {
+    LBM_CUDA(cudaMemcpyAsync(c->tmp, g, 5 * n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    sg = c->tmp;
+  }
+  if (g) {
+    lbm::launch_set_state(c->d, nullptr, sg, c->stream);
+    LBM_CUDA(cudaGetLastError());
+  }
+  if (fl) LBM_TRY(copy_in(c, c->d.fl, fl, n, device_ptrs));
+  LBM_TRY(reset_lists(c));
+  c->parity = 0;
+  c->steps = 0;
+  LBM_CUDA(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int lbm_timing(lbm_ctx* c, int enable) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  LBM_CUDA(cudaStreamSynchronize(c->stream));
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  c->ev.clear();
+  c->timing = enable != 0;
+  static const int zero[2] = {0, 0};
+  LBM_CUDA(cudaMemcpyAsync(c->d.stats + 1, zero, 2 * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  LBM_CUDA(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int lbm_timing_read(lbm_ctx* c, double* fused_ms, double* solve_ms, double* commit_ms,
+                    int64_t* steps_timed, int64_t* tiles_solved, int32_t* max_sweeps) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  LBM_CUDA(cudaStreamSynchronize(c->stream));
+  double tf = 0, ts = 0, tc = 0;
+  for (size_t k = 0; k + 3 < c->ev.size(); k += 4) {
+    float a = 0, b = 0, e = 0;
+    LBM_CUDA(cudaEventElapsedTime(&a, c->ev[k], c->ev[k + 1]));
+    LBM_CUDA(cudaEventElapsedTime(&b, c->ev[k + 1], c->ev[k + 2]));
+    LBM_CUDA(cudaEventElapsedTime(&e, c->ev[k + 2], c->ev[k + 3]));
+    tf += a;
+    ts += b;
+    tc += e;
+  }
+  int st[4];
+  LBM_CUDA(cudaMemcpy(st, c->d.stats, sizeof st, cudaMemcpyDeviceToHost));
+  if (fused_ms) *fused_ms = tf;
+  if (solve_ms) *solve_ms = ts;
+  if (commit_ms) *commit_ms = tc;
+  if (steps_timed) *steps_timed = (int64_t)(c->ev.size() / 4);
+  if (tiles_solved) *tiles_solved = st[1];
+  if (max_sweeps) *max_sweeps = st[2];
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,239 @@
+// Utility kernels: initial equilibria, macroscopic outputs, FP64 reductions,
+// checkpoint gather/scatter and input validation.
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+// ---- population gathers for any node, any layout --------------------------
+
+__device__ __forceinline__ bool flow_active(const Dev& d, int x, int y) {
+  return !is_wall(d, x, y) && d.fl[(long long)y * d.nx + x] >= d.f_act;
+}
+
+// g_i of non-wall node (x, y) in the given layout
+__device__ __forceinline__ void gather_g(const Dev& d, int x, int y, int layout, float g[5]) {
+  const long long n = d.n, s = (long long)y * d.nx + x;
+  g[0] = d.g[s];
+  for (int i = 1; i < 5; ++i) {
+    if (layout == 0) {
+      g[i] = d.g[i * n + s];
+    } else {
+      const int sx = wrapx(d, x - ex9(i)), sy = wrapy(d, y - ey9(i));
+      g[i] = d.g[opp5(i) * n + (long long)sy * d.nx + sx];
+    }
+  }
+}
+
+// f_i of node (x, y): nodes without flow hold theirs in their own slots
+__device__ __forceinline__ void gather_f(const Dev& d, int x, int y, int layout, float f[9]) {
+  const long long n = d.n, s = (long long)y * d.nx + x;
+  const bool self = flow_active(d, x, y);
+  f[0] = d.f[s];
+  for (int i = 1; i < 9; ++i) {
+    if (layout == 0 || !self) {
+      f[i] = d.f[i * n + s];
+    } else {
+      const int sx = wrapx(d, x - ex9(i)), sy = wrapy(d, y - ey9(i));
+      if (flow_active(d, sx, sy)) f[i] = d.f[opp9(i) * n + (long long)sy * d.nx + sx];
+      else f[i] = d.f[i * n + s];
+    }
+  }
+}
+
+__device__ float node_T(const Dev& d, int x, int y, int layout);
+
+// temperature of a non-wall node
+__device__ __forceinline__ float interior_T(const Dev& d, int x, int y, int layout) {
+  float g[5];
+  gather_g(d, x, y, layout, g);
+  return g[0] + g[1] + g[2] + g[3] + g[4];
+}
+
+// temperature of any node; wall nodes report the temperature their wall
+// imposes (Dirichlet value, or the inward neighbour's for an adiabatic wall;
+// a corner follows its vertical wall, then its horizontal wall's Dirichlet
+// value, then its diagonal neighbour)
+__device__ float node_T(const Dev& d, int x, int y, int layout) {
+  if (!is_wall(d, x, y)) return interior_T(d, x, y, layout);
+  int side;
+  if (d.wall_l && x == 0) side = 0;
+  else if (d.wall_r && x == d.nx - 1) side = 1;
+  else if (d.wall_b && y == 0) side = 2;
+  else side = 3;
+  if (d.bc[side] == 1) return side == 0 ? d.wallTl[y] : d.Tbc[side];
+  const bool vx = (d.wall_l || d.wall_r) && (x == 0 || x == d.nx - 1);
+  const bool vy = (d.wall_b || d.wall_t) && (y == 0 || y == d.ny - 1);
+  if (vx && vy) {
+    const int hs = (y == 0) ? 2 : 3;
+    if (d.bc[hs] == 1) return d.Tbc[hs];
+    return interior_T(d, x == 0 ? 1 : d.nx - 2, y == 0 ? 1 : d.ny - 2, layout);
+  }
+  switch (side) {
+    case 0: return interior_T(d, 1, y, layout);
+    case 1: return interior_T(d, d.nx - 2, y, layout);
+    case 2: return interior_T(d, x, 1, layout);
+    default: return interior_T(d, x, d.ny - 2, layout);
+  }
+}
+
+// ---- kernels ----------------------------------------------------------------
+
+__global__ void init_kernel(Dev d, const float* T0) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= d.n) return;
+  const long long n = d.n;
+  // f^eq(rho0, u = 0) = w_i rho0, Eq. (29); stored as the deviation f - w_i rho0 = 0
+  for (int i = 0; i < 9; ++i) d.f[i * n + s] = 0.f;
+  // g^eq(T0, u = 0), Eq. (39): w~_i T0
+  const float T = T0[s];
+  d.g[s] = d.wt0 * T;
+  for (int i = 1; i < 5; ++i) d.g[i * n + s] = d.wt1 * T;
+}
+
+__global__ void macros_kernel(Dev d, int layout, float* ux, float* uy, float* rho, float* T,
+                              float* fl) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= d.n) return;
+  const int y = (int)(s / d.nx), x = (int)(s - (long long)y * d.nx);
+  const float Tn = node_T(d, x, y, layout);
+  float f[9];
+  if (is_wall(d, x, y)) {
+    for (int i = 0; i < 9; ++i) f[i] = d.f[i * d.n + s];
+  } else {
+    gather_f(d, x, y, layout, f);
+  }
+  float dr = 0.f;
+  for (int i = 0; i < 9; ++i) dr += f[i];
+  const float r = d.rho0 + dr;   // stored populations are f_i - w_i rho0
+  float vx = 0.f, vy = 0.f;
+  if (d.flow && flow_active(d, x, y)) {
+    const float jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+    const float jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+    float Fx, Fy;
+    velocity(jx, jy, Tn, d.fl[s], d.phi[s], d.K[s], d, vx, vy, Fx, Fy);
+  }
+  if (ux) ux[s] = vx;
+  if (uy) uy[s] = vy;
+  if (rho) rho[s] = r;
+  if (T) T[s] = Tn;
+  if (fl) fl[s] = d.fl[s];
+}
+
+// per-block FP64 partial sums in a fixed order:
+// [0] mass, [1] enthalpy, [2] sum f_l, [3] non-wall count, [4] Nusselt sum, [5] Nusselt rows
+__global__ void __launch_bounds__(RB) reduce_kernel(Dev d, int layout, double* partials) {
+  __shared__ double sh[6][RB];
+  const int tid = threadIdx.x;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (long long s = blockIdx.x * (long long)RB + tid; s < d.n; s += (long long)gridDim.x * RB) {
+    const int y = (int)(s / d.nx), x = (int)(s - (long long)y * d.nx);
+    if (!is_wall(d, x, y)) {
+      float f[9];
+      gather_f(d, x, y, layout, f);
+      double m = (double)d.rho0;   // stored populations are f_i - w_i rho0
+      for (int i = 0; i < 9; ++i) m += (double)f[i];
+      const double T = (double)interior_T(d, x, y, layout);
+      const double fl = (double)d.fl[s];
+      acc[0] += m;
+      acc[1] += T + (double)d.phi[s] * (double)d.lat * fl;
+      acc[2] += fl;
+      acc[3] += 1.0;
+    }
+    if (d.wall_l && x == 0 && d.nx >= 3 && (!d.wall_b || (y > 0 && y < d.ny - 1))) {
+      const double T0 = node_T(d, 0, y, layout), T1 = node_T(d, 1, y, layout),
+                   T2 = node_T(d, 2, y, layout);
+      acc[4] += -(-3.0 * T0 + 4.0 * T1 - T2) * 0.5 * (double)d.H_over_dT;
+      acc[5] += 1.0;
+    }
+  }
+  for (int k = 0; k < 6; ++k) sh[k][tid] = acc[k];
+  __syncthreads();
+  for (int w = RB / 2; w > 0; w >>= 1) {
+    if (tid < w)
+      for (int k = 0; k < 6; ++k) sh[k][tid] += sh[k][tid + w];
+    __syncthreads();
+  }
+  if (tid == 0)
+    for (int k = 0; k < 6; ++k) partials[blockIdx.x * 6 + k] = sh[k][0];
+}
+
+__global__ void reduce_final_kernel(const double* partials, int nblocks, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double t[6] = {0, 0, 0, 0, 0, 0};
+  for (int b = 0; b < nblocks; ++b)
+    for (int k = 0; k < 6; ++k) t[k] += partials[b * 6 + k];
+  out[0] = t[0];
+  out[1] = t[1];
+  out[2] = t[3] > 0 ? t[2] / t[3] : 0.0;
+  out[3] = t[5] > 0 ? t[4] / t[5] : 0.0;
+}
+
+__global__ void get_state_kernel(Dev d, int layout, float* f, float* g) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= d.n) return;
+  const int y = (int)(s / d.nx), x = (int)(s - (long long)y * d.nx);
+  const long long n = d.n;
+  float fv[9], gv[5];
+  if (is_wall(d, x, y)) {
+    for (int i = 0; i < 9; ++i) fv[i] = d.f[i * n + s];
+    for (int i = 0; i < 5; ++i) gv[i] = d.g[i * n + s];
+  } else {
+    gather_f(d, x, y, layout, fv);
+    gather_g(d, x, y, layout, gv);
+  }
+  if (f)
+    for (int i = 0; i < 9; ++i) f[i * n + s] = fv[i];
+  if (g)
+    for (int i = 0; i < 5; ++i) g[i * n + s] = gv[i];
+}
+
+__global__ void set_state_kernel(Dev d, const float* f, const float* g) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= d.n) return;
+  const long long n = d.n;
+  if (f)
+    for (int i = 0; i < 9; ++i) d.f[i * n + s] = f[i * n + s];
+  if (g)
+    for (int i = 0; i < 5; ++i) d.g[i * n + s] = g[i * n + s];
+}
+
+__global__ void validate_kernel(Dev d, const float* phi, const float* K, const float* T0,
+                                const float* fl0, int* bad) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= d.n) return;
+  const float p = phi[s], k = K[s], t = T0[s], l = fl0[s];
+  bool ok = (p > 0.f && p <= 1.f) && (!d.flow || p < 1.f) && (k > 0.f) && isfinite(t) &&
+            (l >= 0.f && l <= 1.f);
+  if (!ok) atomicExch(bad, 1);
+}
+
+static unsigned grid1(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+void launch_init(const Dev& d, const float* T0, cudaStream_t s) {
+  init_kernel<<<grid1(d.n, 256), 256, 0, s>>>(d, T0);
+}
+void launch_macros(const Dev& d, int layout, float* ux, float* uy, float* rho, float* T,
+                   float* fl, cudaStream_t s) {
+  macros_kernel<<<grid1(d.n, 256), 256, 0, s>>>(d, layout, ux, uy, rho, T, fl);
+}
+int reduce_blocks(const Dev& d) {
+  long long b = (d.n + RB - 1) / RB;
+  return (int)(b < 1024 ? b : 1024);
+}
+void launch_reduce(const Dev& d, int layout, double* partials, double* out, int nblocks,
+                   cudaStream_t s) {
+  reduce_kernel<<<nblocks, RB, 0, s>>>(d, layout, partials);
+  reduce_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, out);
+}
+void launch_get_state(const Dev& d, int layout, float* f, float* g, cudaStream_t s) {
+  get_state_kernel<<<grid1(d.n, 256), 256, 0, s>>>(d, layout, f, g);
+}
+void launch_set_state(const Dev& d, const float* f, const float* g, cudaStream_t s) {
+  set_state_kernel<<<grid1(d.n, 256), 256, 0, s>>>(d, f, g);
+}
+void launch_validate(const Dev& d, const float* phi, const float* K, const float* T0,
+                     const float* fl0, int* bad, cudaStream_t s) {
+  validate_kernel<<<grid1(d.n, 256), 256, 0, s>>>(d, phi, K, T0, fl0, bad);
+}
+
+}  // namespace lbm

@@ -1,0 +1,282 @@
+// Iterative enthalpy method for f_l(n+1) and the latent-heat source, Eq. (38),
+// (40)-(42) and the inner iteration of Sec. 3.2.
+//
+// The fused kernel streamed the source-free thermal populations, so a node y
+// sees T*(y) = sum_i g_i(y).  The latent source S~ = (S0, 0, 0, varpi S0, 0)
+// of node x, S0 = -a(x) (f_l(n+1) - f_l(n)), a = phi dT / (sigma St), adds
+// N^-1 S~ = S0 w~ to the post-collision populations of x, which stream to the
+// neighbours: T(y) = T*(y) + sum_i w~_i S0(y - e_i).  With h = T + a f_l, the
+// enthalpy relation f_l = clamp((h - T_s)/(T_l - T_s + a), 0, 1) is solved for
+// f_l(n+1) as a fixed point.
+//
+// Work list.  The fused kernel appends every 32x32 tile that may hold a phase
+// change this step to list[parity] (a tile flag de-duplicates).  Both kernels
+// below run a fixed grid of CTAs that walk that list, so steps with no front
+// cost almost nothing.  Per-tile status words carry a step stamp (a counter the
+// fused kernel advances), so nothing needs clearing between steps.
+//
+// enthalpy_solve: per listed tile, load T*, f_l(n) and a on the tile plus an
+// 8-node halo into shared memory and run red-black Gauss-Seidel sweeps; each
+// node update solves its own term exactly,
+//   f(x) = clamp((T*(x) + w~_0 a f_l(n) - T_s - w~_1 sum_{i>0} q(x - e_i)) / (T_l - T_s + w~_0 a), 0, 1),
+//   q = a (f - f_l(n)),
+// which has the same fixed point as the plain iteration (the map is monotone
+// with slope < 1).  Sweeps stop when no node moves by more than about four
+// float32 ulps: Gauss-Seidel from f_l(n) approaches the fixed point from one
+// side, so a looser stop would bias every step the same way, and a tighter
+// one can chase a one-ulp rounding cycle forever.  Nodes outside
+// the halo keep f = f_l(n).  The tile's own results go to scratch as
+// (f_l(n), f_l(n+1)).
+//
+// enthalpy_commit: per listed tile, store f_l(n+1), add the streamed source of
+// every changed node to the five populations it reaches, and, before an odd
+// step, swap the two slots of every flow link whose "both ends carry flow"
+// state changed, so the AA layout matches the new flow mask.
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+constexpr int RC = RE / 2;  // nodes of one colour per region row
+
+__device__ __forceinline__ int stamp_of(const Dev& d) { return *d.ctr & 0x0FFFFFFF; }
+__device__ __forceinline__ bool solved(const Dev& d, int tile, int stamp) {
+  return (d.proc[tile] >> 3) == stamp;
+}
+
+// T* at node (x, y) from the populations after the step: natural layout
+// (layout 0) or swapped (layout 1, population i of x sits in x - e_i).
+__device__ __forceinline__ float tstar(const Dev& d, int x, int y, int layout) {
+  const int n = (int)d.n;
+  const int s = y * d.nx + x;
+  if (layout == 0) return d.g[s] + d.g[n + s] + d.g[2 * n + s] + d.g[3 * n + s] + d.g[4 * n + s];
+  const int xm = (x == 0) ? d.nx - 1 : x - 1, xp = (x == d.nx - 1) ? 0 : x + 1;
+  const int ym = (y == 0) ? d.ny - 1 : y - 1, yp = (y == d.ny - 1) ? 0 : y + 1;
+  return d.g[s] + d.g[3 * n + y * d.nx + xm] + d.g[4 * n + ym * d.nx + x] +
+         d.g[1 * n + y * d.nx + xp] + d.g[2 * n + yp * d.nx + x];
+}
+
+template <int PAR>
+__global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
+  constexpr int LAYOUT = 1 - PAR;
+  extern __shared__ float smem[];
+  float* sbase = smem;               // T* + w~0 a f_l(n) - T_s
+  float* sinv = sbase + RE * RE;     // 1 / (T_l - T_s + w~0 a); 0 on fixed nodes
+  float* sa = sinv + RE * RE;        // a; 0 on walls and outside
+  float* sfn = sa + RE * RE;         // f_l(n)
+  float* sq = sfn + RE * RE;         // a (f - f_l(n))
+  float* sf = sq + RE * RE;          // current iterate
+  const int tid = threadIdx.x;
+  const int cnt = d.lcount[PAR];
+  const int stamp = stamp_of(d);
+  const float w0 = d.wt0, w1 = d.wt1, Ts = d.T_s, dTt = d.dTt;
+  for (int li = blockIdx.x; li < cnt; li += gridDim.x) {
+    const int tile = d.list[PAR * d.ntiles + li];
+    const int X0 = (tile % d.etx) * TE, Y0 = (tile / d.etx) * TE;
+#pragma unroll 3
+    for (int k = tid; k < RE * RE; k += EB) {
+      const int ly = k / RE, lx = k - ly * RE;
+      const int gx = wrapx(d, X0 - RH + lx), gy = wrapy(d, Y0 - RH + ly);
+      float base = 0.f, inv = 0.f, a = 0.f, fn = 0.f;
+      if (gx >= 0 && gy >= 0) {
+        const int s = gy * d.nx + gx;
+        fn = d.fl[s];
+        if (!is_wall(d, gx, gy)) {
+          a = d.phi[s] * d.lat;
+          base = tstar(d, gx, gy, LAYOUT) + w0 * a * fn - Ts;
+          inv = 1.f / (dTt + w0 * a);
+        }
+      }
+      sbase[k] = base;
+      sinv[k] = inv;
+      sa[k] = a;
+      sfn[k] = fn;
+      sq[k] = 0.f;
+      sf[k] = fn;
+    }
+    __syncthreads();
+    int it = 0;
+    bool more = true;
+    for (; it < d.max_inner && more; ++it) {
+      bool changed = false;
+#pragma unroll
+      for (int color = 0; color < 2; ++color) {
+        for (int j = tid; j < RE * RC; j += EB) {
+          const int ly = j / RC;
+          const int lx = 2 * (j - ly * RC) + ((ly + color) & 1);
+          const int k = ly * RE + lx;
+          const float a = sa[k];
+          if (a == 0.f) continue;
+          float nb = 0.f;
+          if (lx > 0) nb += sq[k - 1];
+          if (lx < RE - 1) nb += sq[k + 1];
+          if (ly > 0) nb += sq[k - RE];
+          if (ly < RE - 1) nb += sq[k + RE];
+          float v = (sbase[k] - w1 * nb) * sinv[k];
+          v = fminf(fmaxf(v, 0.f), 1.f);
+          if (fabsf(v - sf[k]) > 4.8e-7f * v + 1e-12f) changed = true;
+          sf[k] = v;
+          sq[k] = a * (v - sfn[k]);
+        }
+        __syncthreads();
+      }
+      more = __syncthreads_or(changed);
+    }
+    bool fchg = false, achg = false;
+    for (int k = tid; k < TE * TE; k += EB) {
+      const int ly = k / TE, lx = k - ly * TE;
+      const int gx = X0 + lx, gy = Y0 + ly;
+      if (gx >= d.nx || gy >= d.ny) continue;
+      const int r = (ly + RH) * RE + (lx + RH);
+      const float fo = sfn[r], fnw = sf[r];
+      d.scr[gy * d.nx + gx] = make_float2(fo, fnw);
+      if (fnw != fo) {
+        fchg = true;
+        if ((fo >= d.f_act) != (fnw >= d.f_act)) achg = true;
+      }
+    }
+    const int bits = 1 | (__syncthreads_or(fchg) ? 2 : 0) | (__syncthreads_or(achg) ? 4 : 0);
+    if (tid == 0) {
+      if (more) atomicExch(&d.stats[0], 1);
+      atomicAdd(&d.stats[1], 1);
+      atomicMax(&d.stats[2], it);
+      d.proc[tile] = (stamp << 3) | bits;
+    }
+    __syncthreads();
+  }
+}
+
+template <int PAR>
+__global__ void __launch_bounds__(EB) enthalpy_commit_kernel(Dev d) {
+  constexpr int LAYOUT = 1 - PAR;
+  constexpr int RW = TE + 2;              // tile plus a one-node ring
+  __shared__ float2 sp[RW * RW];          // (f_l(n), f_l(n+1)); (-1,-1) on walls / outside
+  __shared__ unsigned char ssolved[RW * RW];
+  __shared__ int links;
+  const int tid = threadIdx.x;
+  const int cnt = d.lcount[PAR];
+  const int stamp = stamp_of(d);
+  const int n = (int)d.n;
+  // the next step's list starts empty (nothing reads it during this step)
+  if (blockIdx.x == 0 && tid == 0) d.lcount[1 - PAR] = 0;
+  for (int li = blockIdx.x; li < cnt; li += gridDim.x) {
+    const int tile = d.list[PAR * d.ntiles + li];
+    const int tx0 = tile % d.etx, ty0 = tile / d.etx;
+    const int X0 = tx0 * TE, Y0 = ty0 * TE;
+    const int pb = d.proc[tile] & 7;
+    if (tid == 0) {
+      d.flags[tile] = 0;
+      // flow links need attention only around tiles where a node's activity changed
+      int l = 0;
+      if (d.flow && LAYOUT == 1) {
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            int tx = tx0 + dx, ty = ty0 + dy;
+            if (tx < 0 || tx >= d.etx) {
+              if (!d.per_x) continue;
+              tx = (tx + d.etx) % d.etx;
+            }
+            if (ty < 0 || ty >= d.ety) {
+              if (!d.per_y) continue;
+              ty = (ty + d.ety) % d.ety;
+            }
+            const int t = ty * d.etx + tx;
+            if (solved(d, t, stamp) && (d.proc[t] & 4)) l = 1;
+          }
+      }
+      links = l;
+    }
+    __syncthreads();
+    const bool lk = links != 0;
+    if ((pb & 2) || lk) {
+      if (lk) {
+        // old/new liquid fraction of the tile and its ring: scratch in tiles
+        // solved this step, the (unchanged) stored value elsewhere
+#pragma unroll 2
+        for (int k = tid; k < RW * RW; k += EB) {
+          const int ly = k / RW, lx = k - ly * RW;
+          const int gx = wrapx(d, X0 - 1 + lx), gy = wrapy(d, Y0 - 1 + ly);
+          float2 v = make_float2(-1.f, -1.f);
+          unsigned char sol = 0;
+          if (gx >= 0 && gy >= 0 && !is_wall(d, gx, gy)) {
+            const int gs = gy * d.nx + gx;
+            sol = solved(d, (gy / TE) * d.etx + (gx / TE), stamp) ? 1 : 0;
+            if (sol) {
+              v = d.scr[gs];
+            } else {
+              const float f = d.fl[gs];
+              v = make_float2(f, f);
+            }
+          }
+          sp[k] = v;
+          ssolved[k] = sol;
+        }
+        __syncthreads();
+      }
+#pragma unroll 4
+      for (int k = tid; k < TE * TE; k += EB) {
+        const int ly = k / TE, lx = k - ly * TE;
+        const int x = X0 + lx, y = Y0 + ly;
+        if (x >= d.nx || y >= d.ny || is_wall(d, x, y)) continue;
+        const int s = y * d.nx + x;
+        const float2 p = d.scr[s];
+        const float fn = p.x, fnew = p.y;
+        if (fnew != fn) {
+          d.fl[s] = fnew;
+          const float S0 = -d.phi[s] * d.lat * (fnew - fn);
+          // N^-1 S~ = S0 w~, streamed: population i of node x + e_i gains w~_i S0
+#pragma unroll
+          for (int i = 0; i < 5; ++i) {
+            const int rx = wrapx(d, x + ex9(i)), ry = wrapy(d, y + ey9(i));
+            if (rx < 0 || ry < 0 || is_wall(d, rx, ry)) continue;
+            const float w = (i == 0) ? d.wt0 : d.wt1;
+            const int slot = (LAYOUT == 1) ? opp5(i) * n + s : i * n + ry * d.nx + rx;
+            d.g[slot] += w * S0;
+          }
+        }
+        if (lk) {
+          const bool ao = fn >= d.f_act, an = fnew >= d.f_act;
+          const int c = (ly + 1) * RW + (lx + 1);
+#pragma unroll
+          for (int i = 1; i < 9; ++i) {
+            const int q = c + ey9(i) * RW + ex9(i);
+            const float2 pp = sp[q];
+            const bool po = pp.x >= d.f_act, pn = pp.y >= d.f_act;
+            if ((ao && po) == (an && pn)) continue;
+            // link (x, x + e_i) belongs to x for E, N, NE, NW, otherwise to the
+            // partner; a partner in a tile not solved this step cannot handle it
+            const bool own = (i == 1 || i == 2 || i == 5 || i == 6);
+            if (!own && ssolved[q]) continue;
+            const int px = wrapx(d, x + ex9(i)), py = wrapy(d, y + ey9(i));
+            float* A = d.f + i * n + (py * d.nx + px);
+            float* B = d.f + opp9(i) * n + s;
+            const float t = *A;
+            *A = *B;
+            *B = t;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+size_t enthalpy_solve_smem() { return 6 * RE * RE * sizeof(float); }
+
+void enthalpy_setup() {
+  const int bytes = (int)enthalpy_solve_smem();
+  cudaFuncSetAttribute(enthalpy_solve_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(enthalpy_solve_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+void launch_enthalpy_solve(const Dev& d, int parity, cudaStream_t s) {
+  const size_t sm = enthalpy_solve_smem();
+  if (parity == 0) enthalpy_solve_kernel<0><<<d.egrid, EB, sm, s>>>(d);
+  else enthalpy_solve_kernel<1><<<d.egrid, EB, sm, s>>>(d);
+}
+
+void launch_enthalpy_commit(const Dev& d, int parity, cudaStream_t s) {
+  if (parity == 0) enthalpy_commit_kernel<0><<<d.egrid, EB, 0, s>>>(d);
+  else enthalpy_commit_kernel<1><<<d.egrid, EB, 0, s>>>(d);
+}
+
+}  // namespace lbm

@@ -1,0 +1,160 @@
+// Internal declarations shared by the liblbm translation units.
+//
+// Device state layout (structure of arrays, x fastest, plane stride n = nx*ny):
+//   f[9][n]   D2Q9 populations as deviations f_i - w_i rho0 from the rest
+//             equilibrium (keeps FP32 resolution for small velocities), AA in place
+//   g[5][n]   D2Q5 populations, in place with the AA pattern
+//   fl[n]     liquid fraction f_l
+//   phi[n]    porosity, K[n] fully liquid permeability
+// Velocity order, Eq. (15) and (31): 0 rest, 1 E, 2 N, 3 W, 4 S, 5 NE, 6 NW, 7 SW, 8 SE.
+//
+// AA pattern.  Even steps read population i of node x from slot (x, i) and
+// write the post-collision value to slot (x, opp(i)) of the same node.  Odd
+// steps read population i from slot (x - e_i, opp(i)) and write it to slot
+// (x + e_i, i).  After an odd step every population sits in its own node's
+// slot ("natural" layout); after an even step population i of node x sits in
+// node x - e_i ("swapped" layout).  A flow link into a node without flow is
+// resolved on the odd step: the population reflected at the link is read
+// from (x, i) and written to (x, opp(i)).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+constexpr int TX = 32;       // fused kernel tile (threads x)
+constexpr int TY = 8;        // fused kernel tile (threads y)
+constexpr int TE = 32;       // enthalpy tile edge
+constexpr int RH = 8;        // enthalpy halo width
+constexpr int RE = TE + 2 * RH;
+constexpr int EB = 256;      // enthalpy kernels block size
+constexpr int RB = 256;      // reduction block size
+
+struct Dev {
+  int nx, ny;
+  long long n;               // nodes per plane
+  int per_x, per_y;          // periodic axes
+  int wall_l, wall_r, wall_b, wall_t;
+  int bc[4];
+  float Tbc[4];
+  int flow;                  // vartheta
+  float rho0, inv_rho0;
+  float nu_l, g_beta, T_ref;
+  float s_e, s_eps, s_q, s_nu;
+  float z_a, z_e, z_nu;      // 1/tau_T, zeta_e, zeta_nu
+  float varpi, csT2, sigma;
+  float conv;                // vartheta / (sigma c_sT^2)
+  float wt0, wt1;            // D2Q5 weights of Eq. (39)
+  float lat;                 // dT / (sigma St)
+  float T_s, T_l, dTt;
+  float f_act;
+  float scr_T;               // phase-change screen margin in temperature (1e-7 of the scale)
+  float scr_f;               // liquid fraction treated as 0 / 1 by the screen
+  int screen_off;            // 1: every enthalpy tile is solved every step
+  float H_over_dT;
+  int etx, ety;              // enthalpy tiles
+  int ntiles;                // etx * ety
+  int egrid;                 // CTAs of the enthalpy kernels (they walk the tile list)
+  int max_inner;
+  float tol;
+  float* f;
+  float* g;
+  float* fl;
+  const float* phi;
+  const float* K;
+  const float* wallTl;
+  int* flags;                // per enthalpy tile: 1 once listed this step (cleared by the commit)
+  int* list;                 // [2][ntiles]: tiles to solve, one list per step parity
+  int* lcount;               // [2]: entries in each list
+  int* ctr;                  // step counter (advanced by the fused kernel), stamps proc
+  int* proc;                 // per enthalpy tile: (stamp << 3) | bits, bit 0 solved, bit 1
+                             // some f_l changed, bit 2 some node's flow activity changed
+  float2* scr;               // per node of solved tiles: (f_l(n), f_l(n+1))
+  int* stats;                // [0] inner cap hit, [1] tiles solved, [2] max sweeps
+};
+
+__host__ __device__ inline int opp9(int i) {
+  return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
+}
+__host__ __device__ inline int opp5(int i) { return i == 0 ? 0 : ((i + 1) & 3) + 1; }
+
+__device__ __forceinline__ int ex9(int i) {
+  const int e[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  return e[i];
+}
+__device__ __forceinline__ int ey9(int i) {
+  const int e[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  return e[i];
+}
+
+// wrapped coordinate (any number of periods: an enthalpy halo can be wider
+// than a narrow periodic lattice), or -1 outside a non-periodic domain
+__device__ __forceinline__ int wrapx(const Dev& d, int x) {
+  if (x >= 0 && x < d.nx) return x;
+  if (!d.per_x) return -1;
+  x %= d.nx;
+  return x < 0 ? x + d.nx : x;
+}
+__device__ __forceinline__ int wrapy(const Dev& d, int y) {
+  if (y >= 0 && y < d.ny) return y;
+  if (!d.per_y) return -1;
+  y %= d.ny;
+  return y < 0 ? y + d.ny : y;
+}
+__device__ __forceinline__ bool is_wall(const Dev& d, int x, int y) {
+  return (d.wall_l && x == 0) || (d.wall_r && x == d.nx - 1) || (d.wall_b && y == 0) ||
+         (d.wall_t && y == d.ny - 1);
+}
+
+// Permeability and inertial coefficient at varphi = phi f_l, Eq. (6); the
+// input K is the fully liquid permeability (K_eff(f_l = 1) = K).
+__device__ __forceinline__ void porous(float fl, float phi, float K, float& nuK, float& cfK,
+                                       const Dev& d) {
+  float varphi = phi * fl;
+  float r = (1.f - phi) / (1.f - varphi);
+  float Keff = K * fl * fl * fl * r * r;   // +inf stays +inf
+  float cf = 1.75f * rsqrtf(175.f * varphi * varphi * varphi);
+  nuK = d.nu_l / Keff;                     // nu_l / K_eff
+  cfK = cf * rsqrtf(Keff);                 // C_F / sqrt(K_eff)
+}
+
+// Velocity from Eq. (26)-(28) and total force of Eq. (4)-(5) at one node.
+__device__ __forceinline__ void velocity(float jx, float jy, float T, float fl, float phi,
+                                         float K, const Dev& d, float& ux, float& uy,
+                                         float& Fx, float& Fy) {
+  float varphi = phi * fl;
+  float G = d.g_beta * (T - d.T_ref);
+  float nuK, cfK;
+  porous(fl, phi, K, nuK, cfK, d);
+  float vx = jx * d.inv_rho0;
+  float vy = jy * d.inv_rho0 + 0.5f * varphi * G;
+  float l0 = 0.5f * (1.f + 0.5f * varphi * nuK);
+  float l1 = 0.5f * varphi * cfK;
+  float vm = sqrtf(vx * vx + vy * vy);
+  float inv = 1.f / (l0 + sqrtf(l0 * l0 + l1 * vm));
+  ux = vx * inv;
+  uy = vy * inv;
+  float um = sqrtf(ux * ux + uy * uy);
+  float drag = varphi * (nuK + cfK * um);
+  Fx = -drag * ux;
+  Fy = -drag * uy + varphi * G;
+}
+
+// Kernel entry points (defined in the .cu files)
+void launch_fused(const Dev& d, int parity, cudaStream_t s);
+void launch_enthalpy_solve(const Dev& d, int parity, cudaStream_t s);
+void launch_enthalpy_commit(const Dev& d, int parity, cudaStream_t s);
+void enthalpy_setup();
+size_t enthalpy_solve_smem();
+void launch_init(const Dev& d, const float* T0, cudaStream_t s);
+void launch_macros(const Dev& d, int parity, float* ux, float* uy, float* rho, float* T,
+                   float* fl, cudaStream_t s);
+void launch_reduce(const Dev& d, int parity, double* partials, double* out, int nblocks,
+                   cudaStream_t s);
+int reduce_blocks(const Dev& d);
+void launch_get_state(const Dev& d, int parity, float* f, float* g, cudaStream_t s);
+void launch_set_state(const Dev& d, const float* f, const float* g, cudaStream_t s);
+void launch_validate(const Dev& d, const float* phi, const float* K, const float* T0,
+                     const float* fl0, int* bad, cudaStream_t s);
+
+}  // namespace lbm

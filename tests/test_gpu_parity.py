@@ -1,0 +1,211 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Error measure: for each field, max_x |gpu - oracle| / max_x |oracle| (a
+normwise relative error; pointwise relative error is undefined where a field
+crosses zero).  The bar is 1e-4 after 10,000 steps for u, T and f_l; short
+runs are held tighter, at 2e-5, since FP32 rounding (6e-8 per operation)
+accumulates roughly linearly in the step count before the fields' own
+dynamics damp it.
+"""
+import numpy as np
+import pytest
+
+import lbm_workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("ux", "uy", "T", "fl")
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1503_08406_gb300 as P
+    return P
+
+
+def _f32(w):
+    """Round the workload's fields to float32 in place: the CUDA path takes
+    float32 inputs, so the oracle must see the same numbers."""
+    for k in ("phi", "K", "T0", "fl0"):
+        setattr(w, k, getattr(w, k).astype(np.float32).astype(np.float64))
+    return w
+
+
+def _gpu(P, w, steps, **over):
+    lat = P.Lattice(w.nx, w.ny, **{**w.params, **over})
+    lat.set_fields(w.phi, w.K, w.T0, w.fl0, w.wall_T_left)
+    if steps:
+        lat.step(steps)
+    assert lat.status() == 0
+    return lat
+
+
+def _ora(oracle_mod, w, steps):
+    o = oracle_mod.Oracle(w.nx, w.ny, **w.params)
+    o.set_fields(w.phi, w.K, w.T0, w.fl0, w.wall_T_left)
+    if steps:
+        o.step(steps)
+    return o
+
+
+def _errors(got, exp, fields=FIELDS):
+    out = {}
+    for k in fields:
+        scale = np.abs(exp[k]).max()
+        if scale == 0:
+            out[k] = float(np.abs(got[k]).max())
+        else:
+            out[k] = float(np.abs(got[k].astype(np.float64) - exp[k]).max() / scale)
+    return out
+
+
+@pytest.mark.parametrize("steps", [1, 2, 3, 8, 51])
+def test_melted_cavity_matches_oracle(lbm, oracle_mod, steps):
+    """Ragged 40 x 40 cavity (tiles of 32): flow, moving front and walls, both
+    step parities."""
+    w = _f32(W.melted_cavity(40))
+    got = _gpu(lbm, w, steps).macros()
+    exp = _ora(oracle_mod, w, steps).macros()
+    err = _errors(got, exp, FIELDS + ("rho",))
+    assert max(err.values()) < 2e-5, err
+
+
+@pytest.mark.parametrize("shape,flow", [((45, 37), 1), ((33, 70), 0)])
+def test_ragged_periodic_box_matches_oracle(lbm, oracle_mod, shape, flow):
+    w = _f32(W.periodic_box(shape[0], ny=shape[1], flow=flow, T_s=-0.02 * (1 - flow),
+                            T_l=0.02 * (1 - flow)))
+    steps = 120
+    got = _gpu(lbm, w, steps).macros()
+    exp = _ora(oracle_mod, w, steps).macros()
+    fields = FIELDS if flow else ("T", "fl")
+    err = _errors(got, exp, fields)
+    assert max(err.values()) < 5e-5, err
+    # the flow mask really moved in this run
+    if flow:
+        assert ((exp["fl"] >= 1e-3) != (w.fl0 >= 1e-3)).sum() > 0
+
+
+def test_narrow_periodic_lattice(lbm, oracle_mod):
+    """ny = 3 periodic: the enthalpy halo (8 nodes) wraps the lattice several times."""
+    w = _f32(W.conduction_slab(nx=70, ny=3, alpha=0.05))
+    got = _gpu(lbm, w, 400).macros()
+    exp = _ora(oracle_mod, w, 400).macros()
+    err = _errors(got, exp, ("T", "fl"))
+    assert max(err.values()) < 2e-5, err
+
+
+def test_conduction_melting_config(lbm, oracle_mod):
+    """256 x 4 conduction melting, 20,000 steps: interface within 1% of the
+    one-phase Neumann solution (eta = 0.800601) and parity with the oracle."""
+    w = _f32(W.conduction_slab())
+    lat = _gpu(lbm, w, 20000)
+    got = lat.macros()
+    D = lat.derived()["alpha_e"]
+    fl = got["fl"].mean(axis=0)
+    xm = 0.5 * fl[0] + fl[1:].sum()
+    xa = 2 * 0.8006013628 * np.sqrt(D * 20000)
+    assert abs(xm / xa - 1) < 0.01, (xm, xa)
+    exp = _ora(oracle_mod, w, 20000).macros()
+    err = _errors(got, exp, ("T", "fl"))
+    assert max(err.values()) < 1e-4, err
+
+
+def test_parity_cavity_10000_steps(lbm, oracle_mod):
+    """The convection-melting cavity (256^2, Ra = 1e5, heterogeneous porosity
+    seed 1): u, T and f_l within 1e-4 of the FP64 oracle after 10,000 steps."""
+    w = _f32(W.parity_cavity(256))
+    steps = 10000
+    lat = _gpu(lbm, w, steps)
+    got = lat.macros()
+    o = _ora(oracle_mod, w, steps)
+    exp = o.macros()
+    err = _errors(got, exp)
+    assert max(err.values()) < 1e-4, err
+    r_g, r_o = lat.reduce(), o.reduce()
+    assert abs(r_g["melt_frac"] / r_o["melt_frac"] - 1) < 1e-4
+    assert abs(r_g["nu_hot"] / r_o["nu_hot"] - 1) < 1e-4
+
+
+def test_full_size_cavity_matches_oracle(lbm, oracle_mod):
+    """2048^2 (the benchmark size), left third melted so flow runs on a
+    third of the lattice: full-field comparison after 3 steps."""
+    w = _f32(W.melted_cavity(2048, seed=3, Ra=1e6, Da=1e-4))
+    got = _gpu(lbm, w, 3).macros()
+    exp = _ora(oracle_mod, w, 3).macros()
+    err = _errors(got, exp)
+    assert max(err.values()) < 2e-5, err
+
+
+def test_reductions_match_oracle(lbm, oracle_mod):
+    w = W.melted_cavity(64)
+    lat = _gpu(lbm, w, 100)
+    o = _ora(oracle_mod, w, 100)
+    rg, ro = lat.reduce(), o.reduce()
+    for k in ("mass", "enthalpy", "melt_frac", "nu_hot"):
+        assert abs(rg[k] - ro[k]) <= 1e-5 * abs(ro[k]), (k, rg[k], ro[k])
+
+
+def test_conservation_on_periodic_box(lbm):
+    """Closed domain: FP64 sums of the FP32 state conserve mass and enthalpy to
+    FP32 rounding."""
+    w = W.periodic_box(96)
+    lat = _gpu(lbm, w, 0)
+    r0 = lat.reduce()
+    lat.step(500)
+    r1 = lat.reduce()
+    assert abs(r1["mass"] / r0["mass"] - 1) < 1e-6
+    assert abs(r1["enthalpy"] - r0["enthalpy"]) / np.abs(w.T0).sum() < 1e-5
+    assert abs(r1["melt_frac"] - r0["melt_frac"]) > 1e-3
+
+
+def test_state_roundtrip_continues_exactly(lbm):
+    w = W.melted_cavity(64)
+    a = _gpu(lbm, w, 7)                      # odd count: swapped layout
+    f, g, fl = a.get_state()
+    a.step(6)
+    b = _gpu(lbm, w, 0)
+    b.set_state(f, g, fl)
+    b.step(6)
+    ma, mb = a.macros(), b.macros()
+    for k in ("ux", "uy", "rho", "T", "fl"):
+        np.testing.assert_array_equal(ma[k], mb[k])
+
+
+def test_host_and_device_pointer_paths_agree(lbm):
+    w = W.melted_cavity(48)
+    a = _gpu(lbm, w, 0)
+    b = lbm.Lattice(w.nx, w.ny, **w.params)
+    b.set_fields_host(w.phi, w.K, w.T0, w.fl0)
+    a.step(9)
+    b.step(9)
+    ma, mb = a.macros(), b.macros_host()
+    for k in ma:
+        np.testing.assert_array_equal(ma[k], mb[k])
+
+
+def test_inner_iteration_cap_is_reported(lbm):
+    w = W.melted_cavity(48)
+    lat = _gpu(lbm, w, 0, max_inner_iters=1)
+    lat.step(20)
+    assert lat.status() == -4          # LBM_ERR_NOT_CONVERGED, read once ...
+    assert lat.status() == 0           # ... and cleared
+
+
+def test_invalid_fields_rejected(lbm):
+    w = W.melted_cavity(32)
+    lat = lbm.Lattice(w.nx, w.ny, **w.params)
+    bad = w.phi.copy()
+    bad[3, 3] = 1.0          # flow needs porosity < 1
+    with pytest.raises(lbm.LBMError) as e:
+        lat.set_fields(bad, w.K, w.T0, w.fl0)
+    assert e.value.code == -1
+    with pytest.raises(lbm.LBMError):
+        lat.set_fields_host(w.phi, -w.K, w.T0, w.fl0)
+    fl = w.fl0.copy()
+    fl[0, 5] = 1.5
+    with pytest.raises(lbm.LBMError):
+        lat.set_fields(w.phi, w.K, w.T0, fl)
