@@ -157,6 +157,36 @@ int lbm_timing(lbm_ctx* c, int enable);
 int lbm_timing_read(lbm_ctx* c, double* fused_ms, double* solve_ms, double* commit_ms,
                     int64_t* steps_timed, int64_t* tiles_solved, int32_t* max_sweeps);
 
+/* Largest lattice height (rows) lbm_reduce_state_noalloc accepts. */
+#define LBM_NOALLOC_MAX_ROWS 16384
+
+/* The sums of lbm_reduce, computed from a checkpoint the caller holds, without
+ * allocating any memory. The paper has no counterpart: this is an operational
+ * entry point for callers that cannot allocate device memory, e.g. code that
+ * records work into a CUDA graph (cudaMalloc is not allowed while a stream is
+ * being captured), a framework whose allocator owns all device memory, or
+ * monitoring code inside a fixed memory budget. Unlike lbm_create, it needs no
+ * context and no workspace.
+ * Inputs (device pointers, natural layout, as lbm_get_state writes them):
+ * f[9][ny][nx] as deviations f_i - w_i rho0, g[5][ny][nx], fl and phi
+ * [ny][nx]; wall_T_left: NULL or ny device floats (the left-wall profile the
+ * context was given). p supplies nx, ny, bc, T_bc, sigma, St, dT, H, rho0.
+ * out (host, 4 doubles): total mass, total enthalpy, mean f_l, mean left-wall
+ * Nusselt number, as lbm_reduce defines them.
+ * Work is queued on `stream` (a cudaStream_t; NULL: legacy default stream) and
+ * the call synchronises it. Scratch is a fixed array of LBM_NOALLOC_MAX_ROWS x 6
+ * doubles (768 KB) in the library's device memory, which every GPU that loads
+ * the library keeps until the process exits; ny > LBM_NOALLOC_MAX_ROWS returns
+ * LBM_ERR_INVALID_ARG. The first call on a device looks up the array's device
+ * address (with that device current), so make it before any stream capture.
+ * All calls share the array: calls whose kernels may overlap on the GPU (on
+ * different streams without ordering) race and can return wrong sums.
+ * Returns LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_CUDA, LBM_ERR_NO_DEVICE or
+ * LBM_ERR_NONFINITE (a sum is not finite; out is still written). */
+int lbm_reduce_state_noalloc(const lbm_params* p, const float* f, const float* g, const float* fl,
+                             const float* phi, const float* wall_T_left, void* stream,
+                             double out[4]);
+
 /* Static text for an LBM_* code. */
 const char* lbm_error_string(int code);
 
