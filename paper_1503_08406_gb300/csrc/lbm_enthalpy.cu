@@ -22,9 +22,12 @@
 //   q = a (f - f_l(n)),
 // which has the same fixed point as the plain iteration (the map is monotone
 // with slope < 1).  Sweeps stop when no node moves by more than about four
-// float32 ulps: Gauss-Seidel from f_l(n) approaches the fixed point from one
-// side, so a looser stop would bias every step the same way, and a tighter
-// one can chase a one-ulp rounding cycle forever.  Nodes outside
+// float32 ulps of its value and of the terms it is computed from: Gauss-Seidel
+// from f_l(n) approaches the fixed point from one side, so a looser stop would
+// bias every step the same way, and a tighter one can chase a rounding cycle
+// forever (at the melting threshold v is a small difference of two larger
+// terms).  Two more sweeps follow the stop, which shrink what is left of the
+// one-sided error down to rounding noise.  Nodes outside
 // the halo keep f = f_l(n).  The tile's own results go to scratch as
 // (f_l(n), f_l(n+1)).
 //
@@ -96,7 +99,9 @@ __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
     __syncthreads();
     int it = 0;
     bool more = true;
-    for (; it < d.max_inner && more; ++it) {
+    int polish = 2;   // extra sweeps after the stop test passes
+    for (; it < d.max_inner && (more || polish > 0); ++it) {
+      if (!more) --polish;
       bool changed = false;
 #pragma unroll
       for (int color = 0; color < 2; ++color) {
@@ -111,15 +116,19 @@ __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
           if (lx < RE - 1) nb += sq[k + 1];
           if (ly > 0) nb += sq[k - RE];
           if (ly < RE - 1) nb += sq[k + RE];
-          float v = (sbase[k] - w1 * nb) * sinv[k];
+          const float b = sbase[k], inv = sinv[k];
+          float v = (b - w1 * nb) * inv;
           v = fminf(fmaxf(v, 0.f), 1.f);
-          if (fabsf(v - sf[k]) > 4.8e-7f * v + 1e-12f) changed = true;
+          // converged at about four ulps of v and of the terms that make it
+          const float tol = 4.8e-7f * (v + (fabsf(b) + w1 * fabsf(nb)) * inv);
+          if (fabsf(v - sf[k]) > tol) changed = true;
           sf[k] = v;
           sq[k] = a * (v - sfn[k]);
         }
         __syncthreads();
       }
-      more = __syncthreads_or(changed);
+      const bool c = __syncthreads_or(changed);
+      if (more) more = c;
     }
     bool fchg = false, achg = false;
     for (int k = tid; k < TE * TE; k += EB) {
@@ -136,7 +145,10 @@ __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
     }
     const int bits = 1 | (__syncthreads_or(fchg) ? 2 : 0) | (__syncthreads_or(achg) ? 4 : 0);
     if (tid == 0) {
-      if (more) atomicExch(&d.stats[0], 1);
+      if (more) {
+        atomicExch(&d.stats[0], 1);
+        d.stats[3] = tile;
+      }
       atomicAdd(&d.stats[1], 1);
       atomicMax(&d.stats[2], it);
       d.proc[tile] = (stamp << 3) | bits;

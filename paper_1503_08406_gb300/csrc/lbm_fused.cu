@@ -31,14 +31,6 @@
 
 namespace lbm {
 
-// f_l of node (gx, gy) for the activity / screen tests: -1 on walls and outside
-__device__ __forceinline__ float fl_at(const Dev& d, int gx, int gy) {
-  gx = wrapx(d, gx);
-  gy = wrapy(d, gy);
-  if (gx < 0 || gy < 0 || is_wall(d, gx, gy)) return -1.f;
-  return d.fl[gy * d.nx + gx];
-}
-
 // put enthalpy tile t on this step's work list (once)
 __device__ __forceinline__ void mark_tile(const Dev& d, int t, int par) {
   if (d.flags[t] == 0 && atomicExch(&d.flags[t], 1) == 0) {
@@ -57,33 +49,28 @@ __global__ void __launch_bounds__(TX* TY, 4) fused_step_kernel(Dev d) {
   if (y >= ny) return;  // whole warp: one warp is one row segment
   const bool inside = x < nx;
   const bool node = inside && !is_wall(d, x, y);
-
-  // f_l of the 3x3 neighbourhood: three row loads, x +- 1 by warp shuffles
-  const float c0 = node ? d.fl[y * nx + x] : -1.f;
-  const float cN = node ? fl_at(d, x, y + 1) : -1.f;
-  const float cS = node ? fl_at(d, x, y - 1) : -1.f;
-  float w0 = __shfl_up_sync(FULL, c0, 1), wN = __shfl_up_sync(FULL, cN, 1),
-        wS = __shfl_up_sync(FULL, cS, 1);
-  float e0 = __shfl_down_sync(FULL, c0, 1), eN = __shfl_down_sync(FULL, cN, 1),
-        eS = __shfl_down_sync(FULL, cS, 1);
   bool unsafe = false;
   if (node) {
-    if (lane == 0 || x == 0) {
-      w0 = fl_at(d, x - 1, y);
-      wN = fl_at(d, x - 1, y + 1);
-      wS = fl_at(d, x - 1, y - 1);
-    }
-    if (lane == TX - 1 || x == nx - 1) {
-      e0 = fl_at(d, x + 1, y);
-      eN = fl_at(d, x + 1, y + 1);
-      eS = fl_at(d, x + 1, y - 1);
-    }
     const int n = (int)d.n;
     const int s = y * nx + x;
+    // neighbours of a non-wall node are one step away: one wrap at most
     const int xm = (x == 0) ? nx - 1 : x - 1, xp = (x == nx - 1) ? 0 : x + 1;
     const int ym = (y == 0) ? ny - 1 : y - 1, yp = (y == ny - 1) ? 0 : y + 1;
     const int sE = y * nx + xp, sW = y * nx + xm;
     const int sN = yp * nx + x, sS = ym * nx + x;
+    const int nb[9] = {s, sE, sN, sW, sS, yp * nx + xp, yp * nx + xm, ym * nx + xm, ym * nx + xp};
+    // which neighbours are wall nodes
+    const bool cE = d.wall_r && xp == nx - 1, cW = d.wall_l && xm == 0;
+    const bool rN = d.wall_t && yp == ny - 1, rS = d.wall_b && ym == 0;
+    const bool wl[9] = {false, cE, rN, cW, rS, cE || rN, cW || rN, cW || rS, cE || rS};
+    // f_l of the 3x3 neighbourhood (L1 hits for all but the node's own row);
+    // -1 marks a wall
+    const float* FL = d.fl;
+    float fln[9];
+    fln[0] = FL[s];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) fln[i] = wl[i] ? -1.f : FL[nb[i]];
+    const float c0 = fln[0], e0 = fln[1], cN = fln[2], w0 = fln[3], cS = fln[4];
     const float flc = c0;
 
     // ---- thermal gather -------------------------------------------------
@@ -106,9 +93,9 @@ __global__ void __launch_bounds__(TX* TY, 4) fused_step_kernel(Dev d) {
       const float phi = d.phi[s], K = d.K[s];
       const float fa = d.f_act;
       // neighbour flow activity, directions 1..8 (E, N, W, S, NE, NW, SW, SE)
-      const bool act[9] = {true, e0 >= fa, cN >= fa, w0 >= fa, cS >= fa,
-                           eN >= fa, wN >= fa, wS >= fa, eS >= fa};
-      const int nb[9] = {s, sE, sN, sW, sS, yp * nx + xp, yp * nx + xm, ym * nx + xm, ym * nx + xp};
+      bool act[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) act[i] = fln[i] >= fa;
       float f[9];
       float* F = d.f;
       if (PAR == 0) {
@@ -120,7 +107,8 @@ __global__ void __launch_bounds__(TX* TY, 4) fused_step_kernel(Dev d) {
         for (int i = 1; i < 9; ++i) {
           const int o = opp9(i);
           // source node x - e_i is the neighbour in direction opp(i)
-          f[i] = act[o] ? F[o * n + nb[o]] : F[i * n + s];
+          const int off = act[o] ? o * n + nb[o] : i * n + s;
+          f[i] = F[off];
         }
       }
       // populations are stored as deviations from the rest equilibrium,
@@ -184,8 +172,9 @@ __global__ void __launch_bounds__(TX* TY, 4) fused_step_kernel(Dev d) {
         F[s] = fp[0];
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-          if (act[i]) F[i * n + nb[i]] = fp[i];
-          else F[opp9(i) * n + s] = fp[i];   // halfway bounce-back
+          // into a node without flow: halfway bounce-back into our own slot
+          const int off = act[i] ? i * n + nb[i] : opp9(i) * n + s;
+          F[off] = fp[i];
         }
       }
     }

@@ -70,7 +70,8 @@ struct Dev {
   int* proc;                 // per enthalpy tile: (stamp << 3) | bits, bit 0 solved, bit 1
                              // some f_l changed, bit 2 some node's flow activity changed
   float2* scr;               // per node of solved tiles: (f_l(n), f_l(n+1))
-  int* stats;                // [0] inner cap hit, [1] tiles solved, [2] max sweeps
+  int* stats;                // [0] inner cap hit, [1] tiles solved, [2] max sweeps,
+                             // [3] last tile that hit the cap
 };
 
 __host__ __device__ inline int opp9(int i) {
