@@ -125,7 +125,8 @@ __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
           sf[k] = v;
           sq[k] = a * (v - sfn[k]);
         }
-        __syncthreads();
+        // the second colour's barrier also collects the convergence vote
+        if (color == 0) __syncthreads();
       }
       const bool c = __syncthreads_or(changed);
       if (more) more = c;

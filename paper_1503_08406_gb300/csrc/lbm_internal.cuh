@@ -27,7 +27,7 @@ constexpr int TY = 8;        // fused kernel tile (threads y)
 constexpr int TE = 32;       // enthalpy tile edge
 constexpr int RH = 8;        // enthalpy halo width
 constexpr int RE = TE + 2 * RH;
-constexpr int EB = 256;      // enthalpy kernels block size
+constexpr int EB = 1024;     // enthalpy kernels block size (latency-bound: many warps per tile)
 constexpr int RB = 256;      // reduction block size
 
 struct Dev {
