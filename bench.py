@@ -277,6 +277,7 @@ def main(argv=None):
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
+        launches0 = lat.kernel_launches()
         e0.record(stream)
         lat.step(args.steps)
         e1.record(stream)
@@ -284,6 +285,7 @@ def main(argv=None):
         if dist is not None:
             dist.barrier()
     ms_local = e0.elapsed_time(e1)
+    launches = lat.kernel_launches() - launches0
     value, ms = aggregate(ms_local, cells, args.steps, world, dist, device)
     rc = lat.status()
 
@@ -295,6 +297,7 @@ def main(argv=None):
     lat.timing(False)
     nt = max(tr["steps"], 1)
     fused_us = tr["fused_ms"] / nt * 1e3
+    prep_us = tr["prep_ms"] / nt * 1e3
     solve_us = tr["solve_ms"] / nt * 1e3
     commit_us = tr["commit_ms"] / nt * 1e3
     peak, peak_kind = measured_peak()
@@ -342,11 +345,12 @@ def main(argv=None):
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "fused_step_kernel",
                          "algorithmic_bytes_per_launch": bytes_step,
-                         "fused_us_per_launch": fused_us, "solve_us_per_step": solve_us,
+                         "fused_us_per_launch": fused_us, "prep_us_per_step": prep_us,
+                         "solve_us_per_step": solve_us,
                          "commit_us_per_step": commit_us,
                          "tiles_solved_per_step": tr["tiles_solved"] / nt,
                          "max_inner_sweeps": tr["max_sweeps"]},
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": launches,
             "status": rc,
         }
         clocks = clk.summary()

@@ -125,6 +125,13 @@ int lbm_status(lbm_ctx* c);
 /* Steps taken since the last lbm_set_fields / lbm_set_state. */
 int64_t lbm_steps_done(const lbm_ctx* c);
 
+/* Kernels lbm_step has launched on this context (directly or in CUDA graphs),
+ * for accounting: a step is 4 kernels (fused, prep, enthalpy solve, enthalpy
+ * commit); inside a graph the fused pass of every step but the first is split
+ * in two (tiles away from the front, run concurrently with the previous step's
+ * enthalpy kernels, and tiles near it). */
+int64_t lbm_kernel_launches(const lbm_ctx* c);
+
 /* Macroscopic fields at the current time (each nx*ny floats, NULL to skip):
  * velocity from Eq. (26)-(28) (zero on nodes without flow), rho from
  * Eq. (24), T from Eq. (33) (wall nodes: the temperature the wall imposes),
@@ -147,15 +154,16 @@ int lbm_set_state(lbm_ctx* c, const float* f, const float* g, const float* fl, i
 
 /* Per-kernel timing with CUDA events on the context stream. enable != 0
  * starts recording (and clears earlier records and counters); while it is on,
- * lbm_step launches kernel by kernel (no CUDA graph) with events between the
- * kernels. lbm_timing_read synchronises and returns, over the recorded steps,
- * the summed milliseconds of the fused stream-collide kernel, of the enthalpy
- * solve kernel and of the enthalpy commit kernel, the number of steps timed,
- * the number of enthalpy tiles solved and the largest number of inner sweeps
- * one tile needed (NULL outputs are skipped). */
+ * lbm_step launches kernel by kernel (no CUDA graph, no overlap) with events
+ * between the kernels. lbm_timing_read synchronises and returns in ms[0..3]
+ * the summed milliseconds, over the recorded steps, of the fused
+ * stream-collide kernel, the prep kernel (step stamp, near-front map), the
+ * enthalpy solve kernel and the enthalpy commit kernel; also the number of
+ * steps timed, the number of enthalpy tiles solved and the largest number of
+ * inner sweeps one tile needed (NULL counters are skipped). */
 int lbm_timing(lbm_ctx* c, int enable);
-int lbm_timing_read(lbm_ctx* c, double* fused_ms, double* solve_ms, double* commit_ms,
-                    int64_t* steps_timed, int64_t* tiles_solved, int32_t* max_sweeps);
+int lbm_timing_read(lbm_ctx* c, double ms[4], int64_t* steps_timed, int64_t* tiles_solved,
+                    int32_t* max_sweeps);
 
 /* Largest lattice height (rows) lbm_reduce_state_noalloc accepts. */
 #define LBM_NOALLOC_MAX_ROWS 16384

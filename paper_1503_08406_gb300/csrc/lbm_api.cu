@@ -31,9 +31,12 @@ struct lbm_ctx {
   std::vector<cudaEvent_t> ev;   // per step: start, after fused, after enthalpy
   // CUDA graphs of GRAPH_STEPS and 2 steps starting at parity 0, captured on a
   // private stream and replayed on the context stream
-  cudaStream_t cap;
+  cudaStream_t cap, cap2;         // capture streams (the second one runs the far-tile fused pass)
+  cudaEvent_t ev_fork, ev_join;
   cudaGraphExec_t g_long, g_pair;
   bool graphs_off;
+  int64_t launches;                // kernels launched by lbm_step
+  int nl_long, nl_pair;            // kernels in each graph
 };
 
 static const int GRAPH_STEPS = 32;
@@ -109,8 +112,8 @@ int check_params(const lbm_params* p) {
 }
 
 struct Layout {
-  size_t f, g, fl, phi, K, wallTl, flags, list, lcount, ctr, proc, scr, stats, tmp, partials, sums,
-      bad, total;
+  size_t f, g, fl, phi, K, wallTl, flags, list, lcount, ctr, nearmap, proc, scr, stats, tmp,
+      partials, sums, bad, total;
 };
 
 size_t up(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -126,10 +129,11 @@ Layout layout_of(const lbm_params* p, int nred) {
   L.phi = o; o += up(n * sizeof(float));
   L.K = o; o += up(n * sizeof(float));
   L.wallTl = o; o += up((size_t)p->ny * sizeof(float));
-  L.flags = o; o += up(tiles * sizeof(int));
+  L.flags = o; o += up(2 * tiles * sizeof(int));
   L.list = o; o += up(2 * tiles * sizeof(int));
   L.lcount = o; o += up(2 * sizeof(int));
-  L.ctr = o; o += up(sizeof(int));
+  L.ctr = o; o += up(2 * sizeof(int));
+  L.nearmap = o; o += up(tiles * sizeof(int));
   L.proc = o; o += up(tiles * sizeof(int));
   L.scr = o; o += up(n * sizeof(float2));
   L.stats = o; o += up(4 * sizeof(int));
@@ -293,6 +297,7 @@ int lbm_create(const lbm_params* pin, void* stream, void* workspace, size_t work
   d.list = (int*)(b + L.list);
   d.lcount = (int*)(b + L.lcount);
   d.ctr = (int*)(b + L.ctr);
+  d.nearmap = (int*)(b + L.nearmap);
   d.proc = (int*)(b + L.proc);
   d.scr = (float2*)(b + L.scr);
   d.stats = (int*)(b + L.stats);
@@ -316,6 +321,9 @@ void lbm_destroy(lbm_ctx* c) {
   if (c->g_long) cudaGraphExecDestroy(c->g_long);
   if (c->g_pair) cudaGraphExecDestroy(c->g_pair);
   if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->cap2) cudaStreamDestroy(c->cap2);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   if (c->own_ws && c->ws) cudaFree(c->ws);
   delete c;
@@ -333,7 +341,7 @@ int64_t lbm_steps_done(const lbm_ctx* c) { return c ? c->steps : -1; }
 // never equal a later step's stamp
 static int reset_lists(lbm_ctx* c) {
   const Dev& d = c->d;
-  LBM_CUDA(cudaMemsetAsync(d.flags, 0, sizeof(int) * d.ntiles, c->stream));
+  LBM_CUDA(cudaMemsetAsync(d.flags, 0, 2 * sizeof(int) * d.ntiles, c->stream));
   LBM_CUDA(cudaMemsetAsync(d.lcount, 0, 2 * sizeof(int), c->stream));
   return LBM_OK;
 }
@@ -388,17 +396,28 @@ int lbm_set_fields(lbm_ctx* c, const float* phi, const float* K, const float* T0
   return LBM_OK;
 }
 
-static void launch_one_step(lbm_ctx* c, int parity, cudaStream_t st) {
-  lbm::launch_fused(c->d, parity, st);
-  lbm::launch_enthalpy_solve(c->d, parity, st);
-  lbm::launch_enthalpy_commit(c->d, parity, st);
-}
-
-// Capture `steps` (even) steps starting at parity 0 into an executable graph.
-static cudaGraphExec_t capture(lbm_ctx* c, int steps) {
-  if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+// Capture `steps` (even) steps starting at parity 0.  Inside the graph the
+// fused pass of step k+1 is split: its tiles away from step k's front run on a
+// second stream concurrently with step k's enthalpy solve and commit (which
+// touch only nodes within one tile of step k's listed tiles); the tiles near
+// the front run after the commit.
+static cudaGraphExec_t capture(lbm_ctx* c, int steps, int* launches) {
+  // the front kernels (main capture stream) outrank the far-tile fused pass
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  if (!c->cap && cudaStreamCreateWithPriority(&c->cap, cudaStreamNonBlocking, hi) != cudaSuccess) {
     cudaGetLastError();
     c->cap = nullptr;
+    return nullptr;
+  }
+  if (!c->cap2 && cudaStreamCreateWithPriority(&c->cap2, cudaStreamNonBlocking, lo) != cudaSuccess) {
+    cudaGetLastError();
+    c->cap2 = nullptr;
+    return nullptr;
+  }
+  if ((!c->ev_fork && cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess) ||
+      (!c->ev_join && cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
+    cudaGetLastError();
     return nullptr;
   }
   cudaGraph_t g = nullptr;
@@ -406,37 +425,66 @@ static cudaGraphExec_t capture(lbm_ctx* c, int steps) {
     cudaGetLastError();
     return nullptr;
   }
-  for (int k = 0; k < steps; ++k) launch_one_step(c, k & 1, c->cap);
+  int nl = 0;
+  for (int k = 0; k < steps; ++k) {
+    const int par = k & 1;
+    if (k == 0) {
+      lbm::launch_fused(c->d, par, 0, c->cap);
+      nl += 1;
+    } else {
+      lbm::launch_fused(c->d, par, 2, c->cap);       // near tiles, after the last commit
+      cudaStreamWaitEvent(c->cap, c->ev_join, 0);    // and the far tiles
+      nl += 1;
+    }
+    lbm::launch_prep(c->d, par, c->cap);
+    nl += 1;
+    if (k + 1 < steps) {
+      cudaEventRecord(c->ev_fork, c->cap);
+      cudaStreamWaitEvent(c->cap2, c->ev_fork, 0);
+      lbm::launch_fused(c->d, 1 - par, 1, c->cap2);  // next step, far tiles
+      cudaEventRecord(c->ev_join, c->cap2);
+      nl += 1;
+    }
+    lbm::launch_enthalpy_solve(c->d, par, c->cap);
+    lbm::launch_enthalpy_commit(c->d, par, c->cap);
+    nl += 2;
+  }
   if (cudaStreamEndCapture(c->cap, &g) != cudaSuccess || !g) {
     cudaGetLastError();
     return nullptr;
   }
   cudaGraphExec_t ex = nullptr;
-  if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+  if (cudaGraphInstantiateWithFlags(&ex, g, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) {
     cudaGetLastError();
     ex = nullptr;
   }
   cudaGraphDestroy(g);
+  *launches = nl;
   return ex;
 }
 
+static const int EV_PER_STEP = 5;
+
 static int step_direct(lbm_ctx* c) {
-  cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t e[EV_PER_STEP] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   if (c->timing) {
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < EV_PER_STEP; ++k) {
       if (cudaEventCreate(&e[k]) != cudaSuccess) return LBM_ERR_CUDA;
       c->ev.push_back(e[k]);
     }
     cudaEventRecord(e[0], c->stream);
   }
-  lbm::launch_fused(c->d, c->parity, c->stream);
+  lbm::launch_fused(c->d, c->parity, 0, c->stream);
   if (c->timing) cudaEventRecord(e[1], c->stream);
-  lbm::launch_enthalpy_solve(c->d, c->parity, c->stream);
+  lbm::launch_prep(c->d, c->parity, c->stream);
   if (c->timing) cudaEventRecord(e[2], c->stream);
-  lbm::launch_enthalpy_commit(c->d, c->parity, c->stream);
+  lbm::launch_enthalpy_solve(c->d, c->parity, c->stream);
   if (c->timing) cudaEventRecord(e[3], c->stream);
+  lbm::launch_enthalpy_commit(c->d, c->parity, c->stream);
+  if (c->timing) cudaEventRecord(e[4], c->stream);
   c->parity ^= 1;
   c->steps++;
+  c->launches += 4;
   return LBM_OK;
 }
 
@@ -448,17 +496,19 @@ int lbm_step(lbm_ctx* c, int64_t nsteps) {
     LBM_TRY(step_direct(c));
     --nsteps;
   }
-  if (nsteps >= GRAPH_STEPS && !c->g_long) c->g_long = capture(c, GRAPH_STEPS);
-  if (nsteps >= 2 && !c->g_pair) c->g_pair = capture(c, 2);
+  if (nsteps >= GRAPH_STEPS && !c->g_long) c->g_long = capture(c, GRAPH_STEPS, &c->nl_long);
+  if (nsteps >= 2 && !c->g_pair) c->g_pair = capture(c, 2, &c->nl_pair);
   while (nsteps >= GRAPH_STEPS && c->g_long) {
     LBM_CUDA(cudaGraphLaunch(c->g_long, c->stream));
     nsteps -= GRAPH_STEPS;
     c->steps += GRAPH_STEPS;
+    c->launches += c->nl_long;
   }
   while (nsteps >= 2 && c->g_pair) {
     LBM_CUDA(cudaGraphLaunch(c->g_pair, c->stream));
     nsteps -= 2;
     c->steps += 2;
+    c->launches += c->nl_pair;
   }
   while (nsteps > 0) {
     LBM_TRY(step_direct(c));
@@ -466,6 +516,8 @@ int lbm_step(lbm_ctx* c, int64_t nsteps) {
   }
   return cuda_err(cudaGetLastError());
 }
+
+int64_t lbm_kernel_launches(const lbm_ctx* c) { return c ? c->launches : -1; }
 
 int lbm_status(lbm_ctx* c) {
   if (!c) return LBM_ERR_INVALID_ARG;
@@ -584,26 +636,22 @@ int lbm_timing(lbm_ctx* c, int enable) {
   return LBM_OK;
 }
 
-int lbm_timing_read(lbm_ctx* c, double* fused_ms, double* solve_ms, double* commit_ms,
-                    int64_t* steps_timed, int64_t* tiles_solved, int32_t* max_sweeps) {
-  if (!c) return LBM_ERR_INVALID_ARG;
+int lbm_timing_read(lbm_ctx* c, double ms[4], int64_t* steps_timed, int64_t* tiles_solved,
+                    int32_t* max_sweeps) {
+  if (!c || !ms) return LBM_ERR_INVALID_ARG;
   LBM_CUDA(cudaStreamSynchronize(c->stream));
-  double tf = 0, ts = 0, tc = 0;
-  for (size_t k = 0; k + 3 < c->ev.size(); k += 4) {
-    float a = 0, b = 0, e = 0;
-    LBM_CUDA(cudaEventElapsedTime(&a, c->ev[k], c->ev[k + 1]));
-    LBM_CUDA(cudaEventElapsedTime(&b, c->ev[k + 1], c->ev[k + 2]));
-    LBM_CUDA(cudaEventElapsedTime(&e, c->ev[k + 2], c->ev[k + 3]));
-    tf += a;
-    ts += b;
-    tc += e;
+  double t[4] = {0, 0, 0, 0};
+  for (size_t k = 0; k + EV_PER_STEP - 1 < c->ev.size(); k += EV_PER_STEP) {
+    for (int j = 0; j < 4; ++j) {
+      float a = 0;
+      LBM_CUDA(cudaEventElapsedTime(&a, c->ev[k + j], c->ev[k + j + 1]));
+      t[j] += a;
+    }
   }
   int st[4];
   LBM_CUDA(cudaMemcpy(st, c->d.stats, sizeof st, cudaMemcpyDeviceToHost));
-  if (fused_ms) *fused_ms = tf;
-  if (solve_ms) *solve_ms = ts;
-  if (commit_ms) *commit_ms = tc;
-  if (steps_timed) *steps_timed = (int64_t)(c->ev.size() / 4);
+  memcpy(ms, t, sizeof t);
+  if (steps_timed) *steps_timed = (int64_t)(c->ev.size() / EV_PER_STEP);
   if (tiles_solved) *tiles_solved = st[1];
   if (max_sweeps) *max_sweeps = st[2];
   return LBM_OK;

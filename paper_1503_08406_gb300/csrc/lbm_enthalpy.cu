@@ -41,7 +41,7 @@ namespace lbm {
 
 constexpr int RC = RE / 2;  // nodes of one colour per region row
 
-__device__ __forceinline__ int stamp_of(const Dev& d) { return *d.ctr & 0x0FFFFFFF; }
+__device__ __forceinline__ int stamp_of(const Dev& d, int par) { return d.ctr[par] & 0x0FFFFFFF; }
 __device__ __forceinline__ bool solved(const Dev& d, int tile, int stamp) {
   return (d.proc[tile] >> 3) == stamp;
 }
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
   float* sf = sq + RE * RE;          // current iterate
   const int tid = threadIdx.x;
   const int cnt = d.lcount[PAR];
-  const int stamp = stamp_of(d);
+  const int stamp = stamp_of(d, PAR);
   const float w0 = d.wt0, w1 = d.wt1, Ts = d.T_s, dTt = d.dTt;
   for (int li = blockIdx.x; li < cnt; li += gridDim.x) {
     const int tile = d.list[PAR * d.ntiles + li];
@@ -167,17 +167,15 @@ __global__ void __launch_bounds__(EB) enthalpy_commit_kernel(Dev d) {
   __shared__ int links;
   const int tid = threadIdx.x;
   const int cnt = d.lcount[PAR];
-  const int stamp = stamp_of(d);
+  const int stamp = stamp_of(d, PAR);
   const int n = (int)d.n;
-  // the next step's list starts empty (nothing reads it during this step)
-  if (blockIdx.x == 0 && tid == 0) d.lcount[1 - PAR] = 0;
   for (int li = blockIdx.x; li < cnt; li += gridDim.x) {
     const int tile = d.list[PAR * d.ntiles + li];
     const int tx0 = tile % d.etx, ty0 = tile / d.etx;
     const int X0 = tx0 * TE, Y0 = ty0 * TE;
     const int pb = d.proc[tile] & 7;
     if (tid == 0) {
-      d.flags[tile] = 0;
+      d.flags[PAR * d.ntiles + tile] = 0;   // this step's fused pass is done with it
       // flow links need attention only around tiles where a node's activity changed
       int l = 0;
       if (d.flow && LAYOUT == 1) {

@@ -33,17 +33,24 @@ namespace lbm {
 
 // put enthalpy tile t on this step's work list (once)
 __device__ __forceinline__ void mark_tile(const Dev& d, int t, int par) {
-  if (d.flags[t] == 0 && atomicExch(&d.flags[t], 1) == 0) {
+  int* fl = d.flags + par * d.ntiles;
+  if (fl[t] == 0 && atomicExch(&fl[t], 1) == 0) {
     const int i = atomicAdd(&d.lcount[par], 1);
     d.list[par * d.ntiles + i] = t;
   }
 }
 
-template <int PAR, bool FLOW>
+template <int PAR, bool FLOW, int MODE>
 __global__ void __launch_bounds__(TX* TY, 4) fused_step_kernel(Dev d) {
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x;
-  if (blockIdx.x == 0 && blockIdx.y == 0 && lane == 0 && threadIdx.y == 0) atomicAdd(d.ctr, 1);
+  if (MODE != 0) {
+    // split step: this launch takes the CTAs on one side of the near map, whose
+    // entries carry the stamp of the step that marked them (the previous one)
+    const int prev = d.ctr[1 - PAR];
+    const bool nr = d.nearmap[((blockIdx.y * TY) / TE) * d.etx + (blockIdx.x * TX) / TE] == prev;
+    if ((MODE == 1) == nr) return;
+  }
   const int x = blockIdx.x * TX + lane, y = blockIdx.y * TY + threadIdx.y;
   const int nx = d.nx, ny = d.ny;
   if (y >= ny) return;  // whole warp: one warp is one row segment
@@ -88,16 +95,18 @@ __global__ void __launch_bounds__(TX* TY, 4) fused_step_kernel(Dev d) {
     const float T = g0 + g1 + g2 + g3 + g4;
 
     // ---- flow lattice ----------------------------------------------------
+    // All loads of the node are issued before any of them is used, so one
+    // memory round trip covers the step: the populations are read whether or
+    // not the node carries flow, and on odd steps both candidate slots of each
+    // direction (streamed from the neighbour, or reflected at the link) are
+    // read and chosen once the neighbours' activity is known.
     float ux = 0.f, uy = 0.f;
-    if (FLOW && flc >= d.f_act) {
-      const float phi = d.phi[s], K = d.K[s];
-      const float fa = d.f_act;
-      // neighbour flow activity, directions 1..8 (E, N, W, S, NE, NW, SW, SE)
-      bool act[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) act[i] = fln[i] >= fa;
-      float f[9];
-      float* F = d.f;
+    float f[9], fb[9];
+    float phi = 0.f, K = 1.f;
+    float* F = d.f;
+    if (FLOW) {
+      phi = d.phi[s];
+      K = d.K[s];
       if (PAR == 0) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = F[i * n + s];
@@ -106,10 +115,21 @@ __global__ void __launch_bounds__(TX* TY, 4) fused_step_kernel(Dev d) {
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
           const int o = opp9(i);
-          // source node x - e_i is the neighbour in direction opp(i)
-          const int off = act[o] ? o * n + nb[o] : i * n + s;
-          f[i] = F[off];
+          f[i] = F[o * n + nb[o]];   // from the source node x - e_i (direction opp(i) from x)
+          fb[i] = F[i * n + s];      // reflected at the link x - e_i | x
         }
+      }
+    }
+    if (FLOW && flc >= d.f_act) {
+      const float fa = d.f_act;
+      // neighbour flow activity, directions 1..8 (E, N, W, S, NE, NW, SW, SE)
+      bool act[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) act[i] = fln[i] >= fa;
+      if (PAR == 1) {
+#pragma unroll
+        for (int i = 1; i < 9; ++i)
+          if (!act[opp9(i)]) f[i] = fb[i];
       }
       // populations are stored as deviations from the rest equilibrium,
       // f_i - w_i rho0 (sum_i e_i w_i = 0, so j needs no correction)
@@ -252,15 +272,55 @@ __global__ void __launch_bounds__(TX* TY, 4) fused_step_kernel(Dev d) {
     mark_tile(d, (y / TE) * d.etx + (blockIdx.x * TX) / TE, PAR);
 }
 
-void launch_fused(const Dev& d, int parity, cudaStream_t s) {
-  dim3 block(TX, TY), grid((d.nx + TX - 1) / TX, (d.ny + TY - 1) / TY);
+template <int MODE>
+static void launch_mode(const Dev& d, int parity, dim3 grid, dim3 block, cudaStream_t s) {
   if (d.flow) {
-    if (parity == 0) fused_step_kernel<0, true><<<grid, block, 0, s>>>(d);
-    else fused_step_kernel<1, true><<<grid, block, 0, s>>>(d);
+    if (parity == 0) fused_step_kernel<0, true, MODE><<<grid, block, 0, s>>>(d);
+    else fused_step_kernel<1, true, MODE><<<grid, block, 0, s>>>(d);
   } else {
-    if (parity == 0) fused_step_kernel<0, false><<<grid, block, 0, s>>>(d);
-    else fused_step_kernel<1, false><<<grid, block, 0, s>>>(d);
+    if (parity == 0) fused_step_kernel<0, false, MODE><<<grid, block, 0, s>>>(d);
+    else fused_step_kernel<1, false, MODE><<<grid, block, 0, s>>>(d);
   }
+}
+
+void launch_fused(const Dev& d, int parity, int mode, cudaStream_t s) {
+  dim3 block(TX, TY), grid((d.nx + TX - 1) / TX, (d.ny + TY - 1) / TY);
+  if (mode == 0) launch_mode<0>(d, parity, grid, block, s);
+  else if (mode == 1) launch_mode<1>(d, parity, grid, block, s);
+  else launch_mode<2>(d, parity, grid, block, s);
+}
+
+// After a step's fused pass: stamp the step (ctr[par] = ctr[1-par] + 1), empty
+// the next step's list, and stamp the tiles within two tiles of this step's
+// listed tiles in the near map.  The enthalpy kernels of this step touch only
+// nodes within one tile of a listed tile, so the next step's fused pass may
+// run on the unstamped tiles concurrently with them.
+__global__ void __launch_bounds__(256) prep_kernel(Dev d, int par) {
+  const int stamp = d.ctr[1 - par] + 1;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gt == 0) {
+    d.ctr[par] = stamp;
+    d.lcount[1 - par] = 0;
+  }
+  const int cnt = d.lcount[par];
+  for (int j = gt; j < cnt * 25; j += gridDim.x * blockDim.x) {
+    const int t = d.list[par * d.ntiles + j / 25];
+    const int o = j % 25;
+    int tx = t % d.etx + (o % 5 - 2), ty = t / d.etx + (o / 5 - 2);
+    if (tx < 0 || tx >= d.etx) {
+      if (!d.per_x) continue;
+      tx = ((tx % d.etx) + d.etx) % d.etx;
+    }
+    if (ty < 0 || ty >= d.ety) {
+      if (!d.per_y) continue;
+      ty = ((ty % d.ety) + d.ety) % d.ety;
+    }
+    d.nearmap[ty * d.etx + tx] = stamp;
+  }
+}
+
+void launch_prep(const Dev& d, int parity, cudaStream_t s) {
+  prep_kernel<<<32, 256, 0, s>>>(d, parity);
 }
 
 }  // namespace lbm

@@ -117,12 +117,14 @@ def load():
         lib.lbm_status.argtypes = [_VP]
         lib.lbm_steps_done.argtypes = [_VP]
         lib.lbm_steps_done.restype = ctypes.c_int64
+        lib.lbm_kernel_launches.argtypes = [_VP]
+        lib.lbm_kernel_launches.restype = ctypes.c_int64
         lib.lbm_get_macros.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int]
         lib.lbm_reduce.argtypes = [_VP, _DP]
         lib.lbm_get_state.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int]
         lib.lbm_set_state.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int]
         lib.lbm_timing.argtypes = [_VP, ctypes.c_int]
-        lib.lbm_timing_read.argtypes = [_VP, _DP, _DP, _DP, ctypes.POINTER(ctypes.c_int64),
+        lib.lbm_timing_read.argtypes = [_VP, _DP, ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]
         lib.lbm_error_string.argtypes = [ctypes.c_int]
         lib.lbm_error_string.restype = ctypes.c_char_p
@@ -244,6 +246,9 @@ class Lattice:
     def steps_done(self) -> int:
         return int(self.lib.lbm_steps_done(self._h))
 
+    def kernel_launches(self) -> int:
+        return int(self.lib.lbm_kernel_launches(self._h))
+
     def derived(self) -> dict:
         out = (ctypes.c_double * 8)()
         _check(self.lib.lbm_derived(self._h, out), "lbm_derived")
@@ -297,10 +302,9 @@ class Lattice:
         _check(self.lib.lbm_timing(self._h, int(enable)), "lbm_timing")
 
     def timing_read(self) -> dict:
-        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        ms = (ctypes.c_double * 4)()
         n, t, m = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
-        _check(self.lib.lbm_timing_read(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
-                                        ctypes.byref(n), ctypes.byref(t), ctypes.byref(m)),
-               "lbm_timing_read")
-        return dict(fused_ms=a.value, solve_ms=b.value, commit_ms=c.value, steps=n.value,
+        _check(self.lib.lbm_timing_read(self._h, ms, ctypes.byref(n), ctypes.byref(t),
+                                        ctypes.byref(m)), "lbm_timing_read")
+        return dict(fused_ms=ms[0], prep_ms=ms[1], solve_ms=ms[2], commit_ms=ms[3], steps=n.value,
                     tiles_solved=t.value, max_sweeps=m.value)
