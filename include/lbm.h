@@ -126,9 +126,9 @@ int lbm_status(lbm_ctx* c);
 int64_t lbm_steps_done(const lbm_ctx* c);
 
 /* Kernels lbm_step has launched on this context (directly or in CUDA graphs),
- * for accounting: a step is 4 kernels (fused, prep, enthalpy solve, enthalpy
- * commit); inside a graph the fused pass of every step but the first is split
- * in two (tiles away from the front, run concurrently with the previous step's
+ * for accounting: a step is 3 kernels (fused, enthalpy solve, enthalpy commit);
+ * inside a graph the fused pass of every step but the first is split in two
+ * (tiles away from the front, run concurrently with the previous step's
  * enthalpy kernels, and tiles near it). */
 int64_t lbm_kernel_launches(const lbm_ctx* c);
 
@@ -157,8 +157,9 @@ int lbm_set_state(lbm_ctx* c, const float* f, const float* g, const float* fl, i
  * lbm_step launches kernel by kernel (no CUDA graph, no overlap) with events
  * between the kernels. lbm_timing_read synchronises and returns in ms[0..3]
  * the summed milliseconds, over the recorded steps, of the fused
- * stream-collide kernel, the prep kernel (step stamp, near-front map), the
- * enthalpy solve kernel and the enthalpy commit kernel; also the number of
+ * stream-collide kernel, of a preparation stage (zero in this version; kept
+ * for layout), of the enthalpy solve kernel and of the enthalpy commit
+ * kernel; also the number of
  * steps timed, the number of enthalpy tiles solved and the largest number of
  * inner sweeps one tile needed (NULL counters are skipped). */
 int lbm_timing(lbm_ctx* c, int enable);

@@ -133,7 +133,7 @@ Layout layout_of(const lbm_params* p, int nred) {
   L.list = o; o += up(2 * tiles * sizeof(int));
   L.lcount = o; o += up(2 * sizeof(int));
   L.ctr = o; o += up(2 * sizeof(int));
-  L.nearmap = o; o += up(tiles * sizeof(int));
+  L.nearmap = o; o += up(2 * tiles * sizeof(int));
   L.proc = o; o += up(tiles * sizeof(int));
   L.scr = o; o += up(n * sizeof(float2));
   L.stats = o; o += up(4 * sizeof(int));
@@ -397,10 +397,10 @@ int lbm_set_fields(lbm_ctx* c, const float* phi, const float* K, const float* T0
 }
 
 // Capture `steps` (even) steps starting at parity 0.  Inside the graph the
-// fused pass of step k+1 is split: its tiles away from step k's front run on a
-// second stream concurrently with step k's enthalpy solve and commit (which
-// touch only nodes within one tile of step k's listed tiles); the tiles near
-// the front run after the commit.
+// fused pass of step k+1 is split: its tiles more than one tile away from step
+// k's listed tiles run on a second stream concurrently with step k's enthalpy
+// solve and commit (which touch only nodes within eight nodes of a listed
+// tile); the tiles near the front run after the commit.
 static cudaGraphExec_t capture(lbm_ctx* c, int steps, int* launches) {
   // the front kernels (main capture stream) outrank the far-tile fused pass
   int lo = 0, hi = 0;
@@ -430,13 +430,10 @@ static cudaGraphExec_t capture(lbm_ctx* c, int steps, int* launches) {
     const int par = k & 1;
     if (k == 0) {
       lbm::launch_fused(c->d, par, 0, c->cap);
-      nl += 1;
     } else {
       lbm::launch_fused(c->d, par, 2, c->cap);       // near tiles, after the last commit
       cudaStreamWaitEvent(c->cap, c->ev_join, 0);    // and the far tiles
-      nl += 1;
     }
-    lbm::launch_prep(c->d, par, c->cap);
     nl += 1;
     if (k + 1 < steps) {
       cudaEventRecord(c->ev_fork, c->cap);
@@ -475,16 +472,17 @@ static int step_direct(lbm_ctx* c) {
     cudaEventRecord(e[0], c->stream);
   }
   lbm::launch_fused(c->d, c->parity, 0, c->stream);
-  if (c->timing) cudaEventRecord(e[1], c->stream);
-  lbm::launch_prep(c->d, c->parity, c->stream);
-  if (c->timing) cudaEventRecord(e[2], c->stream);
+  if (c->timing) {
+    cudaEventRecord(e[1], c->stream);
+    cudaEventRecord(e[2], c->stream);   // (no separate prep kernel: slot kept at zero)
+  }
   lbm::launch_enthalpy_solve(c->d, c->parity, c->stream);
   if (c->timing) cudaEventRecord(e[3], c->stream);
   lbm::launch_enthalpy_commit(c->d, c->parity, c->stream);
   if (c->timing) cudaEventRecord(e[4], c->stream);
   c->parity ^= 1;
   c->steps++;
-  c->launches += 4;
+  c->launches += 3;
   return LBM_OK;
 }
 

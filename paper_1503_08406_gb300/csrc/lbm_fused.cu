@@ -31,12 +31,30 @@
 
 namespace lbm {
 
-// put enthalpy tile t on this step's work list (once)
+// put enthalpy tile t on this step's work list (once), and stamp the tiles
+// within one tile of it in this parity's near map
 __device__ __forceinline__ void mark_tile(const Dev& d, int t, int par) {
   int* fl = d.flags + par * d.ntiles;
   if (fl[t] == 0 && atomicExch(&fl[t], 1) == 0) {
     const int i = atomicAdd(&d.lcount[par], 1);
     d.list[par * d.ntiles + i] = t;
+    const int stamp = d.ctr[1 - par] + 1;   // this step's stamp
+    const int tx = t % d.etx, ty = t / d.etx;
+    for (int dy = -1; dy <= 1; ++dy) {
+      int yy = ty + dy;
+      if (yy < 0 || yy >= d.ety) {
+        if (!d.per_y) continue;
+        yy = (yy + d.ety) % d.ety;
+      }
+      for (int dx = -1; dx <= 1; ++dx) {
+        int xx = tx + dx;
+        if (xx < 0 || xx >= d.etx) {
+          if (!d.per_x) continue;
+          xx = (xx + d.etx) % d.etx;
+        }
+        d.nearmap[par * d.ntiles + yy * d.etx + xx] = stamp;
+      }
+    }
   }
 }
 
@@ -44,11 +62,19 @@ template <int PAR, bool FLOW, int MODE>
 __global__ void __launch_bounds__(TX* TY, 4) fused_step_kernel(Dev d) {
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x;
+  if (MODE != 1 && blockIdx.x == 0 && blockIdx.y == 0 && lane == 0 && threadIdx.y == 0) {
+    // once per step (the near-tile launch runs after the previous step's
+    // enthalpy kernels, the last readers of the other list): stamp the step
+    // and empty the next step's list
+    d.ctr[PAR] = d.ctr[1 - PAR] + 1;
+    d.lcount[1 - PAR] = 0;
+  }
   if (MODE != 0) {
-    // split step: this launch takes the CTAs on one side of the near map, whose
-    // entries carry the stamp of the step that marked them (the previous one)
+    // split step: this launch takes the CTAs on one side of the previous
+    // step's near map (entries carry the stamp of the step that set them)
     const int prev = d.ctr[1 - PAR];
-    const bool nr = d.nearmap[((blockIdx.y * TY) / TE) * d.etx + (blockIdx.x * TX) / TE] == prev;
+    const int et = ((blockIdx.y * TY) / TE) * d.etx + (blockIdx.x * TX) / TE;
+    const bool nr = d.nearmap[(1 - PAR) * d.ntiles + et] == prev;
     if ((MODE == 1) == nr) return;
   }
   const int x = blockIdx.x * TX + lane, y = blockIdx.y * TY + threadIdx.y;
@@ -288,39 +314,6 @@ void launch_fused(const Dev& d, int parity, int mode, cudaStream_t s) {
   if (mode == 0) launch_mode<0>(d, parity, grid, block, s);
   else if (mode == 1) launch_mode<1>(d, parity, grid, block, s);
   else launch_mode<2>(d, parity, grid, block, s);
-}
-
-// After a step's fused pass: stamp the step (ctr[par] = ctr[1-par] + 1), empty
-// the next step's list, and stamp the tiles within two tiles of this step's
-// listed tiles in the near map.  The enthalpy kernels of this step touch only
-// nodes within one tile of a listed tile, so the next step's fused pass may
-// run on the unstamped tiles concurrently with them.
-__global__ void __launch_bounds__(256) prep_kernel(Dev d, int par) {
-  const int stamp = d.ctr[1 - par] + 1;
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gt == 0) {
-    d.ctr[par] = stamp;
-    d.lcount[1 - par] = 0;
-  }
-  const int cnt = d.lcount[par];
-  for (int j = gt; j < cnt * 25; j += gridDim.x * blockDim.x) {
-    const int t = d.list[par * d.ntiles + j / 25];
-    const int o = j % 25;
-    int tx = t % d.etx + (o % 5 - 2), ty = t / d.etx + (o / 5 - 2);
-    if (tx < 0 || tx >= d.etx) {
-      if (!d.per_x) continue;
-      tx = ((tx % d.etx) + d.etx) % d.etx;
-    }
-    if (ty < 0 || ty >= d.ety) {
-      if (!d.per_y) continue;
-      ty = ((ty % d.ety) + d.ety) % d.ety;
-    }
-    d.nearmap[ty * d.etx + tx] = stamp;
-  }
-}
-
-void launch_prep(const Dev& d, int parity, cudaStream_t s) {
-  prep_kernel<<<32, 256, 0, s>>>(d, parity);
 }
 
 }  // namespace lbm

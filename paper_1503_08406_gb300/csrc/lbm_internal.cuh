@@ -66,8 +66,9 @@ struct Dev {
   int* flags;                // [2][ntiles]: 1 once listed in that parity's step (cleared by the solve)
   int* list;                 // [2][ntiles]: tiles to solve, one list per step parity
   int* lcount;               // [2]: entries in each list
-  int* ctr;                  // [2]: step stamp per parity (the prep kernel sets ctr[p] = ctr[1-p] + 1)
-  int* nearmap;              // [ntiles]: stamp of the last step that had a listed tile within two tiles
+  int* ctr;                  // [2]: step stamp per parity (the fused pass sets ctr[p] = ctr[1-p] + 1)
+  int* nearmap;              // [2][ntiles]: per parity, the stamp of the step that listed a tile
+                             // within one tile of this one
   int* proc;                 // per enthalpy tile: (stamp << 3) | bits, bit 0 solved, bit 1
                              // some f_l changed, bit 2 some node's flow activity changed
   float2* scr;               // per node of solved tiles: (f_l(n), f_l(n+1))
@@ -146,7 +147,6 @@ __device__ __forceinline__ void velocity(float jx, float jy, float T, float fl, 
 // fused kernel over all tiles (mode 0), only tiles away from the last step's
 // front (mode 1) or only tiles near it (mode 2)
 void launch_fused(const Dev& d, int parity, int mode, cudaStream_t s);
-void launch_prep(const Dev& d, int parity, cudaStream_t s);
 void launch_enthalpy_solve(const Dev& d, int parity, cudaStream_t s);
 void launch_enthalpy_commit(const Dev& d, int parity, cudaStream_t s);
 void enthalpy_setup();
