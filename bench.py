@@ -297,7 +297,6 @@ def main(argv=None):
     lat.timing(False)
     nt = max(tr["steps"], 1)
     fused_us = tr["fused_ms"] / nt * 1e3
-    prep_us = tr["prep_ms"] / nt * 1e3
     solve_us = tr["solve_ms"] / nt * 1e3
     commit_us = tr["commit_ms"] / nt * 1e3
     peak, peak_kind = measured_peak()
@@ -343,9 +342,10 @@ def main(argv=None):
                        "l2": "state ~%d MB > 129 MB L2; no flush" % (31 * 4 * cells // 2**20)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "fused_step_kernel",
+                         "kernel": ("fused_tma_kernel" if lat.kernel_variant() == 2
+                                    else "fused_step_kernel"),
                          "algorithmic_bytes_per_launch": bytes_step,
-                         "fused_us_per_launch": fused_us, "prep_us_per_step": prep_us,
+                         "fused_us_per_launch": fused_us,
                          "solve_us_per_step": solve_us,
                          "commit_us_per_step": commit_us,
                          "tiles_solved_per_step": tr["tiles_solved"] / nt,

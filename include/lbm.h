@@ -42,6 +42,8 @@ extern "C" {
 #define LBM_ERR_NOT_CONVERGED (-4)/* an inner enthalpy iteration hit max_inner_iters */
 #define LBM_ERR_OOM (-5)          /* allocation failed or workspace too small */
 #define LBM_ERR_NO_DEVICE (-6)    /* no usable sm_103a device */
+#define LBM_ERR_TIMEOUT (-7)      /* a bounded device-side wait gave up (a bulk copy into shared
+                                     memory did not arrive); the results of that step are invalid */
 
 /* Boundary condition of one side. Periodic sides come in pairs (left/right,
  * bottom/top). A non-periodic side's outer row or column is a wall node:
@@ -74,6 +76,9 @@ typedef struct {
   double  inner_tol;              /* inner iteration stop: max |f(k+1) - f(k)| (FP32 path: >= 1e-6) */
   double  screen_tol;             /* phase-change screen margin in temperature: 0 = 1e-7 of the
                                      temperature scale; < 0 = no screen, every tile is solved */
+  int32_t kernel_variant;         /* stream-collide kernel: 0 auto (TMA-staged where the lattice
+                                     qualifies), 1 ordinary loads, 2 TMA-staged (falls back to 1
+                                     where the lattice does not qualify); results are identical */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -131,6 +136,11 @@ int64_t lbm_steps_done(const lbm_ctx* c);
  * (tiles away from the front, run concurrently with the previous step's
  * enthalpy kernels, and tiles near it). */
 int64_t lbm_kernel_launches(const lbm_ctx* c);
+
+/* Stream-collide kernel this context runs: 1 ordinary loads, 2 TMA-staged
+ * kernel (lattices walled on all four sides with nx a multiple of 4
+ * and nx >= 40, ny >= 10); -1 for NULL. */
+int lbm_kernel_variant(const lbm_ctx* c);
 
 /* Macroscopic fields at the current time (each nx*ny floats, NULL to skip):
  * velocity from Eq. (26)-(28) (zero on nodes without flow), rho from

@@ -37,6 +37,9 @@ struct lbm_ctx {
   bool graphs_off;
   int64_t launches;                // kernels launched by lbm_step
   int nl_long, nl_pair;            // kernels in each graph
+  lbm::TmaMaps maps;               // tensor maps of the TMA-staged fused kernel
+  bool use_tma;
+  const lbm::TmaMaps* tma() const { return use_tma ? &maps : nullptr; }
 };
 
 static const int GRAPH_STEPS = 32;
@@ -108,6 +111,7 @@ int check_params(const lbm_params* p) {
     if (p->bc[k] < LBM_BC_PERIODIC || p->bc[k] > LBM_BC_ADIABATIC) return LBM_ERR_INVALID_ARG;
   if ((p->bc[0] == LBM_BC_PERIODIC) != (p->bc[1] == LBM_BC_PERIODIC)) return LBM_ERR_INVALID_ARG;
   if ((p->bc[2] == LBM_BC_PERIODIC) != (p->bc[3] == LBM_BC_PERIODIC)) return LBM_ERR_INVALID_ARG;
+  if (p->kernel_variant < 0 || p->kernel_variant > 2) return LBM_ERR_INVALID_ARG;
   return LBM_OK;
 }
 
@@ -136,7 +140,7 @@ Layout layout_of(const lbm_params* p, int nred) {
   L.nearmap = o; o += up(2 * tiles * sizeof(int));
   L.proc = o; o += up(tiles * sizeof(int));
   L.scr = o; o += up(n * sizeof(float2));
-  L.stats = o; o += up(4 * sizeof(int));
+  L.stats = o; o += up(8 * sizeof(int));
   L.tmp = o; o += up(9 * n * sizeof(float));
   L.partials = o; o += up((size_t)nred * 6 * sizeof(double));
   L.sums = o; o += up(8 * sizeof(double));
@@ -175,6 +179,7 @@ const char* lbm_error_string(int code) {
     case LBM_ERR_NOT_CONVERGED: return "inner enthalpy iteration hit its cap";
     case LBM_ERR_OOM: return "out of device memory or workspace too small";
     case LBM_ERR_NO_DEVICE: return "no usable CUDA device";
+    case LBM_ERR_TIMEOUT: return "a bounded device-side wait timed out";
     default: return "unknown error";
   }
 }
@@ -305,6 +310,7 @@ int lbm_create(const lbm_params* pin, void* stream, void* workspace, size_t work
   c->partials = (double*)(b + L.partials);
   c->sums = (double*)(b + L.sums);
   c->bad = (int*)(b + L.bad);
+  c->use_tma = p.kernel_variant != 1 && lbm::tma_setup(d, &c->maps);
   if (cudaMemsetAsync(c->ws, 0, L.total, c->stream) != cudaSuccess ||
       cudaStreamSynchronize(c->stream) != cudaSuccess) {
     cudaGetLastError();
@@ -429,16 +435,16 @@ static cudaGraphExec_t capture(lbm_ctx* c, int steps, int* launches) {
   for (int k = 0; k < steps; ++k) {
     const int par = k & 1;
     if (k == 0) {
-      lbm::launch_fused(c->d, par, 0, c->cap);
+      lbm::launch_fused(c->d, c->tma(), par, 0, c->cap);
     } else {
-      lbm::launch_fused(c->d, par, 2, c->cap);       // near tiles, after the last commit
+      lbm::launch_fused(c->d, c->tma(), par, 2, c->cap);       // near tiles, after the last commit
       cudaStreamWaitEvent(c->cap, c->ev_join, 0);    // and the far tiles
     }
     nl += 1;
     if (k + 1 < steps) {
       cudaEventRecord(c->ev_fork, c->cap);
       cudaStreamWaitEvent(c->cap2, c->ev_fork, 0);
-      lbm::launch_fused(c->d, 1 - par, 1, c->cap2);  // next step, far tiles
+      lbm::launch_fused(c->d, c->tma(), 1 - par, 1, c->cap2);  // next step, far tiles
       cudaEventRecord(c->ev_join, c->cap2);
       nl += 1;
     }
@@ -471,7 +477,7 @@ static int step_direct(lbm_ctx* c) {
     }
     cudaEventRecord(e[0], c->stream);
   }
-  lbm::launch_fused(c->d, c->parity, 0, c->stream);
+  lbm::launch_fused(c->d, c->tma(), c->parity, 0, c->stream);
   if (c->timing) {
     cudaEventRecord(e[1], c->stream);
     cudaEventRecord(e[2], c->stream);   // (no separate prep kernel: slot kept at zero)
@@ -517,11 +523,14 @@ int lbm_step(lbm_ctx* c, int64_t nsteps) {
 
 int64_t lbm_kernel_launches(const lbm_ctx* c) { return c ? c->launches : -1; }
 
+int lbm_kernel_variant(const lbm_ctx* c) { return c ? (c->use_tma ? 2 : 1) : -1; }
+
 int lbm_status(lbm_ctx* c) {
   if (!c) return LBM_ERR_INVALID_ARG;
-  int st[4];
+  int st[8];
   LBM_CUDA(cudaMemcpyAsync(st, c->d.stats, sizeof st, cudaMemcpyDeviceToHost, c->stream));
   LBM_CUDA(cudaStreamSynchronize(c->stream));
+  if (st[4]) return LBM_ERR_TIMEOUT;
   if (st[0]) {
     LBM_CUDA(cudaMemsetAsync(c->d.stats, 0, sizeof(int), c->stream));
     LBM_CUDA(cudaStreamSynchronize(c->stream));

@@ -17,6 +17,7 @@
 // resolved on the odd step: the population reflected at the link is read
 // from (x, i) and written to (x, opp(i)).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -55,6 +56,7 @@ struct Dev {
   int etx, ety;              // enthalpy tiles
   int ntiles;                // etx * ety
   int egrid;                 // CTAs of the enthalpy kernels (they walk the tile list)
+  int tgrid, tgrid_far;      // CTAs of the TMA-staged fused kernel (far-tile pass: tgrid_far)
   int max_inner;
   float tol;
   float* f;
@@ -73,7 +75,14 @@ struct Dev {
                              // some f_l changed, bit 2 some node's flow activity changed
   float2* scr;               // per node of solved tiles: (f_l(n), f_l(n+1))
   int* stats;                // [0] inner cap hit, [1] tiles solved, [2] max sweeps,
-                             // [3] last tile that hit the cap
+                             // [3] last tile that hit the cap, [4] a bulk copy timed out
+};
+
+// Tensor maps of the TMA-staged fused kernel (passed as a __grid_constant__
+// kernel parameter): population boxes without halo for even steps and with a
+// 4-column, 1-row halo for odd steps, f_l with the halo, phi and K without.
+struct TmaMaps {
+  CUtensorMap f_even, f_odd, g_even, g_odd, fl, phi, K;
 };
 
 __host__ __device__ inline int opp9(int i) {
@@ -145,8 +154,10 @@ __device__ __forceinline__ void velocity(float jx, float jy, float T, float fl, 
 
 // Kernel entry points (defined in the .cu files)
 // fused kernel over all tiles (mode 0), only tiles away from the last step's
-// front (mode 1) or only tiles near it (mode 2)
-void launch_fused(const Dev& d, int parity, int mode, cudaStream_t s);
+// front (mode 1) or only tiles near it (mode 2); the TMA-staged kernel
+// when m is non-null (maps filled by tma_setup, which also sets tgrid)
+void launch_fused(const Dev& d, const TmaMaps* m, int parity, int mode, cudaStream_t s);
+bool tma_setup(Dev& d, TmaMaps* m);
 void launch_enthalpy_solve(const Dev& d, int parity, cudaStream_t s);
 void launch_enthalpy_commit(const Dev& d, int parity, cudaStream_t s);
 void enthalpy_setup();

@@ -52,6 +52,7 @@ class lbm_params(ctypes.Structure):
         ("f_act", ctypes.c_double),
         ("max_inner_iters", ctypes.c_int32), ("inner_tol", ctypes.c_double),
         ("screen_tol", ctypes.c_double),
+        ("kernel_variant", ctypes.c_int32),
     ]
 
 
@@ -60,7 +61,7 @@ PARAM_DEFAULTS = dict(
     flow=1, Ra=0.0, Pr=0.0, Ma=0.1, J=1.0, lambda_=1.0, sigma=1.0, St=1.0, dT=1.0, H=0.0,
     T_ref=0.0, T_s=0.0, T_l=0.0, varpi=-2.0, rho0=1.0, tau_nu=-1.0, tau_T=-1.0, g_beta=-1.0,
     s_e=0.0, s_eps=0.0, s_q=0.0, zeta_e=0.0, zeta_nu=0.0, f_act=1e-3,
-    max_inner_iters=1000, inner_tol=1e-6, screen_tol=0.0,
+    max_inner_iters=1000, inner_tol=1e-6, screen_tol=0.0, kernel_variant=0,
 )
 
 
@@ -119,6 +120,8 @@ def load():
         lib.lbm_steps_done.restype = ctypes.c_int64
         lib.lbm_kernel_launches.argtypes = [_VP]
         lib.lbm_kernel_launches.restype = ctypes.c_int64
+        lib.lbm_kernel_variant.argtypes = [_VP]
+        lib.lbm_kernel_variant.restype = ctypes.c_int
         lib.lbm_get_macros.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int]
         lib.lbm_reduce.argtypes = [_VP, _DP]
         lib.lbm_get_state.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int]
@@ -248,6 +251,10 @@ class Lattice:
 
     def kernel_launches(self) -> int:
         return int(self.lib.lbm_kernel_launches(self._h))
+
+    def kernel_variant(self) -> int:
+        """1: ordinary-load stream-collide kernel, 2: TMA-staged kernel."""
+        return int(self.lib.lbm_kernel_variant(self._h))
 
     def derived(self) -> dict:
         out = (ctypes.c_double * 8)()
