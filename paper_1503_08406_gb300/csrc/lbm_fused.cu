@@ -374,8 +374,9 @@ constexpr int WX = TX + 2 * HX;  // 40
 constexpr int WY = TY + 2 * HY;  // 10
 constexpr int TMA_MIN_CTAS = 4;  // resident CTAs per SM the register budget allows
 // target tiles per CTA (each CTA takes a run of tiles along x): short runs
-// when the pass has the GPU to itself, long ones for the far-tile pass that
-// shares it with the enthalpy kernels (measured on the 2048^2 cavity)
+// when the pass has the GPU to itself, long ones for the split far- and
+// near-tile passes that share it with the enthalpy kernels (measured on the
+// 2048^2 cavity)
 constexpr int TMA_TPC = 6;
 constexpr int TMA_TPC_FAR = 12;
 constexpr long long TMA_WAIT_NS = 200000000LL;   // bounded mbarrier waits: 0.2 s
@@ -612,7 +613,7 @@ static void launch_mode(const Dev& d, int parity, dim3 grid, dim3 block, cudaStr
 template <int PAR, bool FLOW, int MODE>
 static void launch_tma_one(const Dev& d, const TmaMaps& m, cudaStream_t s) {
   const size_t sm = TmaLayout<PAR>::SMEM;
-  fused_tma_kernel<PAR, FLOW, MODE><<<MODE == 1 ? d.tgrid_far : d.tgrid, dim3(TX, TY), sm, s>>>(d, m);
+  fused_tma_kernel<PAR, FLOW, MODE><<<MODE != 0 ? d.tgrid_far : d.tgrid, dim3(TX, TY), sm, s>>>(d, m);
 }
 
 template <int MODE>

@@ -56,7 +56,7 @@ struct Dev {
   int etx, ety;              // enthalpy tiles
   int ntiles;                // etx * ety
   int egrid;                 // CTAs of the enthalpy kernels (they walk the tile list)
-  int tgrid, tgrid_far;      // CTAs of the TMA-staged fused kernel (far-tile pass: tgrid_far)
+  int tgrid, tgrid_far;      // CTAs of the TMA-staged fused kernel (split passes: tgrid_far)
   int max_inner;
   float tol;
   float* f;
