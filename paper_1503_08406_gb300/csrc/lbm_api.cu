@@ -285,9 +285,10 @@ int lbm_create(const lbm_params* pin, void* stream, void* workspace, size_t work
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
       sms = 1;
-    // one 1024-thread CTA per SM walks the tile list: two working CTAs on one
-    // SM would halve both their speeds while other SMs idle
-    d.egrid = d.ntiles < sms ? d.ntiles : sms;
+    // the solve runs two 512-thread CTAs per SM (they fit beside the far-tile
+    // fused pass they overlap), the commit one 1024-thread CTA per SM
+    d.egrid = d.ntiles < 2 * sms ? d.ntiles : 2 * sms;
+    d.cgrid = d.ntiles < sms ? d.ntiles : sms;
     lbm::enthalpy_setup();
   }
   d.max_inner = p.max_inner_iters;

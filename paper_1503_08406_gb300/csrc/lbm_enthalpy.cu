@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
 }
 
 template <int PAR>
-__global__ void __launch_bounds__(EB) enthalpy_commit_kernel(Dev d) {
+__global__ void __launch_bounds__(CB) enthalpy_commit_kernel(Dev d) {
   constexpr int LAYOUT = 1 - PAR;
   constexpr int RW = TE + 2;              // tile plus a one-node ring
   __shared__ float2 sp[RW * RW];          // (f_l(n), f_l(n+1)); (-1,-1) on walls / outside
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(EB) enthalpy_commit_kernel(Dev d) {
         // old/new liquid fraction of the tile and its ring: scratch in tiles
         // solved this step, the (unchanged) stored value elsewhere
 #pragma unroll 2
-        for (int k = tid; k < RW * RW; k += EB) {
+        for (int k = tid; k < RW * RW; k += CB) {
           const int ly = k / RW, lx = k - ly * RW;
           const int gx = wrapx(d, X0 - 1 + lx), gy = wrapy(d, Y0 - 1 + ly);
           float2 v = make_float2(-1.f, -1.f);
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(EB) enthalpy_commit_kernel(Dev d) {
         __syncthreads();
       }
 #pragma unroll 4
-      for (int k = tid; k < TE * TE; k += EB) {
+      for (int k = tid; k < TE * TE; k += CB) {
         const int ly = k / TE, lx = k - ly * TE;
         const int x = X0 + lx, y = Y0 + ly;
         if (x >= d.nx || y >= d.ny || is_wall(d, x, y)) continue;
@@ -286,8 +286,8 @@ void launch_enthalpy_solve(const Dev& d, int parity, cudaStream_t s) {
 }
 
 void launch_enthalpy_commit(const Dev& d, int parity, cudaStream_t s) {
-  if (parity == 0) enthalpy_commit_kernel<0><<<d.egrid, EB, 0, s>>>(d);
-  else enthalpy_commit_kernel<1><<<d.egrid, EB, 0, s>>>(d);
+  if (parity == 0) enthalpy_commit_kernel<0><<<d.cgrid, CB, 0, s>>>(d);
+  else enthalpy_commit_kernel<1><<<d.cgrid, CB, 0, s>>>(d);
 }
 
 }  // namespace lbm

@@ -82,6 +82,37 @@ struct Geo {
   bool wl[9];
 };
 
+// lattices walled on all four sides: a non-wall node's neighbours never wrap
+__device__ __forceinline__ Geo node_geo_walled(const Dev& d, int x, int y) {
+  Geo q;
+  const int nx = d.nx;
+  q.s = y * nx + x;
+  q.xm = x - 1;
+  q.xp = x + 1;
+  q.ym = y - 1;
+  q.yp = y + 1;
+  q.nb[0] = q.s;
+  q.nb[1] = q.s + 1;
+  q.nb[2] = q.s + nx;
+  q.nb[3] = q.s - 1;
+  q.nb[4] = q.s - nx;
+  q.nb[5] = q.s + nx + 1;
+  q.nb[6] = q.s + nx - 1;
+  q.nb[7] = q.s - nx - 1;
+  q.nb[8] = q.s - nx + 1;
+  const bool cE = x == nx - 2, cW = x == 1, rN = y == d.ny - 2, rS = y == 1;
+  q.wl[0] = false;
+  q.wl[1] = cE;
+  q.wl[2] = rN;
+  q.wl[3] = cW;
+  q.wl[4] = rS;
+  q.wl[5] = cE || rN;
+  q.wl[6] = cW || rN;
+  q.wl[7] = cW || rS;
+  q.wl[8] = cE || rS;
+  return q;
+}
+
 __device__ __forceinline__ Geo node_geo(const Dev& d, int x, int y) {
   Geo q;
   const int nx = d.nx, ny = d.ny;
@@ -274,9 +305,9 @@ __device__ __forceinline__ bool node_update(const Dev& d, int x, int y, const Ge
   if (unsafe) {
     // list the enthalpy tiles holding this node's 3x3 neighbourhood (other
     // than its own, which the caller lists with one vote per warp)
-    const int cx = x / TE, cy = y / TE;
-    const int txs[3] = {q.xm / TE, cx, q.xp / TE};
-    const int tys[3] = {q.ym / TE, cy, q.yp / TE};
+    const int cx = (unsigned)x / TE, cy = (unsigned)y / TE;
+    const int txs[3] = {(int)((unsigned)q.xm / TE), cx, (int)((unsigned)q.xp / TE)};
+    const int tys[3] = {(int)((unsigned)q.ym / TE), cy, (int)((unsigned)q.yp / TE)};
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
@@ -515,6 +546,7 @@ __global__ void __launch_bounds__(TX* TY, TMA_MIN_CTAS)
   }
   __syncthreads();
   unsigned mask = *s_mask;   // tiles not yet processed (the same in every thread)
+  const int tx_b = tbeg % tiles_x, ty_b = tbeg / tiles_x;   // the run's first tile
   unsigned phases = 0u;      // bit k: phase parity the next wait on buffer k expects
   bool failed = false;
   int b = 0;
@@ -529,12 +561,16 @@ __global__ void __launch_bounds__(TX* TY, TMA_MIN_CTAS)
     }
     phases ^= 1u << b;
     const unsigned char* sb = smem + b * L::BYTES;
-    const int t = tbeg + k;
-    const int x0 = (t % tiles_x) * TX, y0 = (t / tiles_x) * TY;
+    int tx = tx_b + k, tyy = ty_b;
+    while (tx >= tiles_x) {   // a run may continue on the next row(s) of tiles
+      tx -= tiles_x;
+      ++tyy;
+    }
+    const int x0 = tx * TX, y0 = tyy * TY;
     const int x = x0 + lane, y = y0 + ty;
     bool unsafe = false;
     if (x < nx && y < ny && !is_wall(d, x, y)) {
-      const Geo q = node_geo(d, x, y);
+      const Geo q = node_geo_walled(d, x, y);
       const float* sF = reinterpret_cast<const float*>(sb + L::F_OFF);
       const float* sG = reinterpret_cast<const float*>(sb + L::G_OFF);
       const float* sFL = reinterpret_cast<const float*>(sb + L::FL_OFF);
@@ -578,7 +614,8 @@ __global__ void __launch_bounds__(TX* TY, TMA_MIN_CTAS)
       }
       unsafe = node_update<PAR, FLOW>(d, x, y, q, fln, g, f, fb, phi, K);
     }
-    if (__any_sync(FULL, unsafe) && lane == 0) mark_tile(d, (y / TE) * d.etx + x0 / TE, PAR);
+    if (__any_sync(FULL, unsafe) && lane == 0)
+      mark_tile(d, ((unsigned)y / TE) * d.etx + (unsigned)x0 / TE, PAR);
     // every thread is done with buffer b before it is refilled with the tile
     // after the next one
     __syncthreads();

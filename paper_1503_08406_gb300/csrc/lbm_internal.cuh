@@ -28,7 +28,8 @@ constexpr int TY = 8;        // fused kernel tile (threads y)
 constexpr int TE = 32;       // enthalpy tile edge
 constexpr int RH = 8;        // enthalpy halo width
 constexpr int RE = TE + 2 * RH;
-constexpr int EB = 1024;     // enthalpy kernels block size (latency-bound: many warps per tile)
+constexpr int EB = 512;      // enthalpy solve block size (two CTAs per SM fit beside the far-tile pass)
+constexpr int CB = 1024;     // enthalpy commit block size
 constexpr int RB = 256;      // reduction block size
 
 struct Dev {
@@ -55,7 +56,7 @@ struct Dev {
   float H_over_dT;
   int etx, ety;              // enthalpy tiles
   int ntiles;                // etx * ety
-  int egrid;                 // CTAs of the enthalpy kernels (they walk the tile list)
+  int egrid, cgrid;          // CTAs of the enthalpy solve / commit kernels (they walk the tile list)
   int tgrid, tgrid_far;      // CTAs of the TMA-staged fused kernel (split passes: tgrid_far)
   int max_inner;
   float tol;
