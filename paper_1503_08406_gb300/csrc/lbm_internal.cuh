@@ -57,7 +57,7 @@ struct Dev {
   int etx, ety;              // enthalpy tiles
   int ntiles;                // etx * ety
   int egrid, cgrid;          // CTAs of the enthalpy solve / commit kernels (they walk the tile list)
-  int tgrid, tgrid_far;      // CTAs of the TMA-staged fused kernel (split passes: tgrid_far)
+  int tgrid;                 // CTAs of the TMA-staged fused kernel
   int max_inner;
   float tol;
   float* f;
