@@ -86,7 +86,7 @@ def test_measured_peak_falls_back(tmp_path, monkeypatch):
 
 def test_traffic_record_matches_kernel_source():
     # the committed ncu record is only used while the fused kernel is unchanged
-    d = json.load(open(os.path.join(ROOT, "profiles", "fused_step_traffic.json")))
+    d = json.load(open(bench.TRAFFIC_FILE))
     t = bench.traffic_per_launch(2048)
     if d["kernel_hash"] == bench.kernel_hash():
         assert t == pytest.approx(d["dram_bytes_per_launch"])
