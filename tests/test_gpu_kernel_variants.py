@@ -46,7 +46,18 @@ def test_variant_selection(lbm):
     assert _run(P, wp, 0, 2).kernel_variant() == 1
 
 
+def _cropped(w, ny):
+    """The cavity's lower ny rows, walled again on top (row ny - 1 becomes the wall row)."""
+    import dataclasses
+    return dataclasses.replace(w, name="%s_%dx%d" % (w.name, w.nx, ny), ny=ny,
+                               phi=w.phi[:ny].copy(), K=w.K[:ny].copy(), T0=w.T0[:ny].copy(),
+                               fl0=w.fl0[:ny].copy())
+
+
 CASES = {
+    # ny - 1 = 96 is a multiple of the tile height: the top wall row is a tile row of its
+    # own, holding no node to update, whose wall slots only the row below writes
+    "cropped_cavity_100x97": (lambda: _cropped(W.melted_cavity(100), 97), 37, 1),
     # ragged in x (100 = 3 tiles + 4) and y (100 = 12 rows of tiles + 4)
     "melted_cavity_100": (lambda: W.melted_cavity(100), 57, 1),
     # no flow lattice, Dirichlet and adiabatic walls, a moving solidification front
