@@ -21,7 +21,8 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v
          "--expt-relaxed-constexpr"]
 # The fused stream-collide is issue-bound: its divisions and square roots use
 # the hardware-approximate forms (about 2 ulp; denormals are still kept).
-PER_FILE = {"lbm_fused.cu": ["-prec-div=false", "-prec-sqrt=false"]}
+APPROX = ["-prec-div=false", "-prec-sqrt=false"]
+PER_FILE = {"lbm_fused_f32.cu": APPROX, "lbm_fused_f16.cu": APPROX, "lbm_fused_bf16.cu": APPROX}
 
 
 def _nvcc() -> str:

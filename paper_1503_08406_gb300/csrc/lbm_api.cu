@@ -112,6 +112,7 @@ int check_params(const lbm_params* p) {
   if ((p->bc[0] == LBM_BC_PERIODIC) != (p->bc[1] == LBM_BC_PERIODIC)) return LBM_ERR_INVALID_ARG;
   if ((p->bc[2] == LBM_BC_PERIODIC) != (p->bc[3] == LBM_BC_PERIODIC)) return LBM_ERR_INVALID_ARG;
   if (p->kernel_variant < 0 || p->kernel_variant > 2) return LBM_ERR_INVALID_ARG;
+  if (p->storage < LBM_STORAGE_FP32 || p->storage > LBM_STORAGE_BF16) return LBM_ERR_INVALID_ARG;
   return LBM_OK;
 }
 
@@ -127,8 +128,9 @@ Layout layout_of(const lbm_params* p, int nred) {
   const size_t tiles = (size_t)((p->nx + lbm::TE - 1) / lbm::TE) * ((p->ny + lbm::TE - 1) / lbm::TE);
   Layout L;
   size_t o = 0;
-  L.f = o; o += up(9 * n * sizeof(float));
-  L.g = o; o += up(5 * n * sizeof(float));
+  const size_t es = p->storage == LBM_STORAGE_FP32 ? sizeof(float) : 2;   // bytes per population
+  L.f = o; o += up(9 * n * es);
+  L.g = o; o += up(5 * n * es);
   L.fl = o; o += up(n * sizeof(float));
   L.phi = o; o += up(n * sizeof(float));
   L.K = o; o += up(n * sizeof(float));
@@ -293,8 +295,13 @@ int lbm_create(const lbm_params* pin, void* stream, void* workspace, size_t work
   }
   d.max_inner = p.max_inner_iters;
   d.tol = (float)(p.inner_tol > 1e-6 ? p.inner_tol : 1e-6);
-  d.f = (float*)(b + L.f);
-  d.g = (float*)(b + L.g);
+  d.f = b + L.f;
+  d.g = b + L.g;
+  d.storage = p.storage;
+  // reference of the stored g deviations: the melting temperature (the middle
+  // of the mushy band), where the phase change needs the finest resolution of
+  // T; 0 for FP32 storage
+  d.g_ref = p.storage != LBM_STORAGE_FP32 ? (float)(0.5 * (p.T_s + p.T_l)) : 0.f;
   d.fl = (float*)(b + L.fl);
   d.phi = (const float*)(b + L.phi);
   d.K = (const float*)(b + L.K);

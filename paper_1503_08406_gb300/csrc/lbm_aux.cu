@@ -13,13 +13,14 @@ __device__ __forceinline__ bool flow_active(const Dev& d, int x, int y) {
 // g_i of non-wall node (x, y) in the given layout
 __device__ __forceinline__ void gather_g(const Dev& d, int x, int y, int layout, float g[5]) {
   const long long n = d.n, s = (long long)y * d.nx + x;
-  g[0] = d.g[s];
+  (void)n;
+  g[0] = ld_g(d, 0, s);
   for (int i = 1; i < 5; ++i) {
     if (layout == 0) {
-      g[i] = d.g[i * n + s];
+      g[i] = ld_g(d, i, s);
     } else {
       const int sx = wrapx(d, x - ex9(i)), sy = wrapy(d, y - ey9(i));
-      g[i] = d.g[opp5(i) * n + (long long)sy * d.nx + sx];
+      g[i] = ld_g(d, opp5(i), (long long)sy * d.nx + sx);
     }
   }
 }
@@ -28,14 +29,15 @@ __device__ __forceinline__ void gather_g(const Dev& d, int x, int y, int layout,
 __device__ __forceinline__ void gather_f(const Dev& d, int x, int y, int layout, float f[9]) {
   const long long n = d.n, s = (long long)y * d.nx + x;
   const bool self = flow_active(d, x, y);
-  f[0] = d.f[s];
+  (void)n;
+  f[0] = ld_f(d, 0, s);
   for (int i = 1; i < 9; ++i) {
     if (layout == 0 || !self) {
-      f[i] = d.f[i * n + s];
+      f[i] = ld_f(d, i, s);
     } else {
       const int sx = wrapx(d, x - ex9(i)), sy = wrapy(d, y - ey9(i));
-      if (flow_active(d, sx, sy)) f[i] = d.f[opp9(i) * n + (long long)sy * d.nx + sx];
-      else f[i] = d.f[i * n + s];
+      if (flow_active(d, sx, sy)) f[i] = ld_f(d, opp9(i), (long long)sy * d.nx + sx);
+      else f[i] = ld_f(d, i, s);
     }
   }
 }
@@ -81,13 +83,12 @@ __device__ float node_T(const Dev& d, int x, int y, int layout) {
 __global__ void init_kernel(Dev d, const float* T0) {
   const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= d.n) return;
-  const long long n = d.n;
   // f^eq(rho0, u = 0) = w_i rho0, Eq. (29); stored as the deviation f - w_i rho0 = 0
-  for (int i = 0; i < 9; ++i) d.f[i * n + s] = 0.f;
+  for (int i = 0; i < 9; ++i) st_f(d, i, s, 0.f);
   // g^eq(T0, u = 0), Eq. (39): w~_i T0
   const float T = T0[s];
-  d.g[s] = d.wt0 * T;
-  for (int i = 1; i < 5; ++i) d.g[i * n + s] = d.wt1 * T;
+  st_g(d, 0, s, d.wt0 * T);
+  for (int i = 1; i < 5; ++i) st_g(d, i, s, d.wt1 * T);
 }
 
 __global__ void macros_kernel(Dev d, int layout, float* ux, float* uy, float* rho, float* T,
@@ -98,7 +99,7 @@ __global__ void macros_kernel(Dev d, int layout, float* ux, float* uy, float* rh
   const float Tn = node_T(d, x, y, layout);
   float f[9];
   if (is_wall(d, x, y)) {
-    for (int i = 0; i < 9; ++i) f[i] = d.f[i * d.n + s];
+    for (int i = 0; i < 9; ++i) f[i] = ld_f(d, i, s);
   } else {
     gather_f(d, x, y, layout, f);
   }
@@ -175,8 +176,8 @@ __global__ void get_state_kernel(Dev d, int layout, float* f, float* g) {
   const long long n = d.n;
   float fv[9], gv[5];
   if (is_wall(d, x, y)) {
-    for (int i = 0; i < 9; ++i) fv[i] = d.f[i * n + s];
-    for (int i = 0; i < 5; ++i) gv[i] = d.g[i * n + s];
+    for (int i = 0; i < 9; ++i) fv[i] = ld_f(d, i, s);
+    for (int i = 0; i < 5; ++i) gv[i] = ld_g(d, i, s);
   } else {
     gather_f(d, x, y, layout, fv);
     gather_g(d, x, y, layout, gv);
@@ -192,9 +193,9 @@ __global__ void set_state_kernel(Dev d, const float* f, const float* g) {
   if (s >= d.n) return;
   const long long n = d.n;
   if (f)
-    for (int i = 0; i < 9; ++i) d.f[i * n + s] = f[i * n + s];
+    for (int i = 0; i < 9; ++i) st_f(d, i, s, f[i * n + s]);
   if (g)
-    for (int i = 0; i < 5; ++i) d.g[i * n + s] = g[i * n + s];
+    for (int i = 0; i < 5; ++i) st_g(d, i, s, g[i * n + s]);
 }
 
 __global__ void validate_kernel(Dev d, const float* phi, const float* K, const float* T0,

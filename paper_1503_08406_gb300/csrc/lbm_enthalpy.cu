@@ -58,11 +58,17 @@ __device__ __forceinline__ bool solved(const Dev& d, int tile, int stamp) {
 __device__ __forceinline__ float tstar(const Dev& d, int x, int y, int layout) {
   const int n = (int)d.n;
   const int s = y * d.nx + x;
-  if (layout == 0) return d.g[s] + d.g[n + s] + d.g[2 * n + s] + d.g[3 * n + s] + d.g[4 * n + s];
+  // the stored g deviations add up to T* - T_m (the weights sum to 1)
+  const float ref = d.storage ? d.g_ref : 0.f;
+  const void* G = d.g;
+  if (layout == 0)
+    return ld_pop(d, G, s) + ld_pop(d, G, n + s) + ld_pop(d, G, 2 * n + s) +
+           ld_pop(d, G, 3 * n + s) + ld_pop(d, G, 4 * n + s) + ref;
   const int xm = (x == 0) ? d.nx - 1 : x - 1, xp = (x == d.nx - 1) ? 0 : x + 1;
   const int ym = (y == 0) ? d.ny - 1 : y - 1, yp = (y == d.ny - 1) ? 0 : y + 1;
-  return d.g[s] + d.g[3 * n + y * d.nx + xm] + d.g[4 * n + ym * d.nx + x] +
-         d.g[1 * n + y * d.nx + xp] + d.g[2 * n + yp * d.nx + x];
+  return ld_pop(d, G, s) + ld_pop(d, G, 3 * n + y * d.nx + xm) +
+         ld_pop(d, G, 4 * n + ym * d.nx + x) + ld_pop(d, G, 1 * n + y * d.nx + xp) +
+         ld_pop(d, G, 2 * n + yp * d.nx + x) + ref;
 }
 
 template <int PAR>
@@ -253,7 +259,10 @@ __global__ void __launch_bounds__(CB) enthalpy_commit_kernel(Dev d) {
             if (rx < 0 || ry < 0 || is_wall(d, rx, ry)) continue;
             const float w = (i == 0) ? d.wt0 : d.wt1;
             const int slot = (LAYOUT == 1) ? opp5(i) * n + s : i * n + ry * d.nx + rx;
-            d.g[slot] += w * S0;
+            // (16-bit storage: rounded stochastically, or every small source
+            // would be lost to rounding in the same direction)
+            st_pop_round(d, d.g, slot, ld_pop(d, d.g, slot) + w * S0,
+                         mix32((unsigned)slot ^ mix32((unsigned)stamp)));
           }
         }
         if (lk) {
@@ -270,11 +279,11 @@ __global__ void __launch_bounds__(CB) enthalpy_commit_kernel(Dev d) {
             const bool own = (i == 1 || i == 2 || i == 5 || i == 6);
             if (!own && ssolved[q]) continue;
             const int px = wrapx(d, x + ex9(i)), py = wrapy(d, y + ey9(i));
-            float* A = d.f + i * n + (py * d.nx + px);
-            float* B = d.f + opp9(i) * n + s;
-            const float t = *A;
-            *A = *B;
-            *B = t;
+            const long long A = (long long)i * n + (py * d.nx + px);
+            const long long B = (long long)opp9(i) * n + s;
+            const float t = ld_pop(d, d.f, A);   // exact for every storage type
+            st_pop(d, d.f, A, ld_pop(d, d.f, B));
+            st_pop(d, d.f, B, t);
           }
         }
       }

@@ -3,7 +3,9 @@
 // Device state layout (structure of arrays, x fastest, plane stride n = nx*ny):
 //   f[9][n]   D2Q9 populations as deviations f_i - w_i rho0 from the rest
 //             equilibrium (keeps FP32 resolution for small velocities), AA in place
-//   g[5][n]   D2Q5 populations, in place with the AA pattern
+//   g[5][n]   D2Q5 populations, in place with the AA pattern; with 16-bit
+//             storage as deviations g_i - w~_i T_m (g_ref below)
+// Populations are FP32, FP16 or BF16 in memory (storage); all arithmetic is FP32.
 //   fl[n]     liquid fraction f_l
 //   phi[n]    porosity, K[n] fully liquid permeability
 // Velocity order, Eq. (15) and (31): 0 rest, 1 E, 2 N, 3 W, 4 S, 5 NE, 6 NW, 7 SW, 8 SE.
@@ -18,8 +20,12 @@
 // from (x, i) and written to (x, opp(i)).
 #pragma once
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 namespace lbm {
 
@@ -60,8 +66,10 @@ struct Dev {
   int tgrid;                 // CTAs of the TMA-staged fused kernel
   int max_inner;
   float tol;
-  float* f;
-  float* g;
+  void* f;                   // 9 planes of the storage type
+  void* g;                   // 5 planes of the storage type
+  int storage;               // 0 FP32, 1 FP16, 2 BF16
+  float g_ref;               // T_m of the stored g deviations (0 for FP32 storage)
   float* fl;
   const float* phi;
   const float* K;
@@ -85,6 +93,132 @@ struct Dev {
 struct TmaMaps {
   CUtensorMap f_even, f_odd, g_even, g_odd, fl, phi, K;
 };
+
+// conversions between a stored population and FP32 (round to nearest on store)
+template <typename S>
+struct Pop;
+template <>
+struct Pop<float> {
+  __device__ static __forceinline__ float ld(const float* p) { return *p; }
+  __device__ static __forceinline__ void st(float* p, float v) { *p = v; }
+};
+// FP16 holds populations scaled by 2^10: the small deviations of slow flow and
+// of temperatures near T_m then stay clear of FP16's subnormal range (below
+// 6.1e-5), where its resolution is absolute, not relative.  Limit: stored
+// magnitudes up to 65504 / 1024 = 64 (|T - T_m| up to ~100 with w~_0 = 0.6).
+constexpr float HALF_SCALE = 1024.f;
+template <>
+struct Pop<__half> {
+  __device__ static __forceinline__ float ld(const __half* p) {
+    return __half2float(*p) * (1.f / HALF_SCALE);
+  }
+  __device__ static __forceinline__ void st(__half* p, float v) {
+    *p = __float2half_rn(v * HALF_SCALE);
+  }
+};
+template <>
+struct Pop<__nv_bfloat16> {
+  __device__ static __forceinline__ float ld(const __nv_bfloat16* p) {
+    return __bfloat162float(*p);
+  }
+  __device__ static __forceinline__ void st(__nv_bfloat16* p, float v) {
+    *p = __float2bfloat16_rn(v);
+  }
+};
+
+// Stores into 16-bit storage round stochastically: up with probability
+// (v - down) / (up - down), so that the expected stored value is v.  Rounding
+// to nearest loses every increment below half an ulp, every time: the small
+// latent-heat sources and the slow relaxation of a nearly converged field
+// then drift systematically.  r: 32 random bits (the top 24 are used).
+constexpr bool STOCHASTIC_ROUNDING = true;
+
+// MurmurHash3's 32-bit finaliser (Appleby), used as a counter-based mixer
+__device__ __forceinline__ unsigned mix32(unsigned h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+// next random word of a per-node sequence (a linear congruential step; only
+// its high bits are used)
+__device__ __forceinline__ unsigned next_rand(unsigned& r) {
+  r = r * 1664525u + 1013904223u;
+  return r;
+}
+
+// Blackwell converts with stochastic rounding in hardware (cvt.rs): the value
+// goes into the low half of a packed pair (the high half, from 0, is dropped)
+constexpr bool HW_STOCHASTIC = true;
+
+template <typename S>
+__device__ __forceinline__ void st_round(S* p, float v, unsigned r) {
+  if constexpr (sizeof(S) == 4 || !STOCHASTIC_ROUNDING) {
+    Pop<S>::st(p, v);
+  } else if constexpr (HW_STOCHASTIC) {
+    unsigned pair;
+    if constexpr (std::is_same<S, __half>::value)
+      asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(pair) : "f"(0.f), "f"(v * HALF_SCALE), "r"(r));
+    else
+      asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(pair) : "f"(0.f), "f"(v), "r"(r));
+    *reinterpret_cast<unsigned short*>(p) = (unsigned short)(pair & 0xffffu);
+  } else {
+    S lo, hi;
+    float flo, fhi;
+    if constexpr (std::is_same<S, __half>::value) {
+      v *= HALF_SCALE;   // exact (a power of two)
+      lo = __float2half_rd(v);
+      hi = __float2half_ru(v);
+      flo = __half2float(lo);
+      fhi = __half2float(hi);
+    } else {
+      lo = __float2bfloat16_rd(v);
+      hi = __float2bfloat16_ru(v);
+      flo = __bfloat162float(lo);
+      fhi = __bfloat162float(hi);
+    }
+    const float u = (float)(r >> 8) * 5.9604645e-8f;   // uniform in [0, 1), 2^-24 steps
+    *p = (u * (fhi - flo) < v - flo) ? hi : lo;
+  }
+}
+
+// Population access with the storage chosen at run time (kernels off the
+// stream-collide path): element i of array base, as FP32.
+__device__ __forceinline__ float ld_pop(const Dev& d, const void* base, long long i) {
+  if (d.storage == 1) return Pop<__half>::ld(static_cast<const __half*>(base) + i);
+  if (d.storage == 2) return Pop<__nv_bfloat16>::ld(static_cast<const __nv_bfloat16*>(base) + i);
+  return static_cast<const float*>(base)[i];
+}
+__device__ __forceinline__ void st_pop(const Dev& d, void* base, long long i, float v) {
+  if (d.storage == 1) Pop<__half>::st(static_cast<__half*>(base) + i, v);
+  else if (d.storage == 2) Pop<__nv_bfloat16>::st(static_cast<__nv_bfloat16*>(base) + i, v);
+  else static_cast<float*>(base)[i] = v;
+}
+__device__ __forceinline__ void st_pop_round(const Dev& d, void* base, long long i, float v,
+                                             unsigned r) {
+  if (d.storage == 1) st_round(static_cast<__half*>(base) + i, v, r);
+  else if (d.storage == 2) st_round(static_cast<__nv_bfloat16*>(base) + i, v, r);
+  else static_cast<float*>(base)[i] = v;
+}
+// f plane k at node s (stored as deviations in every storage)
+__device__ __forceinline__ float ld_f(const Dev& d, int k, long long s) {
+  return ld_pop(d, d.f, k * d.n + s);
+}
+__device__ __forceinline__ void st_f(const Dev& d, int k, long long s, float v) {
+  st_pop(d, d.f, k * d.n + s, v);
+}
+// g plane k at node s: the stored deviation plus w~_k T_m for 16-bit storage
+__device__ __forceinline__ float ld_g(const Dev& d, int k, long long s) {
+  const float v = ld_pop(d, d.g, k * d.n + s);
+  if (d.storage == 0) return v;
+  return v + (k == 0 ? d.wt0 : d.wt1) * d.g_ref;
+}
+__device__ __forceinline__ void st_g(const Dev& d, int k, long long s, float v) {
+  if (d.storage != 0) v -= (k == 0 ? d.wt0 : d.wt1) * d.g_ref;
+  st_pop(d, d.g, k * d.n + s, v);
+}
 
 __host__ __device__ inline int opp9(int i) {
   return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);

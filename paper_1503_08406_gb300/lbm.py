@@ -53,6 +53,7 @@ class lbm_params(ctypes.Structure):
         ("max_inner_iters", ctypes.c_int32), ("inner_tol", ctypes.c_double),
         ("screen_tol", ctypes.c_double),
         ("kernel_variant", ctypes.c_int32),
+        ("storage", ctypes.c_int32),
     ]
 
 
@@ -61,8 +62,11 @@ PARAM_DEFAULTS = dict(
     flow=1, Ra=0.0, Pr=0.0, Ma=0.1, J=1.0, lambda_=1.0, sigma=1.0, St=1.0, dT=1.0, H=0.0,
     T_ref=0.0, T_s=0.0, T_l=0.0, varpi=-2.0, rho0=1.0, tau_nu=-1.0, tau_T=-1.0, g_beta=-1.0,
     s_e=0.0, s_eps=0.0, s_q=0.0, zeta_e=0.0, zeta_nu=0.0, f_act=1e-3,
-    max_inner_iters=1000, inner_tol=1e-6, screen_tol=0.0, kernel_variant=0,
+    max_inner_iters=1000, inner_tol=1e-6, screen_tol=0.0, kernel_variant=0, storage=0,
 )
+
+
+STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 
 
 def make_params(nx: int, ny: int, **kw) -> lbm_params:
@@ -77,6 +81,8 @@ def make_params(nx: int, ny: int, **kw) -> lbm_params:
         p.bc[i] = BC[b] if isinstance(b, str) else int(b)
     for i, t in enumerate(d.pop("T_bc")):
         p.T_bc[i] = float(t)
+    if isinstance(d.get("storage"), str):
+        d["storage"] = STORAGE[d["storage"]]
     for k, v in d.items():
         setattr(p, k, v)
     return p

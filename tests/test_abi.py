@@ -54,6 +54,8 @@ def test_invalid_parameters_rejected_without_device(P):
         dict(nx=2, ny=8),                                                   # too small
         dict(nx=8, ny=8, bc=("periodic", "dirichlet", "adiabatic", "adiabatic")),  # unpaired
         dict(nx=8, ny=8, bc=(7, 1, 2, 2)),                                  # unknown bc
+        dict(nx=8, ny=8, storage=3),                                        # unknown storage
+        dict(nx=8, ny=8, kernel_variant=3),                                 # unknown kernel
     ]
     for c in cases:
         nx, ny = c.pop("nx"), c.pop("ny")
@@ -81,7 +83,12 @@ def test_workspace_size_and_error_strings(P):
     n = 2048 * 2048
     # 14 population planes + f_l + phi + K + scratch pair + staging planes
     assert 25 * 4 * n <= nbytes < 32 * 4 * n
+    # 16-bit storage halves the 14 population planes
+    half = P.lbm_workspace_bytes(P.make_params(2048, 2048, Ra=1e6, Pr=1.0, storage="fp16"))
+    assert nbytes - half == 14 * 2 * n
+    assert P.lbm_workspace_bytes(P.make_params(2048, 2048, Ra=1e6, Pr=1.0, storage="bf16")) == half
     assert P.lbm_error_string(-4) == "inner enthalpy iteration hit its cap"
+    assert P.lbm_error_string(-7) == "a bounded device-side wait timed out"
     assert P.lbm_error_string(0) == "ok"
 
 
