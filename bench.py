@@ -44,6 +44,9 @@ FALLBACK_HBM_GBS = 6800.0
 # solid node: g 5 + 5, f_l read = 11 x 4 B; wall node: nothing
 BYTES_FLOW_NODE = 124
 BYTES_SOLID_NODE = 44
+# with 16-bit population storage: f 18 x 2 B, g 10 x 2 B + f_l, phi, K; solid g 10 x 2 + f_l
+BYTES_FLOW_NODE_16 = 68
+BYTES_SOLID_NODE_16 = 24
 KERNEL_SOURCES = ("paper_1503_08406_gb300/csrc/lbm_fused.cu",
                   "paper_1503_08406_gb300/csrc/lbm_internal.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_tma_traffic_heterogeneous_cavity_2048.json")
@@ -65,6 +68,8 @@ def parse(argv=None):
     ap.add_argument("--n", type=int, default=2048, help="lattice edge (default 2048)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--storage", choices=("fp32", "fp16", "bf16"), default="fp32",
+                    help="population storage (arithmetic is FP32 in every case)")
     return ap.parse_args(argv)
 
 
@@ -257,7 +262,7 @@ def main(argv=None):
 
     w = W.bench_cavity(args.n)
     cells = w.cells
-    lat = Lattice(w.nx, w.ny, **w.params)
+    lat = Lattice(w.nx, w.ny, **{**w.params, "storage": args.storage})
     lat.set_fields(w.phi, w.K, w.T0, w.fl0)
     stream = lat.stream
     lat.step(args.warmup)
@@ -267,7 +272,10 @@ def main(argv=None):
     fl_in = m0["fl"][interior, interior]
     n_flow = int((fl_in >= 1e-3).sum())
     n_solid = int(fl_in.size - n_flow)
-    bytes_step = BYTES_FLOW_NODE * n_flow + BYTES_SOLID_NODE * n_solid
+    if args.storage == "fp32":
+        bytes_step = BYTES_FLOW_NODE * n_flow + BYTES_SOLID_NODE * n_solid
+    else:
+        bytes_step = BYTES_FLOW_NODE_16 * n_flow + BYTES_SOLID_NODE_16 * n_solid
 
     # ---- headline: K steps, CUDA events on the context stream --------------
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -302,7 +310,8 @@ def main(argv=None):
     peak, peak_kind = measured_peak()
     achieved = bytes_step / (fused_us * 1e-6) / 1e9
     # the committed record covers the TMA-staged kernel only
-    traffic = traffic_per_launch(args.n) if lat.kernel_variant() == 2 else None
+    traffic = (traffic_per_launch(args.n)
+               if lat.kernel_variant() == 2 and args.storage == "fp32" else None)
 
     # ---- end to end through the C ABI with pinned host buffers --------------
     e2e = None
@@ -311,7 +320,7 @@ def main(argv=None):
         host_in = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory()
                    for a in (w.phi, w.K, w.T0, w.fl0)]
         host_out = [torch.empty((w.ny, w.nx), dtype=torch.float32).pin_memory() for _ in range(5)]
-        lat2 = Lattice(w.nx, w.ny, **w.params)
+        lat2 = Lattice(w.nx, w.ny, **{**w.params, "storage": args.storage})
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         rc_in = lat2.lib.lbm_set_fields(lat2._h, *[t.data_ptr() for t in host_in], None, 0)
@@ -339,12 +348,15 @@ def main(argv=None):
             "config": {"workload": w.name, "lattice": [w.nx, w.ny], "Ra": 1e6, "Da_mean": 1e-4,
                        "porosity": "clip(0.45+0.15 g, 0.3, 0.6), g smoothed (16 cells), seed 3",
                        "flow_nodes": n_flow, "solid_nodes": n_solid,
+                       "population_storage": args.storage,
                        "parallelism": f"replicas x{world}",
-                       "l2": "state ~%d MB > 129 MB L2; no flush" % (31 * 4 * cells // 2**20)},
+                       # state per node: 14 populations + f_l, phi, K (FP32)
+                       "l2": "state ~%d MB > 129 MB L2; no flush" % (
+                           (14 * (4 if args.storage == "fp32" else 2) + 12) * cells // 2**20)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": ("fused_tma_kernel" if lat.kernel_variant() == 2
-                                    else "fused_step_kernel"),
+                                    else "fused_step_kernel") + "<%s>" % args.storage,
                          "algorithmic_bytes_per_launch": bytes_step,
                          "fused_us_per_launch": fused_us,
                          "solve_us_per_step": solve_us,
