@@ -148,9 +148,43 @@ int64_t lbm_steps_done(const lbm_ctx* c);
 int64_t lbm_kernel_launches(const lbm_ctx* c);
 
 /* Stream-collide kernel this context runs: 1 ordinary loads, 2 TMA-staged
- * kernel (lattices walled on all four sides with nx a multiple of 4
- * and nx >= 40, ny >= 10); -1 for NULL. */
+ * kernel (lattices walled on all four sides whose rows are a multiple of 16
+ * bytes, i.e. nx a multiple of 4 (FP32) or 8 (16-bit storage), nx >= 40
+ * (48 with 16-bit storage), ny >= 10); -1 for NULL. */
 int lbm_kernel_variant(const lbm_ctx* c);
+
+/* Autotuner (survey item f2): times `trial_steps` (even, >= 2) graph-replayed
+ * steps of this context for each stream-collide configuration -- the ordinary-
+ * load kernel and, where the lattice qualifies, the TMA-staged kernel with
+ * 2, 3, 4, 5, 6 or 8 tiles of 32x8 nodes per CTA -- and keeps the fastest.
+ * Every configuration computes the same step (bit for bit), so the trial steps
+ * are real steps of the run: the context advances by 2 trial_steps per
+ * configuration (one untimed run that captures the graphs, one timed), plus
+ * one step first if its step count is odd.  Synchronises.  *variant and *tiles_per_cta (either may be
+ * NULL) receive the choice (tiles_per_cta 0 for the ordinary-load kernel). */
+int lbm_autotune(lbm_ctx* c, int trial_steps, int32_t* variant, int32_t* tiles_per_cta);
+
+/* Batches (survey item f2).  A batch advances several contexts together: each
+ * lbm_batch_step replays one CUDA graph holding LBM_BATCH_STEPS steps of every
+ * context, each context's kernels on its own branch, so small lattices fill the
+ * GPU together instead of one after another.  The contexts stay owned by the
+ * caller, must outlive the batch, and must have the same step count modulo 2
+ * when lbm_batch_step is called; each keeps its own parameters, size and
+ * kernel configuration (tune them before lbm_batch_create).  The results of
+ * every context are bit for bit those of stepping it alone. */
+#define LBM_BATCH_STEPS 32
+typedef struct lbm_batch lbm_batch;
+/* stream: where lbm_batch_step launches (NULL: the default stream).  The graph
+ * is captured on the first lbm_batch_step.  LBM_ERR_INVALID_ARG for count < 1,
+ * NULL or repeated contexts. */
+int lbm_batch_create(lbm_ctx* const* ctxs, int count, void* stream, lbm_batch** out);
+/* Advance every context by nsteps (>= 0): whole graphs of LBM_BATCH_STEPS
+ * steps, the rest through each context's own lbm_step.  Ordered after work
+ * already queued on each context's stream, and before work queued there later.
+ * Asynchronous; LBM_ERR_INVALID_ARG if a context has timing enabled or the
+ * contexts' step counts differ in parity. */
+int lbm_batch_step(lbm_batch* b, int64_t nsteps);
+void lbm_batch_destroy(lbm_batch* b);
 
 /* Macroscopic fields at the current time (each nx*ny floats, NULL to skip):
  * velocity from Eq. (26)-(28) (zero on nodes without flow), rho from

@@ -230,3 +230,26 @@ def bench_cavity(n: int = 2048, seed: int = 3, melted: float = 0.875, Ra: float 
     w.name = "heterogeneous_cavity_%d_seed%d_melted%g" % (n, seed, melted)
     w.meta.update(melted=melted)
     return w
+
+
+BATCH_SIDES = (64, 96, 128, 192, 256, 384, 512)
+
+
+def batched_cavities(count: int = 64, seed: int = 4) -> list:
+    """Uneven convection-melting cavities for the batched runs: side drawn
+    uniformly from BATCH_SIDES, Ra log-uniform in [1e4, 1e7], Da log-uniform
+    in [1e-5, 1e-2], porosity uniform in [0.3, 0.9], Pr = 1, St uniform in
+    [0.1, 1] (one seeded generator, drawn in that order per cavity)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice(BATCH_SIDES))
+        Ra = float(10.0 ** rng.uniform(4.0, 7.0))
+        Da = float(10.0 ** rng.uniform(-5.0, -2.0))
+        eps = float(rng.uniform(0.3, 0.9))
+        St = float(rng.uniform(0.1, 1.0))
+        w = convection_cavity(n, phi=eps, Da=Da, Ra=Ra, St=St)
+        w.name = "batched_%02d_n%d" % (i, n)
+        w.meta.update(Ra=Ra, Da=Da, phi=eps, St=St, seed=seed)
+        out.append(w)
+    return out

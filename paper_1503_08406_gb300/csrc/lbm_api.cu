@@ -39,6 +39,8 @@ struct lbm_ctx {
   int nl_long, nl_pair;            // kernels in each graph
   lbm::TmaMaps maps;               // tensor maps of the TMA-staged fused kernel
   bool use_tma;
+  bool tma_ok;                     // the lattice qualifies for the TMA-staged kernel
+  int tpc;                         // its tiles per CTA
   const lbm::TmaMaps* tma() const { return use_tma ? &maps : nullptr; }
 };
 
@@ -318,7 +320,9 @@ int lbm_create(const lbm_params* pin, void* stream, void* workspace, size_t work
   c->partials = (double*)(b + L.partials);
   c->sums = (double*)(b + L.sums);
   c->bad = (int*)(b + L.bad);
-  c->use_tma = p.kernel_variant != 1 && lbm::tma_setup(d, &c->maps);
+  c->tma_ok = lbm::tma_setup(d, &c->maps);
+  c->use_tma = p.kernel_variant != 1 && c->tma_ok;
+  c->tpc = lbm::TMA_TPC;
   if (cudaMemsetAsync(c->ws, 0, L.total, c->stream) != cudaSuccess ||
       cudaStreamSynchronize(c->stream) != cudaSuccess) {
     cudaGetLastError();
@@ -410,35 +414,37 @@ int lbm_set_fields(lbm_ctx* c, const float* phi, const float* K, const float* T0
   return LBM_OK;
 }
 
-// Capture `steps` (even) steps starting at parity 0.  Inside the graph the
-// fused pass of step k+1 is split: its tiles more than one tile away from step
-// k's listed tiles run on a second stream concurrently with step k's enthalpy
-// solve and commit (which touch only nodes within eight nodes of a listed
-// tile); the tiles near the front run after the commit.
-static cudaGraphExec_t capture(lbm_ctx* c, int steps, int* launches) {
+// Streams and events the graph captures use (created on first need).
+static bool capture_streams(lbm_ctx* c) {
   // the front kernels (main capture stream) outrank the far-tile fused pass
   int lo = 0, hi = 0;
   cudaDeviceGetStreamPriorityRange(&lo, &hi);
   if (!c->cap && cudaStreamCreateWithPriority(&c->cap, cudaStreamNonBlocking, hi) != cudaSuccess) {
     cudaGetLastError();
     c->cap = nullptr;
-    return nullptr;
+    return false;
   }
   if (!c->cap2 && cudaStreamCreateWithPriority(&c->cap2, cudaStreamNonBlocking, lo) != cudaSuccess) {
     cudaGetLastError();
     c->cap2 = nullptr;
-    return nullptr;
+    return false;
   }
   if ((!c->ev_fork && cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess) ||
       (!c->ev_join && cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
     cudaGetLastError();
-    return nullptr;
+    return false;
   }
-  cudaGraph_t g = nullptr;
-  if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
+  return true;
+}
+
+// Record `steps` (even) steps starting at parity 0 on c->cap, which is being
+// captured (alone, or as one branch of a batch capture); returns the number of
+// kernels.  The fused pass of step k+1 is split: its tiles more than one tile
+// away from step k's listed tiles run on a second stream concurrently with step
+// k's enthalpy solve and commit (which touch only nodes within eight nodes of a
+// listed tile); the tiles near the front run after the commit.  Everything
+// forked onto the second stream joins back before the last kernel.
+static int capture_body(lbm_ctx* c, int steps) {
   int nl = 0;
   for (int k = 0; k < steps; ++k) {
     const int par = k & 1;
@@ -460,18 +466,42 @@ static cudaGraphExec_t capture(lbm_ctx* c, int steps, int* launches) {
     lbm::launch_enthalpy_commit(c->d, par, c->cap);
     nl += 2;
   }
-  if (cudaStreamEndCapture(c->cap, &g) != cudaSuccess || !g) {
-    cudaGetLastError();
-    return nullptr;
-  }
+  return nl;
+}
+
+static cudaGraphExec_t instantiate(cudaGraph_t g) {
   cudaGraphExec_t ex = nullptr;
   if (cudaGraphInstantiateWithFlags(&ex, g, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) {
     cudaGetLastError();
     ex = nullptr;
   }
   cudaGraphDestroy(g);
-  *launches = nl;
   return ex;
+}
+
+// A graph of `steps` (even) steps starting at parity 0, replayed on the
+// context stream.
+static cudaGraphExec_t capture(lbm_ctx* c, int steps, int* launches) {
+  if (!capture_streams(c)) return nullptr;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  const int nl = capture_body(c, steps);
+  if (cudaStreamEndCapture(c->cap, &g) != cudaSuccess || !g) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  *launches = nl;
+  return instantiate(g);
+}
+
+// Forget the captured graphs (after a change of kernel configuration).
+static void drop_graphs(lbm_ctx* c) {
+  if (c->g_long) cudaGraphExecDestroy(c->g_long);
+  if (c->g_pair) cudaGraphExecDestroy(c->g_pair);
+  c->g_long = c->g_pair = nullptr;
 }
 
 static const int EV_PER_STEP = 5;
@@ -532,6 +562,179 @@ int lbm_step(lbm_ctx* c, int64_t nsteps) {
 int64_t lbm_kernel_launches(const lbm_ctx* c) { return c ? c->launches : -1; }
 
 int lbm_kernel_variant(const lbm_ctx* c) { return c ? (c->use_tma ? 2 : 1) : -1; }
+
+int lbm_autotune(lbm_ctx* c, int trial_steps, int32_t* variant, int32_t* tiles_per_cta) {
+  if (!c || trial_steps < 2 || (trial_steps & 1) || c->timing) return LBM_ERR_INVALID_ARG;
+  struct Cand {
+    bool tma;
+    int tpc;
+  };
+  std::vector<Cand> cands{{false, 0}};
+  if (c->tma_ok)
+    for (int t : {2, 3, 4, 5, 6, 8}) cands.push_back({true, t});
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    return LBM_ERR_CUDA;
+  }
+  float best = 0.f;
+  Cand pick = {c->use_tma, c->tpc};
+  int rc = LBM_OK;
+  for (const Cand& k : cands) {
+    c->use_tma = k.tma;
+    if (k.tma) {
+      c->tpc = k.tpc;
+      c->d.tgrid = lbm::tma_grid(c->d, k.tpc);
+    }
+    drop_graphs(c);
+    // an even step count, then the trial twice: the first captures the graphs
+    // (host work that would idle the GPU inside the timed region), the second is timed
+    if (c->parity && (rc = lbm_step(c, 1)) != LBM_OK) break;
+    if ((rc = lbm_step(c, trial_steps)) != LBM_OK) break;
+    cudaEventRecord(e0, c->stream);
+    if ((rc = lbm_step(c, trial_steps)) != LBM_OK) break;
+    cudaEventRecord(e1, c->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = LBM_ERR_CUDA;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (&k == &cands[0] || ms < best) {
+      best = ms;
+      pick = k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->use_tma = pick.tma;
+  if (pick.tma) {
+    c->tpc = pick.tpc;
+    c->d.tgrid = lbm::tma_grid(c->d, pick.tpc);
+  }
+  drop_graphs(c);
+  if (rc != LBM_OK) return rc;
+  if (variant) *variant = c->use_tma ? 2 : 1;
+  if (tiles_per_cta) *tiles_per_cta = c->use_tma ? c->tpc : 0;
+  return cuda_err(cudaGetLastError());
+}
+
+// ---- batches -------------------------------------------------------------------
+
+struct lbm_batch {
+  std::vector<lbm_ctx*> ctx;
+  cudaStream_t stream;             // where lbm_batch_step launches
+  cudaStream_t cap;                // capture origin of the batch graph
+  std::vector<cudaEvent_t> ev_in, ev_out;   // per context: fork into / join out of the batch
+  cudaEvent_t ev_done;
+  cudaGraphExec_t graph;
+  std::vector<int> nl;             // kernels per context in one graph replay
+};
+
+void lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (cudaEvent_t e : b->ev_in) cudaEventDestroy(e);
+  for (cudaEvent_t e : b->ev_out) cudaEventDestroy(e);
+  if (b->ev_done) cudaEventDestroy(b->ev_done);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+int lbm_batch_create(lbm_ctx* const* ctxs, int count, void* stream, lbm_batch** out) {
+  if (!out) return LBM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!ctxs || count < 1) return LBM_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i]) return LBM_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return LBM_ERR_INVALID_ARG;
+  }
+  lbm_batch* b = new (std::nothrow) lbm_batch();
+  if (!b) return LBM_ERR_OOM;
+  b->ctx.assign(ctxs, ctxs + count);
+  b->stream = (cudaStream_t)stream;
+  b->cap = nullptr;
+  b->ev_done = nullptr;
+  b->graph = nullptr;
+  bool ok = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; ok && i < count; ++i) {
+    cudaEvent_t a = nullptr, z = nullptr;
+    ok = cudaEventCreateWithFlags(&a, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&z, cudaEventDisableTiming) == cudaSuccess;
+    if (a) b->ev_in.push_back(a);
+    if (z) b->ev_out.push_back(z);
+    ok = ok && capture_streams(ctxs[i]);
+  }
+  if (!ok) {
+    cudaGetLastError();
+    lbm_batch_destroy(b);
+    return LBM_ERR_CUDA;
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+// one graph: LBM_BATCH_STEPS steps of every context, one branch per context
+static int batch_capture(lbm_batch* b) {
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return LBM_ERR_CUDA;
+  }
+  b->nl.assign(b->ctx.size(), 0);
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    lbm_ctx* c = b->ctx[i];
+    cudaEventRecord(b->ev_in[i], b->cap);
+    cudaStreamWaitEvent(c->cap, b->ev_in[i], 0);
+    b->nl[i] = capture_body(c, LBM_BATCH_STEPS);
+    cudaEventRecord(b->ev_out[i], c->cap);
+    cudaStreamWaitEvent(b->cap, b->ev_out[i], 0);
+  }
+  if (cudaStreamEndCapture(b->cap, &g) != cudaSuccess || !g) {
+    cudaGetLastError();
+    return LBM_ERR_CUDA;
+  }
+  b->graph = instantiate(g);
+  return b->graph ? LBM_OK : LBM_ERR_CUDA;
+}
+
+int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
+  if (!b || nsteps < 0) return LBM_ERR_INVALID_ARG;
+  const int par = b->ctx[0]->parity;
+  for (lbm_ctx* c : b->ctx)
+    if (c->timing || c->parity != par) return LBM_ERR_INVALID_ARG;
+  // get every context to an even step count first
+  if (par && nsteps > 0) {
+    for (lbm_ctx* c : b->ctx) LBM_TRY(lbm_step(c, 1));
+    --nsteps;
+  }
+  const int64_t reps = nsteps / LBM_BATCH_STEPS;
+  if (reps > 0) {
+    if (!b->graph) LBM_TRY(batch_capture(b));
+    // the batch runs after what is queued on every context stream ...
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+      LBM_CUDA(cudaEventRecord(b->ev_in[i], b->ctx[i]->stream));
+      LBM_CUDA(cudaStreamWaitEvent(b->stream, b->ev_in[i], 0));
+    }
+    for (int64_t r = 0; r < reps; ++r) LBM_CUDA(cudaGraphLaunch(b->graph, b->stream));
+    // ... and before what is queued there next
+    LBM_CUDA(cudaEventRecord(b->ev_done, b->stream));
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+      lbm_ctx* c = b->ctx[i];
+      LBM_CUDA(cudaStreamWaitEvent(c->stream, b->ev_done, 0));
+      c->steps += reps * LBM_BATCH_STEPS;
+      c->launches += reps * b->nl[i];
+    }
+  }
+  const int64_t rest = nsteps - reps * LBM_BATCH_STEPS;
+  if (rest > 0)
+    for (lbm_ctx* c : b->ctx) LBM_TRY(lbm_step(c, rest));
+  return cuda_err(cudaGetLastError());
+}
 
 int lbm_status(lbm_ctx* c) {
   if (!c) return LBM_ERR_INVALID_ARG;

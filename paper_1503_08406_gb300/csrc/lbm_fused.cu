@@ -20,6 +20,18 @@ void launch_fused(const Dev& d, const TmaMaps* m, int parity, int mode, cudaStre
   else launch_fused_f32(d, m, parity, mode, s);
 }
 
+int tma_grid(const Dev& d, int tpc) {
+  const long long ntile = (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY);
+  const long long slots = d.tslots > 0 ? d.tslots : 1;
+  if (tpc < 1) tpc = 1;
+  long long waves = (ntile + slots * tpc / 2) / (slots * tpc);
+  if (waves < 1) waves = 1;
+  long long grid = waves * slots;
+  if (grid > ntile) grid = ntile;
+  if ((ntile + grid - 1) / grid > 32) grid = (ntile + 31) / 32;
+  return (int)grid;
+}
+
 bool tma_setup(Dev& d, TmaMaps* m) {
   if (d.storage == 1) return tma_setup_f16(d, m);
   if (d.storage == 2) return tma_setup_bf16(d, m);

@@ -439,10 +439,6 @@ constexpr int HY = 1;            // halo rows each side
 constexpr int WX = TX + 2 * HX;  // 40
 constexpr int WY = TY + 2 * HY;  // 10
 constexpr int TMA_MIN_CTAS = 4;  // resident CTAs per SM the register budget allows
-// target tiles per CTA: few enough that CTAs retire often (the enthalpy
-// kernels overlapping the far-tile pass need SMs), enough to hide the first
-// copy of each CTA (measured on the 2048^2 cavity: 4-5 best, 2-3 and 6-12 slower)
-constexpr int TMA_TPC = 5;
 constexpr long long TMA_WAIT_NS = 200000000LL;   // bounded mbarrier waits: 0.2 s
 constexpr int TMA_NBUF_EVEN = 2;
 constexpr int TMA_NBUF_ODD = 2;
@@ -778,22 +774,12 @@ static bool tma_setup_t(Dev& d, TmaMaps* m, CUtensorMapDataType dt) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, fused_tma_kernel<S, 1, true, 0>, TX * TY,
                                                 s1);
   if (cudaGetLastError() != cudaSuccess || per0 <= 0 || per1 <= 0) return false;
-  // whole waves of resident CTAs, each CTA about TMA_TPC tiles
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
     return false;
-  const long long ntile = (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY);
-  const long long slots = (long long)sms * (per0 < per1 ? per0 : per1);
-  auto grid_for = [&](long long tpc) {
-    long long waves = (ntile + slots * tpc / 2) / (slots * tpc);
-    if (waves < 1) waves = 1;
-    long long grid = waves * slots;
-    if (grid > ntile) grid = ntile;
-    if ((ntile + grid - 1) / grid > 32) grid = (ntile + 31) / 32;
-    return (int)grid;
-  };
-  d.tgrid = grid_for(TMA_TPC);
+  d.tslots = sms * (per0 < per1 ? per0 : per1);
+  d.tgrid = tma_grid(d, TMA_TPC);
   return true;
 }
 

@@ -37,6 +37,11 @@ constexpr int RE = TE + 2 * RH;
 constexpr int EB = 512;      // enthalpy solve block size (two CTAs per SM fit beside the far-tile pass)
 constexpr int CB = 1024;     // enthalpy commit block size
 constexpr int RB = 256;      // reduction block size
+// default tiles per CTA of the TMA-staged kernel: few enough that CTAs retire
+// often (the enthalpy kernels overlapping the far-tile pass need SMs), enough
+// to hide the first copy of each CTA (2048^2 cavity: 4-5 best, 2-3 and 6-12
+// slower); lbm_autotune picks per lattice
+constexpr int TMA_TPC = 5;
 
 struct Dev {
   int nx, ny;
@@ -64,6 +69,7 @@ struct Dev {
   int ntiles;                // etx * ety
   int egrid, cgrid;          // CTAs of the enthalpy solve / commit kernels (they walk the tile list)
   int tgrid;                 // CTAs of the TMA-staged fused kernel
+  int tslots;                // its CTAs resident at once (SMs x CTAs per SM)
   int max_inner;
   float tol;
   void* f;                   // 9 planes of the storage type
@@ -293,6 +299,9 @@ __device__ __forceinline__ void velocity(float jx, float jy, float T, float fl, 
 // when m is non-null (maps filled by tma_setup, which also sets tgrid)
 void launch_fused(const Dev& d, const TmaMaps* m, int parity, int mode, cudaStream_t s);
 bool tma_setup(Dev& d, TmaMaps* m);
+// CTAs of the TMA-staged kernel for about tpc tiles per CTA, in whole waves of
+// the resident CTAs (d.tslots), at most 32 tiles per CTA
+int tma_grid(const Dev& d, int tpc);
 void launch_enthalpy_solve(const Dev& d, int parity, cudaStream_t s);
 void launch_enthalpy_commit(const Dev& d, int parity, cudaStream_t s);
 void enthalpy_setup();

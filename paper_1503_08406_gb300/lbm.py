@@ -128,6 +128,13 @@ def load():
         lib.lbm_kernel_launches.restype = ctypes.c_int64
         lib.lbm_kernel_variant.argtypes = [_VP]
         lib.lbm_kernel_variant.restype = ctypes.c_int
+        lib.lbm_autotune.argtypes = [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_int32)]
+        lib.lbm_batch_create.argtypes = [ctypes.POINTER(_VP), ctypes.c_int, _VP,
+                                         ctypes.POINTER(_VP)]
+        lib.lbm_batch_step.argtypes = [_VP, ctypes.c_int64]
+        lib.lbm_batch_destroy.argtypes = [_VP]
+        lib.lbm_batch_destroy.restype = None
         lib.lbm_get_macros.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int]
         lib.lbm_reduce.argtypes = [_VP, _DP]
         lib.lbm_get_state.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int]
@@ -258,6 +265,14 @@ class Lattice:
     def kernel_launches(self) -> int:
         return int(self.lib.lbm_kernel_launches(self._h))
 
+    def autotune(self, trial_steps: int = 32) -> tuple[int, int]:
+        """Pick the fastest stream-collide configuration for this lattice (real
+        steps of the run); returns (kernel variant, tiles per CTA)."""
+        v, t = ctypes.c_int32(), ctypes.c_int32()
+        _check(self.lib.lbm_autotune(self._h, int(trial_steps), ctypes.byref(v), ctypes.byref(t)),
+               "lbm_autotune")
+        return v.value, t.value
+
     def kernel_variant(self) -> int:
         """1: ordinary-load stream-collide kernel, 2: TMA-staged kernel."""
         return int(self.lib.lbm_kernel_variant(self._h))
@@ -321,3 +336,33 @@ class Lattice:
                                         ctypes.byref(m)), "lbm_timing_read")
         return dict(fused_ms=ms[0], prep_ms=ms[1], solve_ms=ms[2], commit_ms=ms[3], steps=n.value,
                     tiles_solved=t.value, max_sweeps=m.value)
+
+
+class Batch:
+    """Several lattices advanced together through one CUDA graph per 32 steps
+    (lbm_batch_* in include/lbm.h).  Keeps references to the lattices."""
+
+    def __init__(self, lattices, stream=None):
+        torch = _torch()
+        self.lattices = list(lattices)
+        self.lib = load()
+        self.stream = stream or torch.cuda.Stream()
+        arr = (_VP * len(self.lattices))(*[lat._h.value for lat in self.lattices])
+        h = _VP()
+        _check(self.lib.lbm_batch_create(arr, len(self.lattices), self.stream.cuda_stream,
+                                         ctypes.byref(h)), "lbm_batch_create")
+        self._h = h
+
+    def step(self, nsteps: int):
+        _check(self.lib.lbm_batch_step(self._h, int(nsteps)), "lbm_batch_step")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
