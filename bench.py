@@ -70,6 +70,11 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--storage", choices=("fp32", "fp16", "bf16"), default="fp32",
                     help="population storage (arithmetic is FP32 in every case)")
+    ap.add_argument("--workload", choices=("cavity", "batched"), default="cavity",
+                    help="cavity: the 2048^2 heterogeneous cavity (default); batched: 64 "
+                         "uneven cavities advanced together through one CUDA graph")
+    ap.add_argument("--autotune", action="store_true",
+                    help="batched workload: tune each cavity's stream-collide kernel first")
     return ap.parse_args(argv)
 
 
@@ -241,6 +246,89 @@ def reference_arm(args):
     return 0
 
 
+def batched(args, torch):
+    """64 uneven cavities (sides 64..512, Ra 1e4..1e7, seed 4): the same steps
+    run one cavity after another (each through its own CUDA graphs) and all
+    together through one batch graph; one JSON line, value = the batched
+    whole-job MLUPS."""
+    import lbm_workloads as W
+    from paper_1503_08406_gb300 import Batch, Lattice
+    ws = W.batched_cavities(64, seed=4)
+    cells = sum(w.cells for w in ws)
+    stream = torch.cuda.current_stream()
+    lats = []
+    for w in ws:
+        lat = Lattice(w.nx, w.ny, stream=stream, **{**w.params, "storage": args.storage})
+        lat.set_fields(w.phi, w.K, w.T0, w.fl0)
+        lats.append(lat)
+    tuned = []
+    if args.autotune:
+        for lat in lats:
+            tuned.append(lat.autotune(16))
+        for lat in lats:   # same step count everywhere again
+            lat.step(max(x.steps_done() for x in lats) - lat.steps_done())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # one after another: every cavity's steps on the same stream
+    for lat in lats:
+        lat.step(args.warmup)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for lat in lats:
+        lat.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    b = Batch(lats)
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    launches0 = sum(lat.kernel_launches() for lat in lats)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    with ClockSampler(vis.split(",")[0] if vis else "0") as clk:
+        torch.cuda.synchronize()
+        e0.record(b.stream)
+        b.step(args.steps)
+        e1.record(b.stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = sum(lat.kernel_launches() for lat in lats) - launches0
+    status = max((lat.status() for lat in lats), key=abs)
+    # algorithmic bytes of the stream-collide passes of all cavities per step
+    bf, bs = ((BYTES_FLOW_NODE, BYTES_SOLID_NODE) if args.storage == "fp32"
+              else (BYTES_FLOW_NODE_16, BYTES_SOLID_NODE_16))
+    nbytes = 0
+    for lat in lats:
+        fl = lat.macros()["fl"][1:-1, 1:-1]
+        nf = int((fl >= 1e-3).sum())
+        nbytes += bf * nf + bs * (fl.size - nf)
+    peak, peak_kind = measured_peak()
+    achieved = nbytes / (ms / args.steps * 1e-3) / 1e9
+    value = cells * args.steps / (ms * 1e-3) / 1e6
+    line = {
+        "metric": METRIC + ", 64 batched cavities", "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "batched_cavities_64_seed4", "cells": cells,
+                   "sides": sorted({w.nx for w in ws}), "population_storage": args.storage,
+                   "graph": "one CUDA graph per 32 steps, one branch per cavity",
+                   "autotuned": tuned if args.autotune else None,
+                   "l2": "state ~%d MB > 129 MB L2; no flush" % (
+                       (14 * (4 if args.storage == "fp32" else 2) + 12) * cells // 2**20)},
+        "sequential": {"value": cells * args.steps / (ms_seq * 1e-3) / 1e6, "unit": UNIT,
+                       "ms_per_step": ms_seq / args.steps,
+                       "note": "the same steps, one cavity after another on one stream"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "whole batched step (stream-collide bytes / step time)",
+                     "algorithmic_bytes_per_step": nbytes},
+        "gpu_launches": launches, "status": status, "clocks": clk.summary(),
+        "e2e": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+    b.close()
+    return 0
+
+
 def main(argv=None):
     args = parse(argv)
     if args.impl == "reference":
@@ -250,6 +338,12 @@ def main(argv=None):
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device (there is no CPU path)")
     torch.cuda.set_device(local)
+    if args.workload == "batched":
+        if world > 1:
+            raise SystemExit("the batched workload runs on one GPU")
+        import __graft_entry__
+        __graft_entry__.build()
+        return batched(args, torch)
     dist = init_dist(world, "nccl")
     device = torch.device("cuda", local)
     if local == 0:

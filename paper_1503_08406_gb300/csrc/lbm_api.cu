@@ -686,14 +686,16 @@ static int batch_capture(lbm_batch* b) {
     return LBM_ERR_CUDA;
   }
   b->nl.assign(b->ctx.size(), 0);
+  // every branch forks from the start of the capture and joins at its end (a
+  // fork recorded after an earlier branch's join would chain the branches)
+  cudaEventRecord(b->ev_done, b->cap);
   for (size_t i = 0; i < b->ctx.size(); ++i) {
     lbm_ctx* c = b->ctx[i];
-    cudaEventRecord(b->ev_in[i], b->cap);
-    cudaStreamWaitEvent(c->cap, b->ev_in[i], 0);
+    cudaStreamWaitEvent(c->cap, b->ev_done, 0);
     b->nl[i] = capture_body(c, LBM_BATCH_STEPS);
     cudaEventRecord(b->ev_out[i], c->cap);
-    cudaStreamWaitEvent(b->cap, b->ev_out[i], 0);
   }
+  for (size_t i = 0; i < b->ctx.size(); ++i) cudaStreamWaitEvent(b->cap, b->ev_out[i], 0);
   if (cudaStreamEndCapture(b->cap, &g) != cudaSuccess || !g) {
     cudaGetLastError();
     return LBM_ERR_CUDA;
