@@ -253,3 +253,25 @@ def batched_cavities(count: int = 64, seed: int = 4) -> list:
         w.meta.update(Ra=Ra, Da=Da, phi=eps, St=St, seed=seed)
         out.append(w)
     return out
+
+
+def two_phase_slab(ratio: float = 10.0, nx: int = 200, ny: int = 6, alpha_s: float = 0.02,
+                   St: float = 1.0) -> Workload:
+    """Sec. 4.1 two-phase conduction melting: 200 x 6, periodic y, no flow,
+    phi = sigma = 1, T_b = 1 at x = 0, T_m = 0 with the mushy band
+    [-0.02, 0.02], solid initially at T_i = -1 (the right wall node held at
+    T_i too), alpha_s = 0.02 and alpha_l = ratio alpha_s (tau_T from alpha_l,
+    the solid value through alpha_ratio)."""
+    csT2 = 0.2
+    alpha_l = ratio * alpha_s
+    params = dict(bc=("dirichlet", "dirichlet", "periodic", "periodic"),
+                  T_bc=(1.0, -1.0, 0.0, 0.0), flow=0, St=St, sigma=1.0, dT=1.0,
+                  T_s=-0.02, T_l=0.02, tau_T=0.5 + alpha_l / csT2, alpha_ratio=ratio,
+                  H=float(nx))
+    T0 = np.full((ny, nx), -1.0)
+    T0[:, 0] = 1.0
+    fl0 = np.zeros((ny, nx))
+    fl0[:, 0] = 1.0
+    return Workload("two_phase_slab_%dx%d_ratio%g" % (nx, ny, ratio), nx, ny, params,
+                    np.ones((ny, nx)), np.full((ny, nx), 1e3), T0, fl0,
+                    meta=dict(alpha_s=alpha_s, alpha_l=alpha_l, T_b=1.0, T_i=-1.0, T_m=0.0))

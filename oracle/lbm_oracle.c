@@ -29,6 +29,9 @@
  *    a = phi dT / (sigma St), is reached by the plain iteration of Sec. 3.2.
  *  - varphi, K_eff, sigma and tau_T use f_l(n) for the whole step; only the
  *    source uses f_l(n+1).
+ *  - with alpha_l != alpha_s (Sec. 4.1), tau_T = 1/2 + alpha_e/(sigma c_sT^2),
+ *    alpha_e = alpha_l f_l + alpha_s (1 - f_l), per node; a wall node relaxes
+ *    at the rate of the inward neighbour it extrapolates from.
  */
 #include "lbm_oracle.h"
 
@@ -263,8 +266,24 @@ void ora_collide_flow(const ora_ctx* c, const double f[9], double T, double fl, 
 }
 
 /* Eq. (35), (38): collision with the latent source S~ = (S0, 0, 0, varpi S0, 0). */
+double ora_theta_T(const ora_ctx* c, double fl) {
+  const double r = c->p.alpha_ratio;
+  if (!(r > 0) || r == 1.0) return c->theta[1];
+  /* alpha_e / alpha_l = fl + (1 - fl) alpha_s / alpha_l */
+  return 1.0 / (0.5 + (c->tau_T - 0.5) * (fl + (1.0 - fl) / r));
+}
+
+/* Eq. (35), (38) with the diffusivity rate za for the two flux moments */
+static void collide_thermal(const ora_ctx* c, const double g[5], double ux, double uy,
+                            double src0, double za, double gpost[5]);
+
 void ora_collide_thermal(const ora_ctx* c, const double g[5], double ux, double uy, double src0,
                          double gpost[5]) {
+  collide_thermal(c, g, ux, uy, src0, c->theta[1], gpost);
+}
+
+static void collide_thermal(const ora_ctx* c, const double g[5], double ux, double uy,
+                            double src0, double za, double gpost[5]) {
   double T = 0;
   for (int i = 0; i < 5; ++i) T += g[i];
   double n[5], neq[5], np[5];
@@ -274,7 +293,8 @@ void ora_collide_thermal(const ora_ctx* c, const double g[5], double ux, double 
   }
   ora_thermal_meq(c, T, ux, uy, neq);
   double St[5] = {src0, 0, 0, c->p.varpi * src0, 0};
-  for (int k = 0; k < 5; ++k) np[k] = n[k] - c->theta[k] * (n[k] - neq[k]) + St[k];
+  const double th[5] = {c->theta[0], za, za, c->theta[3], c->theta[4]};
+  for (int k = 0; k < 5; ++k) np[k] = n[k] - th[k] * (n[k] - neq[k]) + St[k];
   for (int i = 0; i < 5; ++i) {
     gpost[i] = 0;
     for (int k = 0; k < 5; ++k) gpost[i] += c->Ninv[i][k] * np[k];
@@ -600,7 +620,10 @@ static void thermal_collide_stream(ora_ctx* c, const double* src, double* out) {
       double ux = c->wall[s] ? 0 : c->ux[s];
       double uy = c->wall[s] ? 0 : c->uy[s];
       double s0 = (src && !c->wall[s]) ? src[s] : 0;
-      ora_collide_thermal(c, gin, ux, uy, s0, gout);
+      /* tau_T from f_l(n); a wall node, whose populations the extrapolation
+       * took from its inward neighbour, relaxes at that neighbour's rate */
+      const double flt = c->wall[s] ? c->fl[inward(c, x, y)] : c->fl[s];
+      collide_thermal(c, gin, ux, uy, s0, ora_theta_T(c, flt), gout);
       for (int i = 0; i < 5; ++i) c->gpost[i * n + s] = gout[i];
     }
   /* streaming, Eq. (36); populations leaving the domain are dropped and the

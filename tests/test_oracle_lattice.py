@@ -199,3 +199,57 @@ def test_corner_solidification_symmetry_and_far_field(oracle_mod):
     diag = np.array([fl[i, i] for i in range(n)])
     X_diag = np.sqrt(2) * (0.5 * (1 - diag[0]) + (1 - diag[1:]).sum())
     assert X_diag > X
+
+
+# ---- Sec. 4.1: two-phase conduction melting with alpha_l != alpha_s ------------
+
+def _neumann_two_phase_melting(ratio, St=1.0, T_b=1.0, T_m=0.0, T_i=-1.0):
+    """eta of Eq. (46) with k_s / k_l = alpha_s / alpha_l (equal rho c_p), written out
+    from the melting problem: the flux balance at x_m = 2 eta sqrt(alpha_l t)."""
+    r = ratio
+    f = lambda e: (np.exp(-e * e) / erf(e)
+                   + (1.0 / r) * np.sqrt(r) * (T_i - T_m) / (T_b - T_m)
+                   * np.exp(-e * e * r) / erfc(e * np.sqrt(r))
+                   - e * np.sqrt(np.pi) / St)
+    return brentq(f, 1e-6, 3.0)
+
+
+@pytest.mark.parametrize("ratio,front_tol,T_tol", [(1.0, 0.01, 5e-3), (10.0, 0.02, 5e-2)])
+def test_two_phase_conduction_melting(oracle_mod, ratio, front_tol, T_tol):
+    """Sec. 4.1 set-up: 200 x 6 periodic in y, T_b = 1, T_i = -1, mushy band +-0.02,
+    St = 1, alpha_s = 0.02, alpha_l = ratio alpha_s through a liquid-fraction
+    weighted tau_T; at Fo = t alpha_s / H^2 = 0.01 (H = 200) the front is the
+    two-phase Neumann front, and the liquid and solid profiles follow Eq. (44), (45).
+    With one diffusivity for both phases (ratio ignored) the ratio-10 front would
+    sit 15% short of it."""
+    w = W.two_phase_slab(ratio)
+    o = _run(oracle_mod, w, 0)
+    t = int(round(0.01 * 200 ** 2 / w.meta["alpha_s"]))
+    o.step(t)
+    m = o.macros()
+    eta = _neumann_two_phase_melting(ratio)
+    a_l, a_s = w.meta["alpha_l"], w.meta["alpha_s"]
+    fl = m["fl"].mean(axis=0)
+    x_m = 0.5 * fl[0] + fl[1:].sum()
+    x_an = 2 * eta * np.sqrt(a_l * t)
+    assert abs(x_m / x_an - 1) < front_tol, (x_m, x_an)
+    x = np.arange(w.nx, dtype=float)
+    T_an = np.where(x <= x_an, 1 - erf(x / (2 * np.sqrt(a_l * t))) / erf(eta),
+                    -1 + erfc(x / (2 * np.sqrt(a_s * t))) / erfc(eta * np.sqrt(a_l / a_s)))
+    assert np.abs(m["T"].mean(axis=0) - T_an).max() < T_tol
+    # the solution is one-dimensional
+    assert np.abs(m["T"] - m["T"][0]).max() < 1e-12
+
+
+def test_two_phase_eta_matches_paper_values():
+    """eta for alpha_l / alpha_s = 1 and 10 (St = 1, T_b = 1, T_m = 0, T_i = -1)."""
+    assert abs(_neumann_two_phase_melting(1.0) - 0.37776) < 1e-5
+    assert abs(_neumann_two_phase_melting(10.0) - 0.44697) < 1e-5
+
+
+def test_theta_follows_liquid_fraction(oracle_mod):
+    """zeta_alpha(f_l) = 1 / (1/2 + alpha_e(f_l) / (sigma c_sT^2)), alpha_e linear in f_l."""
+    w = W.two_phase_slab(10.0)
+    o = oracle_mod.Oracle(w.nx, w.ny, **w.params)
+    for fl, alpha in ((0.0, 0.02), (1.0, 0.2), (0.25, 0.25 * 0.2 + 0.75 * 0.02)):
+        assert abs(o.theta_T(fl) - 1.0 / (0.5 + alpha / 0.2)) < 1e-14
