@@ -89,6 +89,10 @@ typedef struct {
                                      qualifies), 1 ordinary loads, 2 TMA-staged (falls back to 1
                                      where the lattice does not qualify); results are identical */
   int32_t storage;                /* LBM_STORAGE_*: population storage (default FP32) */
+  double  alpha_ratio;            /* alpha_l / alpha_s (Sec. 4.1): tau_T (the liquid value) is
+                                     applied per node as 1/2 + (tau_T - 1/2)(f_l + (1 - f_l)/ratio),
+                                     i.e. alpha_e = alpha_l f_l + alpha_s (1 - f_l); 0 or 1: one
+                                     diffusivity for both phases */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;

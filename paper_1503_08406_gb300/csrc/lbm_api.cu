@@ -115,6 +115,7 @@ int check_params(const lbm_params* p) {
   if ((p->bc[2] == LBM_BC_PERIODIC) != (p->bc[3] == LBM_BC_PERIODIC)) return LBM_ERR_INVALID_ARG;
   if (p->kernel_variant < 0 || p->kernel_variant > 2) return LBM_ERR_INVALID_ARG;
   if (p->storage < LBM_STORAGE_FP32 || p->storage > LBM_STORAGE_BF16) return LBM_ERR_INVALID_ARG;
+  if (!(p->alpha_ratio >= 0)) return LBM_ERR_INVALID_ARG;
   return LBM_OK;
 }
 
@@ -259,6 +260,9 @@ int lbm_create(const lbm_params* pin, void* stream, void* workspace, size_t work
   d.s_q = (float)p.s_q;
   d.s_nu = p.flow ? (float)(1.0 / der[0]) : 0.f;
   d.z_a = (float)(1.0 / der[1]);
+  d.alpha_var = (p.alpha_ratio > 0 && p.alpha_ratio != 1.0) ? 1 : 0;
+  d.tauT_l = (float)der[1];
+  d.inv_aratio = d.alpha_var ? (float)(1.0 / p.alpha_ratio) : 1.f;
   d.z_e = (float)p.zeta_e;
   d.z_nu = (float)p.zeta_nu;
   d.varpi = (float)p.varpi;

@@ -277,8 +277,11 @@ __device__ __forceinline__ bool node_update(const Dev& d, int x, int y, const Ge
   const float n3 = -4.f * g0 + g1 + g2 + g3 + g4;
   const float n4 = g1 - g2 + g3 - g4;
   const float th = d.conv * d.csT2;   // vartheta / sigma
-  const float b1 = -0.5f * d.z_a * (n1 - th * ux * T);
-  const float b2 = -0.5f * d.z_a * (n2 - th * uy * T);
+  // zeta_alpha = 1/tau_T; with alpha_l != alpha_s, alpha_e follows f_l(n) (Sec. 4.1)
+  const float za =
+      d.alpha_var ? 1.f / (0.5f + (d.tauT_l - 0.5f) * (flc + (1.f - flc) * d.inv_aratio)) : d.z_a;
+  const float b1 = -0.5f * za * (n1 - th * ux * T);
+  const float b2 = -0.5f * za * (n2 - th * uy * T);
   const float b3 = -0.05f * d.z_e * (n3 - d.varpi * T);
   const float b4 = -0.25f * d.z_nu * n4;
   const float gp0 = g0 - 4.f * b3;

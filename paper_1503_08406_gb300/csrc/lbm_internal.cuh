@@ -55,6 +55,8 @@ struct Dev {
   float nu_l, g_beta, T_ref;
   float s_e, s_eps, s_q, s_nu;
   float z_a, z_e, z_nu;      // 1/tau_T, zeta_e, zeta_nu
+  int alpha_var;             // tau_T depends on f_l (alpha_l != alpha_s)
+  float tauT_l, inv_aratio;  // liquid tau_T, alpha_s / alpha_l
   float varpi, csT2, sigma;
   float conv;                // vartheta / (sigma c_sT^2)
   float wt0, wt1;            // D2Q5 weights of Eq. (39)

@@ -54,6 +54,7 @@ class lbm_params(ctypes.Structure):
         ("screen_tol", ctypes.c_double),
         ("kernel_variant", ctypes.c_int32),
         ("storage", ctypes.c_int32),
+        ("alpha_ratio", ctypes.c_double),
     ]
 
 
@@ -62,7 +63,7 @@ PARAM_DEFAULTS = dict(
     flow=1, Ra=0.0, Pr=0.0, Ma=0.1, J=1.0, lambda_=1.0, sigma=1.0, St=1.0, dT=1.0, H=0.0,
     T_ref=0.0, T_s=0.0, T_l=0.0, varpi=-2.0, rho0=1.0, tau_nu=-1.0, tau_T=-1.0, g_beta=-1.0,
     s_e=0.0, s_eps=0.0, s_q=0.0, zeta_e=0.0, zeta_nu=0.0, f_act=1e-3,
-    max_inner_iters=1000, inner_tol=1e-6, screen_tol=0.0, kernel_variant=0, storage=0,
+    max_inner_iters=1000, inner_tol=1e-6, screen_tol=0.0, kernel_variant=0, storage=0, alpha_ratio=0.0,
 )
 
 
