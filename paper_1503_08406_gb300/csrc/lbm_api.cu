@@ -294,9 +294,15 @@ int lbm_create(const lbm_params* pin, void* stream, void* workspace, size_t work
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
       sms = 1;
     // the solve runs two 512-thread CTAs per SM (they fit beside the far-tile
-    // fused pass they overlap), the commit one 1024-thread CTA per SM
+    // fused pass they overlap), the commit one 1024-thread CTA per SM; a small
+    // lattice lists few tiles, so it gets at most an eighth of its tiles (at
+    // least 32) in CTAs: CTAs with nothing to do still take shared memory and
+    // slots from the lattices they run beside in a batch
+    const int cap = d.ntiles / 8 > 32 ? d.ntiles / 8 : 32;
     d.egrid = d.ntiles < 2 * sms ? d.ntiles : 2 * sms;
+    if (d.egrid > cap) d.egrid = cap;
     d.cgrid = d.ntiles < sms ? d.ntiles : sms;
+    if (d.cgrid > cap) d.cgrid = cap;
     lbm::enthalpy_setup();
   }
   d.max_inner = p.max_inner_iters;
