@@ -47,7 +47,8 @@ BYTES_SOLID_NODE = 44
 # with 16-bit population storage: f 18 x 2 B, g 10 x 2 B + f_l, phi, K; solid g 10 x 2 + f_l
 BYTES_FLOW_NODE_16 = 68
 BYTES_SOLID_NODE_16 = 24
-KERNEL_SOURCES = ("paper_1503_08406_gb300/csrc/lbm_fused.cu",
+KERNEL_SOURCES = ("paper_1503_08406_gb300/csrc/lbm_fused.cuh",
+                  "paper_1503_08406_gb300/csrc/lbm_fused_f32.cu",
                   "paper_1503_08406_gb300/csrc/lbm_internal.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_tma_traffic_heterogeneous_cavity_2048.json")
 
