@@ -39,7 +39,6 @@
 
 namespace lbm {
 
-constexpr int RC = RE / 2;  // nodes of one colour per region row
 // Over-relaxation factor of the projected SOR sweeps.  The Jacobi map of the
 // self-solved update has spectral radius at most 4 w~_1 a / (T_l - T_s + w~_0 a),
 // which is 2/3 with the paper's varpi = -2; red-black SOR on this diagonally
@@ -81,6 +80,7 @@ __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
   float* sfn = sa + RE * RE;         // f_l(n)
   float* sq = sfn + RE * RE;         // a (f - f_l(n))
   float* sf = sq + RE * RE;          // current iterate
+  __shared__ int sbox[4];            // box of the nodes the sweeps update: x0, x1, y0, y1
   const int tid = threadIdx.x;
   const int cnt = d.lcount[PAR];
   const int stamp = stamp_of(d, PAR);
@@ -110,6 +110,65 @@ __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
       sf[k] = fn;
     }
     __syncthreads();
+    // Nodes whose update is clamped whatever their neighbours do are fixed now
+    // and left out of the sweeps: with q_j in [-a_j f_l(n)_j, a_j (1 - f_l(n)_j)],
+    // the unclamped value (b - w~_1 sum_j q_j) inv stays <= 0 (or >= 1) when it
+    // does so at the extreme sum.  The sweeps then cover only the bounding box of
+    // the nodes left (a band along the front); the fixed point is unchanged.
+    if (tid == 0) {
+      sbox[0] = RE;
+      sbox[1] = -1;
+      sbox[2] = RE;
+      sbox[3] = -1;
+    }
+    __syncthreads();
+    {
+      int bx0 = RE, bx1 = -1, by0 = RE, by1 = -1;
+      for (int k = tid; k < RE * RE; k += EB) {
+        const float inv = sinv[k];
+        if (inv == 0.f) continue;
+        const int ly = k / RE, lx = k - ly * RE;
+        float nlo = 0.f, nhi = 0.f;   // extreme neighbour sums of q
+        auto acc = [&](int j) {
+          nlo -= sa[j] * sfn[j];
+          nhi += sa[j] * (1.f - sfn[j]);
+        };
+        if (lx > 0) acc(k - 1);
+        if (lx < RE - 1) acc(k + 1);
+        if (ly > 0) acc(k - RE);
+        if (ly < RE - 1) acc(k + RE);
+        const float b = sbase[k];
+        const float hi_raw = (b - w1 * nlo) * inv, lo_raw = (b - w1 * nhi) * inv;
+        float v = -1.f;
+        if (hi_raw < -1e-6f) v = 0.f;            // clamped to 0 for any neighbour values
+        else if (lo_raw > 1.f + 1e-6f) v = 1.f;  // clamped to 1
+        if (v >= 0.f) {
+          sf[k] = v;
+          sq[k] = sa[k] * (v - sfn[k]);
+          sinv[k] = 0.f;
+        } else {
+          bx0 = min(bx0, lx);
+          bx1 = max(bx1, lx);
+          by0 = min(by0, ly);
+          by1 = max(by1, ly);
+        }
+      }
+      bx0 = __reduce_min_sync(0xffffffffu, bx0);
+      bx1 = __reduce_max_sync(0xffffffffu, bx1);
+      by0 = __reduce_min_sync(0xffffffffu, by0);
+      by1 = __reduce_max_sync(0xffffffffu, by1);
+      if ((tid & 31) == 0 && bx1 >= 0) {
+        atomicMin(&sbox[0], bx0);
+        atomicMax(&sbox[1], bx1);
+        atomicMin(&sbox[2], by0);
+        atomicMax(&sbox[3], by1);
+      }
+    }
+    __syncthreads();
+    const int lx0 = sbox[0], ly0 = sbox[2];
+    const int ncol = sbox[1] >= lx0 ? (sbox[1] - lx0 + 2) >> 1 : 0;   // per colour and row
+    const int nbox = ncol * (sbox[3] - ly0 + 1);
+    const float inv_ncol = ncol ? 1.f / (float)ncol : 0.f;
     int it = 0;
     bool more = true;
     int polish = 2;   // extra sweeps after the stop test passes
@@ -121,18 +180,22 @@ __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
       bool changed = false;
 #pragma unroll
       for (int color = 0; color < 2; ++color) {
-        for (int j = tid; j < RE * RC; j += EB) {
-          const int ly = j / RC;
-          const int lx = 2 * (j - ly * RC) + ((ly + color) & 1);
+        for (int j = tid; j < nbox; j += EB) {
+          // (row, column pair) of the box; exact for j < 2^16 and ncol <= 24
+          const int r = (int)(((float)j + 0.5f) * inv_ncol);
+          const int ly = ly0 + r;
+          const int lx = lx0 + ((lx0 + ly + color) & 1) + 2 * (j - r * ncol);
+          if (lx >= RE) continue;
           const int k = ly * RE + lx;
+          const float inv = sinv[k];
+          if (inv == 0.f) continue;   // wall, outside, or fixed above
           const float a = sa[k];
-          if (a == 0.f) continue;
           float nb = 0.f;
           if (lx > 0) nb += sq[k - 1];
           if (lx < RE - 1) nb += sq[k + 1];
           if (ly > 0) nb += sq[k - RE];
           if (ly < RE - 1) nb += sq[k + RE];
-          const float b = sbase[k], inv = sinv[k];
+          const float b = sbase[k];
           const float fo = sf[k];
           const float raw = (b - w1 * nb) * inv;
           float v = (om == 1.f) ? raw : fo + om * (raw - fo);
