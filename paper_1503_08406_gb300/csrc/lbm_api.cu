@@ -888,3 +888,138 @@ int lbm_timing_read(lbm_ctx* c, double ms[4], int64_t* steps_timed, int64_t* til
 }
 
 }  // extern "C"
+
+// ---- adjoint of the conduction step ------------------------------------------------
+
+namespace {
+
+// device buffers of one adjoint run, freed on scope exit
+struct DevMem {
+  std::vector<void*> ptrs;
+  float* get(size_t count) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, count * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    return static_cast<float*>(p);
+  }
+  ~DevMem() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+};
+
+}  // namespace
+
+int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32_t mu_sweeps,
+                     float* d_phi, float* d_wall_T_left, double* J, int device_ptrs) {
+  if (!c || nsteps < 1 || checkpoint_every < 0 || mu_sweeps < 0 || !d_phi || !d_wall_T_left || !J)
+    return LBM_ERR_INVALID_ARG;
+  const lbm_params& p = c->p;
+  if (p.flow || c->timing || p.storage != LBM_STORAGE_FP32 || c->d.alpha_var) return LBM_ERR_INVALID_ARG;
+  if (!c->d.per_y || c->d.per_x || p.bc[0] != LBM_BC_DIRICHLET) return LBM_ERR_INVALID_ARG;
+  const int64_t K = checkpoint_every > 0 ? checkpoint_every
+                                         : (int64_t)ceil(sqrt((double)nsteps));
+  const int sweeps = mu_sweeps > 0 ? mu_sweeps : 30;
+  const size_t n = (size_t)c->d.n, st = 6 * n;   // a state: g (5 planes) and f_l
+  const int64_t ncp = nsteps / K + 1;
+  DevMem mem;
+  float* cps = mem.get((size_t)ncp * st);
+  float* seg = mem.get((size_t)(K + 1) * st);
+  float* fin = mem.get(st);
+  lbm::AdjBuffers b;
+  b.a = mem.get(n);
+  b.lamg = mem.get(5 * n);
+  b.lamf = mem.get(n);
+  b.lamf_tot = mem.get(n);
+  b.ls = mem.get(n);
+  b.cinv = mem.get(n);
+  b.mu0 = mem.get(n);
+  b.mu1 = mem.get(n);
+  b.lamgpre = mem.get(5 * n);
+  b.lama = mem.get(n);
+  b.lamtw = mem.get((size_t)c->d.ny);
+  b.At = mem.get(25);
+  double* dJ = reinterpret_cast<double*>(mem.get(2));
+  if (!cps || !seg || !fin || !b.a || !b.lamg || !b.lamf || !b.lamf_tot || !b.ls || !b.cinv ||
+      !b.mu0 || !b.mu1 || !b.lamgpre || !b.lama || !b.lamtw || !b.At || !dJ)
+    return LBM_ERR_OOM;
+  // transposed collision matrix with u = 0: g+ = A g,
+  // A = N^-1 [(I - Theta) N + Theta e 1^T], e = (1, 0, 0, varpi, 0), Eq. (32)-(37)
+  {
+    static const double N5[5][5] = {{1, 1, 1, 1, 1}, {0, 1, 0, -1, 0}, {0, 0, 1, 0, -1},
+                                    {-4, 1, 1, 1, 1}, {0, 1, -1, 1, -1}};
+    const double th[5] = {1.0, c->d.z_a, c->d.z_a, c->d.z_e, c->d.z_nu};
+    const double eq[5] = {1.0, 0.0, 0.0, p.varpi, 0.0};
+    float At[25];
+    for (int i = 0; i < 5; ++i)
+      for (int j = 0; j < 5; ++j) {
+        double a = 0.0;
+        for (int k = 0; k < 5; ++k) {
+          double nk = 0.0;
+          for (int m = 0; m < 5; ++m) nk += N5[k][m] * N5[k][m];
+          const double ninv = N5[k][i] / nk;   // (N^-1)[i][k]
+          a += ninv * ((1.0 - th[k]) * N5[k][j] + th[k] * eq[k]);
+        }
+        At[j * 5 + i] = (float)a;
+      }
+    LBM_CUDA(cudaMemcpyAsync(b.At, At, sizeof At, cudaMemcpyHostToDevice, c->stream));
+  }
+  auto save = [&](float* dst) -> int {
+    LBM_TRY(lbm_get_state(c, nullptr, dst, dst + 5 * n, 1));
+    return LBM_OK;
+  };
+  auto restore = [&](const float* src) -> int {
+    LBM_TRY(lbm_set_state(c, nullptr, src, src + 5 * n, 1));
+    return LBM_OK;
+  };
+  const int64_t steps0 = c->steps;
+  // forward, keeping a state every K steps
+  LBM_TRY(save(cps));
+  for (int64_t j = 1; j < ncp; ++j) {
+    LBM_TRY(lbm_step(c, K));
+    LBM_TRY(save(cps + (size_t)j * st));
+  }
+  const int64_t done = (ncp - 1) * K;
+  if (nsteps > done) LBM_TRY(lbm_step(c, nsteps - done));
+  LBM_TRY(save(fin));
+  lbm::adj_objective(c->d, fin + 5 * n, dJ, c->stream);
+  // reverse sweep, one segment at a time, its states recomputed from the checkpoint
+  lbm::adj_seed(c->d, b.lamf, b.lamg, b.a, c->stream);
+  LBM_CUDA(cudaMemsetAsync(b.lama, 0, n * sizeof(float), c->stream));
+  LBM_CUDA(cudaMemsetAsync(b.lamtw, 0, c->d.ny * sizeof(float), c->stream));
+  for (int64_t j = ncp - 1; j >= 0; --j) {
+    const int64_t first = j * K;
+    const int64_t len = (j == ncp - 1) ? nsteps - first : K;
+    if (len <= 0) continue;
+    LBM_TRY(restore(cps + (size_t)j * st));
+    LBM_CUDA(cudaMemcpyAsync(seg, cps + (size_t)j * st, st * sizeof(float),
+                             cudaMemcpyDeviceToDevice, c->stream));
+    for (int64_t m = 1; m <= len; ++m) {
+      LBM_TRY(lbm_step(c, 1));
+      LBM_TRY(save(seg + (size_t)m * st));
+    }
+    for (int64_t m = len - 1; m >= 0; --m) {
+      const float* s0 = seg + (size_t)m * st;
+      const float* s1 = seg + (size_t)(m + 1) * st;
+      lbm::adj_step(c->d, b, s1, s0 + 5 * n, s1 + 5 * n, sweeps, c->stream);
+    }
+    LBM_CUDA(cudaGetLastError());
+  }
+  // back to where the forward run ended
+  LBM_TRY(restore(fin));
+  c->steps = steps0 + nsteps;
+  // d J / d phi = (dT / (sigma St)) d J / d a
+  std::vector<float> la(n), lt(c->d.ny);
+  LBM_CUDA(cudaMemcpyAsync(la.data(), b.lama, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(cudaMemcpyAsync(lt.data(), b.lamtw, c->d.ny * sizeof(float), cudaMemcpyDeviceToHost,
+                           c->stream));
+  LBM_CUDA(cudaMemcpyAsync(J, dJ, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(cudaStreamSynchronize(c->stream));
+  for (size_t s = 0; s < n; ++s) la[s] *= c->d.lat;
+  const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+  LBM_CUDA(cudaMemcpy(d_phi, la.data(), n * sizeof(float), kind));
+  LBM_CUDA(cudaMemcpy(d_wall_T_left, lt.data(), c->d.ny * sizeof(float), kind));
+  return LBM_OK;
+}

@@ -316,6 +316,25 @@ void launch_reduce(const Dev& d, int parity, double* partials, double* out, int 
 int reduce_blocks(const Dev& d);
 void launch_get_state(const Dev& d, int parity, float* f, float* g, cudaStream_t s);
 void launch_set_state(const Dev& d, const float* f, const float* g, cudaStream_t s);
+// Adjoint of the conduction step (lbm_adjoint.cu); all buffers n floats unless noted
+struct AdjBuffers {
+  float* a;          // a = phi dT / (sigma St)
+  float* lamg;       // 5 n: adjoint of the populations after the step being reversed
+  float* lamf;       // adjoint of f_l after the step (in), before it (out)
+  float* lamf_tot;   // adjoint of f_l after the step, the source's share included
+  float* ls;         // source adjoint sum_i w~_i lam_g_i(y + e_i)
+  float* cinv;       // 1/(T_l - T_s + a) on unclamped nodes, else 0
+  float* mu0;        // fixed-point adjoint, ping-pong
+  float* mu1;
+  float* lamgpre;    // 5 n: adjoint of the populations before the step
+  float* lama;       // accumulated adjoint of a
+  float* lamtw;      // ny: accumulated adjoint of the left wall profile
+  float* At;         // 25: transposed collision matrix (u = 0)
+};
+void adj_seed(const Dev& d, float* lamf, float* lamg, float* a, cudaStream_t s);
+void adj_objective(const Dev& d, const float* fl, double* out, cudaStream_t s);
+void adj_step(const Dev& d, const AdjBuffers& b, const float* g1, const float* f0, const float* f1,
+              int mu_sweeps, cudaStream_t s);
 void launch_validate(const Dev& d, const float* phi, const float* K, const float* T0,
                      const float* fl0, int* bad, cudaStream_t s);
 

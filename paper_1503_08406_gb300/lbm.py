@@ -131,6 +131,8 @@ def load():
         lib.lbm_kernel_variant.restype = ctypes.c_int
         lib.lbm_autotune.argtypes = [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_int32)]
+        lib.lbm_adjoint_melt.argtypes = [_VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                         _VP, _VP, _DP, ctypes.c_int]
         lib.lbm_batch_create.argtypes = [ctypes.POINTER(_VP), ctypes.c_int, _VP,
                                          ctypes.POINTER(_VP)]
         lib.lbm_batch_step.argtypes = [_VP, ctypes.c_int64]
@@ -273,6 +275,18 @@ class Lattice:
         _check(self.lib.lbm_autotune(self._h, int(trial_steps), ctypes.byref(v), ctypes.byref(t)),
                "lbm_autotune")
         return v.value, t.value
+
+    def adjoint_melt(self, nsteps: int, checkpoint_every: int = 0, mu_sweeps: int = 0):
+        """Run nsteps steps; return the melted fraction after them and its
+        gradient with respect to the porosity field ([ny, nx]) and the left
+        wall's temperature profile ([ny]) (lbm_adjoint_melt in include/lbm.h)."""
+        dphi = np.zeros((self.ny, self.nx), dtype=np.float32)
+        dtw = np.zeros(self.ny, dtype=np.float32)
+        J = ctypes.c_double()
+        _check(self.lib.lbm_adjoint_melt(self._h, int(nsteps), int(checkpoint_every),
+                                         int(mu_sweeps), dphi.ctypes.data, dtw.ctypes.data,
+                                         ctypes.byref(J), 0), "lbm_adjoint_melt")
+        return J.value, dphi, dtw
 
     def kernel_variant(self) -> int:
         """1: ordinary-load stream-collide kernel, 2: TMA-staged kernel."""
