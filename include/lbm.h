@@ -157,7 +157,7 @@ int64_t lbm_kernel_launches(const lbm_ctx* c);
  * (48 with 16-bit storage), ny >= 10); -1 for NULL. */
 int lbm_kernel_variant(const lbm_ctx* c);
 
-/* Autotuner (survey item f2): times `trial_steps` (even, >= 2) graph-replayed
+/* Autotuner: times `trial_steps` (even, >= 2) graph-replayed
  * steps of this context for each stream-collide configuration -- the ordinary-
  * load kernel and, where the lattice qualifies, the TMA-staged kernel with
  * 2, 3, 4, 5, 6 or 8 tiles of 32x8 nodes per CTA -- and keeps the fastest.
@@ -168,7 +168,7 @@ int lbm_kernel_variant(const lbm_ctx* c);
  * NULL) receive the choice (tiles_per_cta 0 for the ordinary-load kernel). */
 int lbm_autotune(lbm_ctx* c, int trial_steps, int32_t* variant, int32_t* tiles_per_cta);
 
-/* Adjoint of the conduction step (survey item f1, in part).  Runs nsteps
+/* Adjoint of the conduction step.  Runs nsteps
  * steps forward from the context's current state and returns the melted
  * fraction J (mean f_l over non-wall nodes) after them, with its gradient with
  * respect to the porosity field (d_phi, nx*ny) and to the left wall's
@@ -176,8 +176,9 @@ int lbm_autotune(lbm_ctx* c, int trial_steps, int32_t* variant, int32_t* tiles_p
  * (the reverse of the wall extrapolation, collision, streaming, latent source
  * and, by the implicit function theorem, the enthalpy fixed point; the clamp of
  * Eq. (42) differentiates to 0 or 1).  States are kept every checkpoint_every
- * steps (0: sqrt(nsteps)) and the steps between recomputed; mu_sweeps Jacobi
- * sweeps solve the fixed point's adjoint per step (0: 30).  The context ends
+ * steps (0: sqrt(nsteps)) and the steps between recomputed (a CUDA graph per
+ * segment); Jacobi sweeps solve the fixed point's adjoint per step until the
+ * largest change is within 4e-7 of the value, at most mu_sweeps (0: 64).  The context ends
  * where the forward run left it (nsteps further on).  Covers: no flow
  * (flow = 0), periodic in y with wall columns at x = 0 (Dirichlet, the
  * profile) and x = nx - 1 (Dirichlet or adiabatic), FP32 storage, one thermal
@@ -187,7 +188,7 @@ int lbm_autotune(lbm_ctx* c, int trial_steps, int32_t* variant, int32_t* tiles_p
 int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32_t mu_sweeps,
                      float* d_phi, float* d_wall_T_left, double* J, int device_ptrs);
 
-/* Batches (survey item f2).  A batch advances several contexts together: each
+/* Batches.  A batch advances several contexts together: each
  * lbm_batch_step replays one CUDA graph holding LBM_BATCH_STEPS steps of every
  * context, each context's kernels on its own branch, so small lattices fill the
  * GPU together instead of one after another.  The contexts stay owned by the

@@ -17,8 +17,9 @@
 // nodes where 0 < z < 1 (elsewhere the clamp's derivative is 0): with
 // c = 1/(T_l - T_s + a) on those nodes and 0 elsewhere, the adjoint mu solves
 //   mu(y) = lam_f(y) + a(y) c(y) mu(y) - a(y) sum_i w~_i (c mu)(y + e_i),
-// solved here by Jacobi sweeps with the self term exact (a contraction: the
-// row sums of the coupling are at most 4 w~_1 a / (T_l - T_s + w~_0 a) <= 2/3).
+// solved here by Jacobi sweeps over those nodes only, with the self term exact
+// (a contraction: the row sums of the coupling are at most
+// 4 w~_1 a / (T_l - T_s + w~_0 a) <= 2/3).
 // At the fixed point z = f on those nodes, which removes the direct term of
 // d z / d a.
 #include "lbm_internal.cuh"
@@ -44,7 +45,7 @@ __device__ __forceinline__ float wt(const Dev& d, int i) { return i == 0 ? d.wt0
 //   c(y) = 1/(T_l - T_s + a) where 0 < z < 1, z from the state after the step
 __global__ void adj_prep_kernel(Dev d, const float* g1, const float* f0, const float* f1,
                                 const float* a, const float* lamg, const float* lamf_in,
-                                float* lamf, float* ls, float* cinv) {
+                                float* lamf, float* ls, float* cinv, int* list, int* count) {
   const int s = blockIdx.x * AB + threadIdx.x;
   if (s >= (int)d.n) return;
   const int y = s / d.nx, x = s - y * d.nx;
@@ -64,7 +65,10 @@ __global__ void adj_prep_kernel(Dev d, const float* g1, const float* f0, const f
     for (int i = 0; i < 5; ++i) T1 += g1[i * n + s];
     const float inv = 1.f / (d.dTt + a[s]);
     const float z = (T1 + a[s] * f1[s] - d.T_s) * inv;
-    if (z > 0.f && z < 1.f) c = inv;
+    if (z > 0.f && z < 1.f) {
+      c = inv;
+      list[atomicAdd(count, 1)] = s;   // the fixed point's adjoint couples these nodes only
+    }
     lamf[s] = lamf_in[s] - a[s] * L;
   } else {
     lamf[s] = lamf_in[s];
@@ -73,24 +77,51 @@ __global__ void adj_prep_kernel(Dev d, const float* g1, const float* f0, const f
   (void)f0;
 }
 
-// One Jacobi sweep of the fixed point's adjoint (self term exact).
-__global__ void adj_mu_kernel(Dev d, const float* a, const float* cinv, const float* lamf,
-                              const float* mu, float* mu_out) {
-  const int s = blockIdx.x * AB + threadIdx.x;
-  if (s >= (int)d.n) return;
-  const int y = s / d.nx, x = s - y * d.nx;
-  if (x == 0 || x == d.nx - 1) {
-    mu_out[s] = 0.f;
-    return;
-  }
-  float nb = 0.f;
+// The fixed point's adjoint on the unclamped nodes (elsewhere c mu = 0, and
+// only c mu is used further on): Jacobi sweeps with the self term exact, from
+// mu = 0, in one CTA (the unclamped nodes are a band along the front), until
+// no node changes by more than MU_RTOL of its value or after max_sweeps; the
+// result is left in mu0.  Leaves the list count at zero for the next step.
+constexpr float MU_RTOL = 4e-7f;
+
+__global__ void __launch_bounds__(1024) adj_mu_kernel(Dev d, const float* a, const float* cinv,
+                                                      const float* lamf, const int* list,
+                                                      int* count, float* mu0, float* mu1,
+                                                      int max_sweeps) {
+  const int cnt = *count;
+  for (int j = threadIdx.x; j < cnt; j += blockDim.x) mu0[list[j]] = 0.f;
+  __syncthreads();
+  float* mu = mu0;
+  float* mo = mu1;
+  for (int k = 0; k < max_sweeps; ++k) {
+    int moved = 0;
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+      const int s = list[j];
+      const int y = s / d.nx, x = s - y * d.nx;
+      float nb = 0.f;
 #pragma unroll
-  for (int i = 1; i < 5; ++i) {
-    const int t = adj_nb(d, x, y, ex9(i), ey9(i));
-    if (t >= 0) nb += cinv[t] * mu[t];
+      for (int i = 1; i < 5; ++i) {
+        const int t = adj_nb(d, x, y, ex9(i), ey9(i));
+        if (t >= 0) {
+          const float ct = cinv[t];
+          if (ct != 0.f) nb += ct * mu[t];
+        }
+      }
+      const float as = a[s], cs = cinv[s];
+      const float v = (lamf[s] - as * d.wt1 * nb) / (1.f - as * (1.f - d.wt0) * cs);
+      moved |= fabsf(v - mu[s]) > MU_RTOL * fabsf(v);
+      mo[s] = v;
+    }
+    moved = __syncthreads_or(moved);
+    float* t = mu;
+    mu = mo;
+    mo = t;
+    if (!moved) break;
   }
-  const float as = a[s], cs = cinv[s];
-  mu_out[s] = (lamf[s] - as * d.wt1 * nb) / (1.f - as * (1.f - d.wt0) * cs);
+  if (mu != mu0)
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) mu0[list[j]] = mu[list[j]];
+  __syncthreads();
+  if (threadIdx.x == 0) *count = 0;
 }
 
 // The rest of the step's adjoint: from nu = c mu, the adjoint of the
@@ -116,7 +147,7 @@ __global__ void adj_back_kernel(Dev d, const float* f0, const float* f1, const f
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
     const int t = adj_nb(d, x, y, ex9(i), ey9(i));
-    lp[i] = (t >= 0) ? lamg[i * n + t] + cinv[t] * mu[t] : 0.f;
+    lp[i] = (t >= 0) ? lamg[i * n + t] + (cinv[t] != 0.f ? cinv[t] * mu[t] : 0.f) : 0.f;
   }
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
@@ -134,7 +165,7 @@ __global__ void adj_back_kernel(Dev d, const float* f0, const float* f1, const f
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
     const int t = adj_nb(d, x, y, ex9(i), ey9(i));
-    if (t >= 0) sn += wt(d, i) * cinv[t] * mu[t];
+    if (t >= 0 && cinv[t] != 0.f) sn += wt(d, i) * cinv[t] * mu[t];
   }
   const float tot = ls[s] + sn;
   lamf0[s] = a[s] * tot;
@@ -209,21 +240,13 @@ void adj_objective(const Dev& d, const float* fl, double* out, cudaStream_t s) {
 void adj_step(const Dev& d, const AdjBuffers& b, const float* g1, const float* f0, const float* f1,
               int mu_sweeps, cudaStream_t s) {
   const unsigned nb = blocks(d.n);
-  adj_prep_kernel<<<nb, AB, 0, s>>>(d, g1, f0, f1, b.a, b.lamg, b.lamf, b.lamf_tot, b.ls, b.cinv);
-  cudaMemsetAsync(b.mu0, 0, d.n * sizeof(float), s);
-  float* mu = b.mu0;
-  float* mo = b.mu1;
-  for (int k = 0; k < mu_sweeps; ++k) {
-    adj_mu_kernel<<<nb, AB, 0, s>>>(d, b.a, b.cinv, b.lamf_tot, mu, mo);
-    float* t = mu;
-    mu = mo;
-    mo = t;
-  }
-  adj_back_kernel<<<nb, AB, 0, s>>>(d, f0, f1, b.a, b.cinv, mu, b.ls, b.lamg, b.lamf_tot, b.At,
+  adj_prep_kernel<<<nb, AB, 0, s>>>(d, g1, f0, f1, b.a, b.lamg, b.lamf, b.lamf_tot, b.ls, b.cinv,
+                                    b.list, b.count);
+  adj_mu_kernel<<<1, 1024, 0, s>>>(d, b.a, b.cinv, b.lamf_tot, b.list, b.count, b.mu0, b.mu1,
+                                   mu_sweeps);
+  adj_back_kernel<<<nb, AB, 0, s>>>(d, f0, f1, b.a, b.cinv, b.mu0, b.ls, b.lamg, b.lamf_tot, b.At,
                                     b.lamgpre, b.lamf, b.lama);
   adj_walls_kernel<<<blocks(d.ny), AB, 0, s>>>(d, b.lamgpre, b.lamtw);
-  // the step's input adjoint becomes the next (earlier) step's output adjoint
-  cudaMemcpyAsync(b.lamg, b.lamgpre, 5 * d.n * sizeof(float), cudaMemcpyDeviceToDevice, s);
 }
 
 }  // namespace lbm

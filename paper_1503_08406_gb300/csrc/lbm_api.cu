@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "lbm.h"
@@ -921,7 +922,7 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
   if (!c->d.per_y || c->d.per_x || p.bc[0] != LBM_BC_DIRICHLET) return LBM_ERR_INVALID_ARG;
   const int64_t K = checkpoint_every > 0 ? checkpoint_every
                                          : (int64_t)ceil(sqrt((double)nsteps));
-  const int sweeps = mu_sweeps > 0 ? mu_sweeps : 30;
+  const int sweeps = mu_sweeps > 0 ? mu_sweeps : 64;
   const size_t n = (size_t)c->d.n, st = 6 * n;   // a state: g (5 planes) and f_l
   const int64_t ncp = nsteps / K + 1;
   DevMem mem;
@@ -941,9 +942,12 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
   b.lama = mem.get(n);
   b.lamtw = mem.get((size_t)c->d.ny);
   b.At = mem.get(25);
+  b.list = reinterpret_cast<int*>(mem.get(n));
+  b.count = reinterpret_cast<int*>(mem.get(1));
   double* dJ = reinterpret_cast<double*>(mem.get(2));
   if (!cps || !seg || !fin || !b.a || !b.lamg || !b.lamf || !b.lamf_tot || !b.ls || !b.cinv ||
-      !b.mu0 || !b.mu1 || !b.lamgpre || !b.lama || !b.lamtw || !b.At || !dJ)
+      !b.mu0 || !b.mu1 || !b.lamgpre || !b.lama || !b.lamtw || !b.At || !b.list || !b.count ||
+      !dJ)
     return LBM_ERR_OOM;
   // transposed collision matrix with u = 0: g+ = A g,
   // A = N^-1 [(I - Theta) N + Theta e 1^T], e = (1, 0, 0, varpi, 0), Eq. (32)-(37)
@@ -989,6 +993,43 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
   lbm::adj_seed(c->d, b.lamf, b.lamg, b.a, c->stream);
   LBM_CUDA(cudaMemsetAsync(b.lama, 0, n * sizeof(float), c->stream));
   LBM_CUDA(cudaMemsetAsync(b.lamtw, 0, c->d.ny * sizeof(float), c->stream));
+  LBM_CUDA(cudaMemsetAsync(b.count, 0, sizeof(int), c->stream));
+  LBM_CUDA(cudaMemsetAsync(b.mu0, 0, n * sizeof(float), c->stream));
+  LBM_CUDA(cudaMemsetAsync(b.mu1, 0, n * sizeof(float), c->stream));
+  // One segment after its checkpoint is restored (parity 0): the len steps
+  // forward, each state kept, then the len reverse steps; the same launches
+  // for every whole segment, so they are captured once per (len, buffer
+  // parity) and replayed.
+  auto record_segment = [&](cudaStream_t sm, int64_t len) {
+    int par = 0;
+    for (int64_t m = 1; m <= len; ++m) {
+      float* sv = seg + (size_t)m * st;
+      lbm::launch_fused(c->d, c->tma(), par, 0, sm);
+      lbm::launch_enthalpy_solve(c->d, par, sm);
+      lbm::launch_enthalpy_commit(c->d, par, sm);
+      par ^= 1;
+      lbm::launch_get_state(c->d, par, nullptr, sv, sm);
+      cudaMemcpyAsync(sv + 5 * n, c->d.fl, n * sizeof(float), cudaMemcpyDeviceToDevice, sm);
+    }
+    for (int64_t m = len - 1; m >= 0; --m) {
+      const float* s0 = seg + (size_t)m * st;
+      const float* s1 = seg + (size_t)(m + 1) * st;
+      lbm::adj_step(c->d, b, s1, s0 + 5 * n, s1 + 5 * n, sweeps, sm);
+      std::swap(b.lamg, b.lamgpre);
+    }
+  };
+  struct SegGraph {
+    int64_t len;
+    float* lamg;
+    cudaGraphExec_t ex;
+  };
+  struct SegGraphs {
+    std::vector<SegGraph> v;
+    ~SegGraphs() {
+      for (SegGraph& g : v) cudaGraphExecDestroy(g.ex);
+    }
+  } graphs;
+  const bool can_capture = capture_streams(c);
   for (int64_t j = ncp - 1; j >= 0; --j) {
     const int64_t first = j * K;
     const int64_t len = (j == ncp - 1) ? nsteps - first : K;
@@ -996,14 +1037,29 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
     LBM_TRY(restore(cps + (size_t)j * st));
     LBM_CUDA(cudaMemcpyAsync(seg, cps + (size_t)j * st, st * sizeof(float),
                              cudaMemcpyDeviceToDevice, c->stream));
-    for (int64_t m = 1; m <= len; ++m) {
-      LBM_TRY(lbm_step(c, 1));
-      LBM_TRY(save(seg + (size_t)m * st));
+    float* const lamg0 = b.lamg;
+    float* const lamgpre0 = b.lamgpre;
+    cudaGraphExec_t ex = nullptr;
+    for (const SegGraph& g : graphs.v)
+      if (g.len == len && g.lamg == lamg0) ex = g.ex;
+    if (!ex && can_capture && len == K) {
+      cudaGraph_t gr = nullptr;
+      if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        record_segment(c->cap, len);
+        if (cudaStreamEndCapture(c->cap, &gr) == cudaSuccess && gr) {
+          ex = instantiate(gr);
+          if (ex) graphs.v.push_back({len, lamg0, ex});
+        }
+      }
+      cudaGetLastError();
+      b.lamg = lamg0;
+      b.lamgpre = lamgpre0;
     }
-    for (int64_t m = len - 1; m >= 0; --m) {
-      const float* s0 = seg + (size_t)m * st;
-      const float* s1 = seg + (size_t)(m + 1) * st;
-      lbm::adj_step(c->d, b, s1, s0 + 5 * n, s1 + 5 * n, sweeps, c->stream);
+    if (ex) {
+      LBM_CUDA(cudaGraphLaunch(ex, c->stream));
+      if (len & 1) std::swap(b.lamg, b.lamgpre);
+    } else {
+      record_segment(c->stream, len);
     }
     LBM_CUDA(cudaGetLastError());
   }

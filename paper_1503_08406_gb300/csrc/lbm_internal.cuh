@@ -330,9 +330,13 @@ struct AdjBuffers {
   float* lama;       // accumulated adjoint of a
   float* lamtw;      // ny: accumulated adjoint of the left wall profile
   float* At;         // 25: transposed collision matrix (u = 0)
+  int* list;         // n: the step's unclamped nodes
+  int* count;        // their number (kept at 0 between steps)
 };
 void adj_seed(const Dev& d, float* lamf, float* lamg, float* a, cudaStream_t s);
 void adj_objective(const Dev& d, const float* fl, double* out, cudaStream_t s);
+// one step of the reverse sweep: from b.lamg / b.lamf (after the step) to
+// b.lamgpre / b.lamf (before it); the caller swaps b.lamg and b.lamgpre
 void adj_step(const Dev& d, const AdjBuffers& b, const float* g1, const float* f0, const float* f1,
               int mu_sweeps, cudaStream_t s);
 void launch_validate(const Dev& d, const float* phi, const float* K, const float* T0,

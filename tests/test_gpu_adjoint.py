@@ -6,7 +6,7 @@ discrete adjoint (reverse of the step, the enthalpy fixed point by the
 implicit function theorem) with checkpointing; the FP64 reference
 (oracle/adjoint_ref.py) differentiates the same map by autograd and is itself
 pinned to finite differences of the C oracle.  The CUDA path runs in FP32, so
-the bars are relative, 1e-3 for the wall profile (the benchmark spec's figure) and
+the bars are relative, 1e-3 for the wall profile and
 for the porosity field normwise.
 """
 import numpy as np
