@@ -923,18 +923,20 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
   const int64_t K = checkpoint_every > 0 ? checkpoint_every
                                          : (int64_t)ceil(sqrt((double)nsteps));
   const int sweeps = mu_sweeps > 0 ? mu_sweeps : 64;
-  const size_t n = (size_t)c->d.n, st = 6 * n;   // a state: g (5 planes) and f_l
+  const size_t n = (size_t)c->d.n, st = 6 * n;   // a checkpoint: g (5 planes) and f_l
   const int64_t ncp = nsteps / K + 1;
+  if (!lbm::adj_init()) return LBM_ERR_CUDA;
   DevMem mem;
   float* cps = mem.get((size_t)ncp * st);
-  float* seg = mem.get((size_t)(K + 1) * st);
+  float* segT = mem.get((size_t)(K + 1) * n);   // T after each step of a segment
+  float* segF = mem.get((size_t)(K + 1) * n);   // f_l at the segment's start and after each step
   float* fin = mem.get(st);
   lbm::AdjBuffers b;
   b.a = mem.get(n);
   b.lamg = mem.get(5 * n);
   b.lamf = mem.get(n);
   b.lamf_tot = mem.get(n);
-  b.ls = mem.get(n);
+  b.nu = mem.get(n);
   b.cinv = mem.get(n);
   b.mu0 = mem.get(n);
   b.mu1 = mem.get(n);
@@ -943,11 +945,12 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
   b.lamtw = mem.get((size_t)c->d.ny);
   b.At = mem.get(25);
   b.list = reinterpret_cast<int*>(mem.get(n));
+  b.pos = reinterpret_cast<int*>(mem.get(n));
   b.count = reinterpret_cast<int*>(mem.get(1));
   double* dJ = reinterpret_cast<double*>(mem.get(2));
-  if (!cps || !seg || !fin || !b.a || !b.lamg || !b.lamf || !b.lamf_tot || !b.ls || !b.cinv ||
-      !b.mu0 || !b.mu1 || !b.lamgpre || !b.lama || !b.lamtw || !b.At || !b.list || !b.count ||
-      !dJ)
+  if (!cps || !segT || !segF || !fin || !b.a || !b.lamg || !b.lamf || !b.lamf_tot || !b.nu ||
+      !b.cinv || !b.mu0 || !b.mu1 || !b.lamgpre || !b.lama || !b.lamtw || !b.At || !b.list ||
+      !b.pos || !b.count || !dJ)
     return LBM_ERR_OOM;
   // transposed collision matrix with u = 0: g+ = A g,
   // A = N^-1 [(I - Theta) N + Theta e 1^T], e = (1, 0, 0, varpi, 0), Eq. (32)-(37)
@@ -1003,18 +1006,17 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
   auto record_segment = [&](cudaStream_t sm, int64_t len) {
     int par = 0;
     for (int64_t m = 1; m <= len; ++m) {
-      float* sv = seg + (size_t)m * st;
       lbm::launch_fused(c->d, c->tma(), par, 0, sm);
       lbm::launch_enthalpy_solve(c->d, par, sm);
       lbm::launch_enthalpy_commit(c->d, par, sm);
       par ^= 1;
-      lbm::launch_get_state(c->d, par, nullptr, sv, sm);
-      cudaMemcpyAsync(sv + 5 * n, c->d.fl, n * sizeof(float), cudaMemcpyDeviceToDevice, sm);
+      lbm::launch_temperature(c->d, par, segT + (size_t)m * n, sm);
+      cudaMemcpyAsync(segF + (size_t)m * n, c->d.fl, n * sizeof(float), cudaMemcpyDeviceToDevice,
+                      sm);
     }
     for (int64_t m = len - 1; m >= 0; --m) {
-      const float* s0 = seg + (size_t)m * st;
-      const float* s1 = seg + (size_t)(m + 1) * st;
-      lbm::adj_step(c->d, b, s1, s0 + 5 * n, s1 + 5 * n, sweeps, sm);
+      lbm::adj_step(c->d, b, segT + (size_t)(m + 1) * n, segF + (size_t)m * n,
+                    segF + (size_t)(m + 1) * n, sweeps, sm);
       std::swap(b.lamg, b.lamgpre);
     }
   };
@@ -1035,7 +1037,7 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
     const int64_t len = (j == ncp - 1) ? nsteps - first : K;
     if (len <= 0) continue;
     LBM_TRY(restore(cps + (size_t)j * st));
-    LBM_CUDA(cudaMemcpyAsync(seg, cps + (size_t)j * st, st * sizeof(float),
+    LBM_CUDA(cudaMemcpyAsync(segF, cps + (size_t)j * st + 5 * n, n * sizeof(float),
                              cudaMemcpyDeviceToDevice, c->stream));
     float* const lamg0 = b.lamg;
     float* const lamgpre0 = b.lamgpre;

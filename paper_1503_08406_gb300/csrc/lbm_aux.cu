@@ -169,23 +169,36 @@ __global__ void reduce_final_kernel(const double* partials, int nblocks, double*
   out[3] = t[5] > 0 ? t[4] / t[5] : 0.0;
 }
 
-__global__ void get_state_kernel(Dev d, int layout, float* f, float* g) {
+// f (9 planes), g (5 planes) and T = sum_i g_i (one plane) in the natural
+// layout; each output is optional
+__global__ void get_state_kernel(Dev d, int layout, float* f, float* g, float* T) {
   const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= d.n) return;
   const int y = (int)(s / d.nx), x = (int)(s - (long long)y * d.nx);
   const long long n = d.n;
-  float fv[9], gv[5];
-  if (is_wall(d, x, y)) {
-    for (int i = 0; i < 9; ++i) fv[i] = ld_f(d, i, s);
-    for (int i = 0; i < 5; ++i) gv[i] = ld_g(d, i, s);
-  } else {
-    gather_f(d, x, y, layout, fv);
-    gather_g(d, x, y, layout, gv);
-  }
-  if (f)
+  const bool wall = is_wall(d, x, y);
+  if (f) {
+    float fv[9];
+    if (wall)
+      for (int i = 0; i < 9; ++i) fv[i] = ld_f(d, i, s);
+    else
+      gather_f(d, x, y, layout, fv);
     for (int i = 0; i < 9; ++i) f[i * n + s] = fv[i];
-  if (g)
-    for (int i = 0; i < 5; ++i) g[i * n + s] = gv[i];
+  }
+  if (g || T) {
+    float gv[5];
+    if (wall)
+      for (int i = 0; i < 5; ++i) gv[i] = ld_g(d, i, s);
+    else
+      gather_g(d, x, y, layout, gv);
+    if (g)
+      for (int i = 0; i < 5; ++i) g[i * n + s] = gv[i];
+    if (T) {
+      float t = 0.f;
+      for (int i = 0; i < 5; ++i) t += gv[i];
+      T[s] = t;
+    }
+  }
 }
 
 __global__ void set_state_kernel(Dev d, const float* f, const float* g) {
@@ -227,7 +240,10 @@ void launch_reduce(const Dev& d, int layout, double* partials, double* out, int 
   reduce_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, out);
 }
 void launch_get_state(const Dev& d, int layout, float* f, float* g, cudaStream_t s) {
-  get_state_kernel<<<grid1(d.n, 256), 256, 0, s>>>(d, layout, f, g);
+  get_state_kernel<<<grid1(d.n, 256), 256, 0, s>>>(d, layout, f, g, nullptr);
+}
+void launch_temperature(const Dev& d, int layout, float* T, cudaStream_t s) {
+  get_state_kernel<<<grid1(d.n, 256), 256, 0, s>>>(d, layout, nullptr, nullptr, T);
 }
 void launch_set_state(const Dev& d, const float* f, const float* g, cudaStream_t s) {
   set_state_kernel<<<grid1(d.n, 256), 256, 0, s>>>(d, f, g);

@@ -315,30 +315,36 @@ void launch_reduce(const Dev& d, int parity, double* partials, double* out, int 
                    cudaStream_t s);
 int reduce_blocks(const Dev& d);
 void launch_get_state(const Dev& d, int parity, float* f, float* g, cudaStream_t s);
+// T = sum_i g_i per node, natural layout
+void launch_temperature(const Dev& d, int parity, float* T, cudaStream_t s);
 void launch_set_state(const Dev& d, const float* f, const float* g, cudaStream_t s);
 // Adjoint of the conduction step (lbm_adjoint.cu); all buffers n floats unless noted
 struct AdjBuffers {
   float* a;          // a = phi dT / (sigma St)
   float* lamg;       // 5 n: adjoint of the populations after the step being reversed
   float* lamf;       // adjoint of f_l after the step (in), before it (out)
-  float* lamf_tot;   // adjoint of f_l after the step, the source's share included
-  float* ls;         // source adjoint sum_i w~_i lam_g_i(y + e_i)
+  float* lamf_tot;   // band nodes: adjoint of f_l after the step, the source's share included
   float* cinv;       // 1/(T_l - T_s + a) on unclamped nodes, else 0
-  float* mu0;        // fixed-point adjoint, ping-pong
+  float* nu;         // band nodes: c mu, mu the fixed point's adjoint
+  float* mu0;        // mu in global memory (wide bands), ping-pong
   float* mu1;
   float* lamgpre;    // 5 n: adjoint of the populations before the step
   float* lama;       // accumulated adjoint of a
   float* lamtw;      // ny: accumulated adjoint of the left wall profile
   float* At;         // 25: transposed collision matrix (u = 0)
   int* list;         // n: the step's unclamped nodes
+  int* pos;          // n: a band node's place in the list
   int* count;        // their number (kept at 0 between steps)
 };
 void adj_seed(const Dev& d, float* lamf, float* lamg, float* a, cudaStream_t s);
 void adj_objective(const Dev& d, const float* fl, double* out, cudaStream_t s);
 // one step of the reverse sweep: from b.lamg / b.lamf (after the step) to
-// b.lamgpre / b.lamf (before it); the caller swaps b.lamg and b.lamgpre
-void adj_step(const Dev& d, const AdjBuffers& b, const float* g1, const float* f0, const float* f1,
+// b.lamgpre / b.lamf (before it), given T and f_l after the step and f_l
+// before it; the caller swaps b.lamg and b.lamgpre
+void adj_step(const Dev& d, const AdjBuffers& b, const float* T1, const float* f0, const float* f1,
               int mu_sweeps, cudaStream_t s);
+// once per process before adj_step: the band kernel's shared-memory opt-in
+bool adj_init();
 void launch_validate(const Dev& d, const float* phi, const float* K, const float* T0,
                      const float* fl0, int* bad, cudaStream_t s);
 
