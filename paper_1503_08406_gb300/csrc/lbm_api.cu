@@ -928,29 +928,29 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
   if (!lbm::adj_init()) return LBM_ERR_CUDA;
   DevMem mem;
   float* cps = mem.get((size_t)ncp * st);
-  float* segT = mem.get((size_t)(K + 1) * n);   // T after each step of a segment
-  float* segF = mem.get((size_t)(K + 1) * n);   // f_l at the segment's start and after each step
+  // per step of a segment (index m: the state after its m-th step): f_l (m = 0:
+  // the segment's start), the clamp state c, the band list and its length
+  float* segF = mem.get((size_t)(K + 1) * n);
+  float* segC = mem.get((size_t)(K + 1) * n);
+  int* segL = reinterpret_cast<int*>(mem.get((size_t)(K + 1) * n));
+  int* segN = reinterpret_cast<int*>(mem.get((size_t)(K + 1)));
   float* fin = mem.get(st);
   lbm::AdjBuffers b;
   b.a = mem.get(n);
   b.lamg = mem.get(5 * n);
   b.lamf = mem.get(n);
-  b.lamf_tot = mem.get(n);
   b.nu = mem.get(n);
-  b.cinv = mem.get(n);
+  b.rhs = mem.get(n);
   b.mu0 = mem.get(n);
   b.mu1 = mem.get(n);
   b.lamgpre = mem.get(5 * n);
   b.lama = mem.get(n);
   b.lamtw = mem.get((size_t)c->d.ny);
   b.At = mem.get(25);
-  b.list = reinterpret_cast<int*>(mem.get(n));
   b.pos = reinterpret_cast<int*>(mem.get(n));
-  b.count = reinterpret_cast<int*>(mem.get(1));
-  double* dJ = reinterpret_cast<double*>(mem.get(2));
-  if (!cps || !segT || !segF || !fin || !b.a || !b.lamg || !b.lamf || !b.lamf_tot || !b.nu ||
-      !b.cinv || !b.mu0 || !b.mu1 || !b.lamgpre || !b.lama || !b.lamtw || !b.At || !b.list ||
-      !b.pos || !b.count || !dJ)
+  double* dJ = reinterpret_cast<double*>(mem.get(2 * 129));
+  if (!cps || !segF || !segC || !segL || !segN || !fin || !b.a || !b.lamg || !b.lamf || !b.nu ||
+      !b.rhs || !b.mu0 || !b.mu1 || !b.lamgpre || !b.lama || !b.lamtw || !b.At || !b.pos || !dJ)
     return LBM_ERR_OOM;
   // transposed collision matrix with u = 0: g+ = A g,
   // A = N^-1 [(I - Theta) N + Theta e 1^T], e = (1, 0, 0, varpi, 0), Eq. (32)-(37)
@@ -996,7 +996,6 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
   lbm::adj_seed(c->d, b.lamf, b.lamg, b.a, c->stream);
   LBM_CUDA(cudaMemsetAsync(b.lama, 0, n * sizeof(float), c->stream));
   LBM_CUDA(cudaMemsetAsync(b.lamtw, 0, c->d.ny * sizeof(float), c->stream));
-  LBM_CUDA(cudaMemsetAsync(b.count, 0, sizeof(int), c->stream));
   LBM_CUDA(cudaMemsetAsync(b.mu0, 0, n * sizeof(float), c->stream));
   LBM_CUDA(cudaMemsetAsync(b.mu1, 0, n * sizeof(float), c->stream));
   // One segment after its checkpoint is restored (parity 0): the len steps
@@ -1005,18 +1004,20 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
   // parity) and replayed.
   auto record_segment = [&](cudaStream_t sm, int64_t len) {
     int par = 0;
+    cudaMemsetAsync(segN, 0, (size_t)(K + 1) * sizeof(int), sm);
     for (int64_t m = 1; m <= len; ++m) {
       lbm::launch_fused(c->d, c->tma(), par, 0, sm);
       lbm::launch_enthalpy_solve(c->d, par, sm);
       lbm::launch_enthalpy_commit(c->d, par, sm);
       par ^= 1;
-      lbm::launch_temperature(c->d, par, segT + (size_t)m * n, sm);
+      lbm::adj_clamp(c->d, par, b.a, segC + (size_t)m * n, segL + (size_t)m * n, segN + m, sm);
       cudaMemcpyAsync(segF + (size_t)m * n, c->d.fl, n * sizeof(float), cudaMemcpyDeviceToDevice,
                       sm);
     }
     for (int64_t m = len - 1; m >= 0; --m) {
-      lbm::adj_step(c->d, b, segT + (size_t)(m + 1) * n, segF + (size_t)m * n,
-                    segF + (size_t)(m + 1) * n, sweeps, sm);
+      const size_t o = (size_t)(m + 1) * n;
+      lbm::adj_step(c->d, b, segC + o, segL + o, segN + m + 1, segF + (size_t)m * n, segF + o,
+                    sweeps, sm);
       std::swap(b.lamg, b.lamgpre);
     }
   };

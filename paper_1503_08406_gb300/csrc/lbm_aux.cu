@@ -10,21 +10,6 @@ __device__ __forceinline__ bool flow_active(const Dev& d, int x, int y) {
   return !is_wall(d, x, y) && d.fl[(long long)y * d.nx + x] >= d.f_act;
 }
 
-// g_i of non-wall node (x, y) in the given layout
-__device__ __forceinline__ void gather_g(const Dev& d, int x, int y, int layout, float g[5]) {
-  const long long n = d.n, s = (long long)y * d.nx + x;
-  (void)n;
-  g[0] = ld_g(d, 0, s);
-  for (int i = 1; i < 5; ++i) {
-    if (layout == 0) {
-      g[i] = ld_g(d, i, s);
-    } else {
-      const int sx = wrapx(d, x - ex9(i)), sy = wrapy(d, y - ey9(i));
-      g[i] = ld_g(d, opp5(i), (long long)sy * d.nx + sx);
-    }
-  }
-}
-
 // f_i of node (x, y): nodes without flow hold theirs in their own slots
 __device__ __forceinline__ void gather_f(const Dev& d, int x, int y, int layout, float f[9]) {
   const long long n = d.n, s = (long long)y * d.nx + x;

@@ -256,6 +256,21 @@ __device__ __forceinline__ int wrapy(const Dev& d, int y) {
   y %= d.ny;
   return y < 0 ? y + d.ny : y;
 }
+
+// g_i of non-wall node (x, y) in the given layout (AA pattern: after an odd
+// step a node's populations sit in its upstream neighbours' opposite slots)
+__device__ __forceinline__ void gather_g(const Dev& d, int x, int y, int layout, float g[5]) {
+  const long long s = (long long)y * d.nx + x;
+  g[0] = ld_g(d, 0, s);
+  for (int i = 1; i < 5; ++i) {
+    if (layout == 0) {
+      g[i] = ld_g(d, i, s);
+    } else {
+      const int sx = wrapx(d, x - ex9(i)), sy = wrapy(d, y - ey9(i));
+      g[i] = ld_g(d, opp5(i), (long long)sy * d.nx + sx);
+    }
+  }
+}
 __device__ __forceinline__ bool is_wall(const Dev& d, int x, int y) {
   return (d.wall_l && x == 0) || (d.wall_r && x == d.nx - 1) || (d.wall_b && y == 0) ||
          (d.wall_t && y == d.ny - 1);
@@ -323,26 +338,29 @@ struct AdjBuffers {
   float* a;          // a = phi dT / (sigma St)
   float* lamg;       // 5 n: adjoint of the populations after the step being reversed
   float* lamf;       // adjoint of f_l after the step (in), before it (out)
-  float* lamf_tot;   // band nodes: adjoint of f_l after the step, the source's share included
-  float* cinv;       // 1/(T_l - T_s + a) on unclamped nodes, else 0
   float* nu;         // band nodes: c mu, mu the fixed point's adjoint
+  float* rhs;        // band nodes (wide bands): right-hand side of mu's equation
   float* mu0;        // mu in global memory (wide bands), ping-pong
   float* mu1;
   float* lamgpre;    // 5 n: adjoint of the populations before the step
   float* lama;       // accumulated adjoint of a
   float* lamtw;      // ny: accumulated adjoint of the left wall profile
   float* At;         // 25: transposed collision matrix (u = 0)
-  int* list;         // n: the step's unclamped nodes
-  int* pos;          // n: a band node's place in the list
-  int* count;        // their number (kept at 0 between steps)
+  int* pos;          // n: a band node's place in the band list
 };
 void adj_seed(const Dev& d, float* lamf, float* lamg, float* a, cudaStream_t s);
+// J into out[0]; out holds 129 doubles (the rest: partial sums)
 void adj_objective(const Dev& d, const float* fl, double* out, cudaStream_t s);
-// one step of the reverse sweep: from b.lamg / b.lamf (after the step) to
-// b.lamgpre / b.lamf (before it), given T and f_l after the step and f_l
-// before it; the caller swaps b.lamg and b.lamgpre
-void adj_step(const Dev& d, const AdjBuffers& b, const float* T1, const float* f0, const float* f1,
-              int mu_sweeps, cudaStream_t s);
+// after a recomputed step, populations in `layout`: c = 1/(T_l - T_s + a) on
+// the unclamped non-wall nodes (0 elsewhere) and their list, appended at
+// list[*count] (count zeroed by the caller)
+void adj_clamp(const Dev& d, int layout, const float* a, float* cinv, int* list, int* count,
+               cudaStream_t s);
+// one step of the reverse sweep, given that step's clamp state and f_l before
+// and after it: from b.lamg / b.lamf (after the step) to b.lamgpre / b.lamf
+// (before it); the caller swaps b.lamg and b.lamgpre
+void adj_step(const Dev& d, const AdjBuffers& b, const float* cinv, const int* list,
+              const int* count, const float* f0, const float* f1, int mu_sweeps, cudaStream_t s);
 // once per process before adj_step: the band kernel's shared-memory opt-in
 bool adj_init();
 void launch_validate(const Dev& d, const float* phi, const float* K, const float* T0,
