@@ -168,23 +168,27 @@ int lbm_kernel_variant(const lbm_ctx* c);
  * NULL) receive the choice (tiles_per_cta 0 for the ordinary-load kernel). */
 int lbm_autotune(lbm_ctx* c, int trial_steps, int32_t* variant, int32_t* tiles_per_cta);
 
-/* Adjoint of the conduction step.  Runs nsteps
- * steps forward from the context's current state and returns the melted
- * fraction J (mean f_l over non-wall nodes) after them, with its gradient with
- * respect to the porosity field (d_phi, nx*ny) and to the left wall's
- * temperature profile (d_wall_T_left, ny), by the discrete adjoint of the step
- * (the reverse of the wall extrapolation, collision, streaming, latent source
- * and, by the implicit function theorem, the enthalpy fixed point; the clamp of
- * Eq. (42) differentiates to 0 or 1).  States are kept every checkpoint_every
- * steps (0: sqrt(nsteps)) and the steps between recomputed (a CUDA graph per
- * segment); Jacobi sweeps solve the fixed point's adjoint per step until the
- * largest change is within 4e-7 of the value, at most mu_sweeps (0: 64).  The context ends
- * where the forward run left it (nsteps further on).  Covers: no flow
- * (flow = 0), periodic in y with wall columns at x = 0 (Dirichlet, the
- * profile) and x = nx - 1 (Dirichlet or adiabatic), FP32 storage, one thermal
- * diffusivity; LBM_ERR_INVALID_ARG otherwise.  Allocates its buffers
- * (checkpoints and one segment of states) with cudaMalloc and synchronises.
- * device_ptrs: d_phi and d_wall_T_left are device (1) or host (0) pointers. */
+/* Adjoint of the conduction step.  Runs nsteps steps forward from the
+ * context's current state and returns the melted fraction J (mean f_l over
+ * non-wall nodes) after them, with its gradient with respect to the porosity
+ * field (d_phi, nx*ny) and to the left wall's temperature profile
+ * (d_wall_T_left, ny), by the discrete adjoint of the step (the reverse of the
+ * wall extrapolation, collision, streaming, latent source and, by the implicit
+ * function theorem, the enthalpy fixed point; the clamp of Eq. (42)
+ * differentiates to 1 on the nodes with 0 < f_l < 1 after the step, else 0).
+ * The reverse sweep needs f_l after every step.  checkpoint_every = 0: kept
+ * for all steps (4 bytes per node and step) when that takes at most half the
+ * free device memory, else as for sqrt(nsteps); checkpoint_every = K > 0: the
+ * whole state kept every K steps and the steps between recomputed (a CUDA
+ * graph per segment).  All choices give the same result.  Jacobi sweeps solve
+ * the fixed point's adjoint per step until the largest change is within 4e-7
+ * of the value, at most mu_sweeps (0: 64).  The context ends where the forward
+ * run left it (nsteps further on).  Covers: no flow (flow = 0), periodic in y
+ * with wall columns at x = 0 (Dirichlet, the profile) and x = nx - 1
+ * (Dirichlet or adiabatic), FP32 storage, one thermal diffusivity;
+ * LBM_ERR_INVALID_ARG otherwise.  Allocates its buffers with cudaMalloc
+ * (LBM_ERR_OOM if that fails) and synchronises.  device_ptrs: d_phi and
+ * d_wall_T_left are device (1) or host (0) pointers. */
 int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32_t mu_sweeps,
                      float* d_phi, float* d_wall_T_left, double* J, int device_ptrs);
 

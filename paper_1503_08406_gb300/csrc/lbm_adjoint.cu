@@ -39,13 +39,12 @@ __device__ __forceinline__ int adj_nb(const Dev& d, int x, int y, int dx, int dy
 
 __device__ __forceinline__ float wt(const Dev& d, int i) { return i == 0 ? d.wt0 : d.wt1; }
 
-// The clamp state of each step is taken while the step is recomputed
-// (adj_clamp_kernel, on the state after it).  Each reversed step is then two
-// kernels.  adj_band_kernel (one CTA) solves the fixed point's adjoint on the
-// unclamped nodes, a band along the front, and leaves nu = c mu there.
-// adj_full_kernel passes over the whole lattice once: with
-// lam_g+_i(x) = lam_g'_i(x + e_i) + nu(x + e_i) and S(y) = sum_i w~_i lam_g+_i(y)
-// (the source adjoint of step F, the fixed point's share included),
+// Each reversed step is two kernels.  adj_band_kernel (one CTA) solves the
+// fixed point's adjoint on the unclamped nodes, a band along the front, and
+// leaves nu = c mu there (0 elsewhere).  adj_full_kernel passes over the whole
+// lattice once: with lam_g+_i(x) = lam_g'_i(x + e_i) + nu(x + e_i) and
+// S(y) = sum_i w~_i lam_g+_i(y) (the source adjoint of step F, the fixed
+// point's share included),
 //   lam_gpre = A^T lam_g+ per node
 //   lam_f(n)(y) = a(y) S(y)                       (wall: lam_f')
 //   lam_a(y) += -(f(n+1) - f(n))(y) S(y)
@@ -53,30 +52,23 @@ __device__ __forceinline__ float wt(const Dev& d, int i) { return i == 0 ? d.wt0
 //          Dirichlet value's adjoint is sum_i w~_i lam_gpre_i(x_b); the wall
 //          nodes' own populations do not reach the next step (the
 //          extrapolation rewrites them).
+// The unclamped nodes of a step are the non-wall nodes with 0 < f_l < 1 after
+// it (the solver converges to f = z there, and clamps elsewhere); the full
+// pass of one reversed step lists them for the next (its f(n) is the next
+// one's f(n+1)).
 
-// After a recomputed step (populations in `layout`, f_l in d.fl): c per node
-// and the list of unclamped non-wall nodes.
-__global__ void adj_clamp_kernel(Dev d, int layout, const float* a, float* cinv, int* list,
-                                 int* count) {
+__device__ __forceinline__ bool band_node(const Dev& d, const float* f, int t) {
+  if (t < 0) return false;
+  const int x = t % d.nx;
+  const float v = f[t];
+  return x != 0 && x != d.nx - 1 && v > 0.f && v < 1.f;
+}
+
+// the band of the state with liquid fraction f, appended at list[*count]
+__global__ void adj_list_kernel(Dev d, const float* f, int* list, int* count) {
   const int s = blockIdx.x * AB + threadIdx.x;
   if (s >= (int)d.n) return;
-  const int y = s / d.nx, x = s - y * d.nx;
-  float c = 0.f;
-  if (x != 0 && x != d.nx - 1) {
-    float g[5];
-    gather_g(d, x, y, layout, g);
-    float T = 0.f;
-#pragma unroll
-    for (int i = 0; i < 5; ++i) T += g[i];
-    const float as = a[s];
-    const float inv = 1.f / (d.dTt + as);
-    const float z = (T + as * d.fl[s] - d.T_s) * inv;
-    if (z > 0.f && z < 1.f) {
-      c = inv;
-      list[atomicAdd(count, 1)] = s;
-    }
-  }
-  cinv[s] = c;
+  if (band_node(d, f, s)) list[atomicAdd(count, 1)] = s;
 }
 
 // The fixed point's adjoint on the band: right-hand side
@@ -85,15 +77,12 @@ __global__ void adj_clamp_kernel(Dev d, int layout, const float* a, float* cinv,
 // its value or after max_sweeps.  Up to BAND_CAP band nodes sweep in shared
 // memory (each node's coefficients and its neighbours' places in the list
 // staged once); a wider band sweeps in global memory.  Jacobi makes the
-// result independent of the list's order.
+// result independent of the list's order.  First clears nu on the previous
+// band (old_list) and empties that list for the full pass to refill.
 constexpr float MU_RTOL = 4e-7f;
 constexpr int BAND_CAP = 4096;
 constexpr int BAND_THREADS = 1024;
 constexpr int BAND_SMEM = BAND_CAP * (int)(sizeof(float4) + sizeof(ushort4) + 5 * sizeof(float));
-
-__device__ __forceinline__ bool in_band(const float* cinv, int t) {
-  return t >= 0 && cinv[t] != 0.f;
-}
 
 // right-hand side of mu's equation at band node s
 __device__ __forceinline__ float band_rhs(const Dev& d, const AdjBuffers& b, int s) {
@@ -109,10 +98,13 @@ __device__ __forceinline__ float band_rhs(const Dev& d, const AdjBuffers& b, int
 }
 
 __global__ void __launch_bounds__(BAND_THREADS) adj_band_kernel(Dev d, AdjBuffers b,
-                                                                const float* cinv, const int* list,
-                                                                const int* count, int max_sweeps) {
+                                                                const float* f1, const int* list,
+                                                                const int* count,
+                                                                const int* old_list,
+                                                                int* old_count, int max_sweeps) {
   extern __shared__ float4 band_smem[];
-  const int cnt = *count;
+  const int cnt = *count, ocnt = *old_count;
+  for (int j = threadIdx.x; j < ocnt; j += blockDim.x) b.nu[old_list[j]] = 0.f;
   if (cnt <= BAND_CAP) {
     float4* ct = band_smem;                                    // c of the 4 neighbours
     ushort4* ix = reinterpret_cast<ushort4*>(ct + BAND_CAP);   // their places in the list
@@ -131,14 +123,14 @@ __global__ void __launch_bounds__(BAND_THREADS) adj_band_kernel(Dev d, AdjBuffer
 #pragma unroll
       for (int i = 1; i < 5; ++i) {
         const int t = adj_nb(d, x, y, ex9(i), ey9(i));
-        const bool on = in_band(cinv, t);
-        c4[i - 1] = on ? cinv[t] : 0.f;
+        const bool on = band_node(d, f1, t);
+        c4[i - 1] = on ? 1.f / (d.dTt + b.a[t]) : 0.f;
         i4[i - 1] = (unsigned short)(on ? b.pos[t] : j);
       }
       ct[j] = make_float4(c4[0], c4[1], c4[2], c4[3]);
       ix[j] = make_ushort4(i4[0], i4[1], i4[2], i4[3]);
       const float as = b.a[s];
-      const float den = 1.f - as * (1.f - d.wt0) * cinv[s];
+      const float den = 1.f - as * (1.f - d.wt0) / (d.dTt + as);
       rhs[j] = band_rhs(d, b, s) / den;
       kk[j] = as * d.wt1 / den;
       mu[j] = 0.f;
@@ -162,16 +154,15 @@ __global__ void __launch_bounds__(BAND_THREADS) adj_band_kernel(Dev d, AdjBuffer
     }
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
       const int s = list[j];
-      b.nu[s] = cinv[s] * mu[j];
+      b.nu[s] = mu[j] / (d.dTt + b.a[s]);
     }
   } else {
     float* mu = b.mu0;
     float* mo = b.mu1;
-    float* rhs = b.rhs;
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
       const int s = list[j];
       const float as = b.a[s];
-      rhs[s] = band_rhs(d, b, s) / (1.f - as * (1.f - d.wt0) * cinv[s]);
+      b.rhs[s] = band_rhs(d, b, s) / (1.f - as * (1.f - d.wt0) / (d.dTt + as));
       mu[s] = 0.f;
     }
     __syncthreads();
@@ -184,10 +175,10 @@ __global__ void __launch_bounds__(BAND_THREADS) adj_band_kernel(Dev d, AdjBuffer
 #pragma unroll
         for (int i = 1; i < 5; ++i) {
           const int t = adj_nb(d, x, y, ex9(i), ey9(i));
-          nb += in_band(cinv, t) ? cinv[t] * mu[t] : 0.f;
+          nb += band_node(d, f1, t) ? mu[t] / (d.dTt + b.a[t]) : 0.f;
         }
         const float as = b.a[s];
-        const float v = rhs[s] - as * d.wt1 / (1.f - as * (1.f - d.wt0) * cinv[s]) * nb;
+        const float v = b.rhs[s] - as * d.wt1 / (1.f - as * (1.f - d.wt0) / (d.dTt + as)) * nb;
         moved |= fabsf(v - mu[s]) > MU_RTOL * fabsf(v);
         mo[s] = v;
       }
@@ -199,19 +190,21 @@ __global__ void __launch_bounds__(BAND_THREADS) adj_band_kernel(Dev d, AdjBuffer
     }
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
       const int s = list[j];
-      b.nu[s] = cinv[s] * mu[s];
+      b.nu[s] = mu[s] / (d.dTt + b.a[s]);
     }
   }
+  __syncthreads();
+  if (threadIdx.x == 0) *old_count = 0;
 }
 
 // lam_g+ of node (x, y) and A^T of it
-__device__ __forceinline__ void pre_pops(const Dev& d, const AdjBuffers& b, const float* cinv,
-                                         int x, int y, float lp[5], float out[5]) {
+__device__ __forceinline__ void pre_pops(const Dev& d, const AdjBuffers& b, int x, int y,
+                                         float lp[5], float out[5]) {
   const int n = (int)d.n;
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
     const int t = adj_nb(d, x, y, ex9(i), ey9(i));
-    lp[i] = (t >= 0) ? b.lamg[i * n + t] + (cinv[t] != 0.f ? b.nu[t] : 0.f) : 0.f;
+    lp[i] = (t >= 0) ? b.lamg[i * n + t] + b.nu[t] : 0.f;
   }
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
@@ -222,14 +215,14 @@ __device__ __forceinline__ void pre_pops(const Dev& d, const AdjBuffers& b, cons
   }
 }
 
-__global__ void adj_full_kernel(Dev d, AdjBuffers b, const float* cinv, const float* f0,
-                                const float* f1) {
+__global__ void adj_full_kernel(Dev d, AdjBuffers b, const float* f0, const float* f1,
+                                int* next_list, int* next_count) {
   const int s = blockIdx.x * AB + threadIdx.x;
   if (s >= (int)d.n) return;
   const int y = s / d.nx, x = s - y * d.nx;
   const int n = (int)d.n;
   float lp[5], pre[5];
-  pre_pops(d, b, cinv, x, y, lp, pre);
+  pre_pops(d, b, x, y, lp, pre);
   if (x == 0 || x == d.nx - 1) {
     if (x == 0 && d.bc[0] == 1) {
       float wl = 0.f;
@@ -245,7 +238,7 @@ __global__ void adj_full_kernel(Dev d, AdjBuffers b, const float* cinv, const fl
   for (int side = 0; side < 2; ++side) {
     if (x != (side ? d.nx - 2 : 1)) continue;
     float lw[5], pw[5];
-    pre_pops(d, b, cinv, side ? d.nx - 1 : 0, y, lw, pw);
+    pre_pops(d, b, side ? d.nx - 1 : 0, y, lw, pw);
     float wl = 0.f;
 #pragma unroll
     for (int i = 0; i < 5; ++i) wl += wt(d, i) * pw[i];
@@ -258,8 +251,28 @@ __global__ void adj_full_kernel(Dev d, AdjBuffers b, const float* cinv, const fl
   float S = 0.f;
 #pragma unroll
   for (int i = 0; i < 5; ++i) S += wt(d, i) * lp[i];
+  const float fa = f0[s];
   b.lamf[s] = b.a[s] * S;
-  b.lama[s] += -(f1[s] - f0[s]) * S;
+  b.lama[s] += -(f1[s] - fa) * S;
+  if (fa > 0.f && fa < 1.f) next_list[atomicAdd(next_count, 1)] = s;
+}
+
+// Forward runs that keep every step's f_l: copies d.fl to base + k n, k the
+// counter at *ctr, which the last block to finish advances (no block waits).
+__global__ void adj_save_kernel(Dev d, float* base, unsigned* ctr, unsigned* done) {
+  const unsigned k = *ctr;
+  const long long n = d.n;
+  float* dst = base + (long long)k * n;
+  for (long long s = blockIdx.x * (long long)AB + threadIdx.x; s < n; s += (long long)gridDim.x * AB)
+    dst[s] = d.fl[s];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(done, 1u) == gridDim.x - 1) {
+      *done = 0;
+      *ctr = k + 1;
+    }
+  }
 }
 
 // J = mean f_l over non-wall nodes: FP64 partial sums per row block, then
@@ -318,15 +331,21 @@ bool adj_init() {
                               BAND_SMEM) == cudaSuccess;
 }
 
-void adj_clamp(const Dev& d, int layout, const float* a, float* cinv, int* list, int* count,
-               cudaStream_t s) {
-  adj_clamp_kernel<<<blocks(d.n), AB, 0, s>>>(d, layout, a, cinv, list, count);
+void adj_list(const Dev& d, const float* f, int* list, int* count, cudaStream_t s) {
+  adj_list_kernel<<<blocks(d.n), AB, 0, s>>>(d, f, list, count);
 }
 
-void adj_step(const Dev& d, const AdjBuffers& b, const float* cinv, const int* list,
-              const int* count, const float* f0, const float* f1, int mu_sweeps, cudaStream_t s) {
-  adj_band_kernel<<<1, BAND_THREADS, BAND_SMEM, s>>>(d, b, cinv, list, count, mu_sweeps);
-  adj_full_kernel<<<blocks(d.n), AB, 0, s>>>(d, b, cinv, f0, f1);
+void adj_save(const Dev& d, float* base, unsigned* ctr, cudaStream_t s) {
+  long long nb = (d.n + 4LL * AB - 1) / (4LL * AB);
+  if (nb > 4 * 152) nb = 4 * 152;
+  adj_save_kernel<<<(unsigned)nb, AB, 0, s>>>(d, base, ctr, ctr + 1);
+}
+
+void adj_step(const Dev& d, const AdjBuffers& b, const float* f0, const float* f1, int* list,
+              int* count, int* old_list, int* old_count, int mu_sweeps, cudaStream_t s) {
+  adj_band_kernel<<<1, BAND_THREADS, BAND_SMEM, s>>>(d, b, f1, list, count, old_list, old_count,
+                                                     mu_sweeps);
+  adj_full_kernel<<<blocks(d.n), AB, 0, s>>>(d, b, f0, f1, old_list, old_count);
 }
 
 }  // namespace lbm

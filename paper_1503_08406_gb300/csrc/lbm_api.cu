@@ -455,7 +455,8 @@ static bool capture_streams(lbm_ctx* c) {
 // k's enthalpy solve and commit (which touch only nodes within eight nodes of a
 // listed tile); the tiles near the front run after the commit.  Everything
 // forked onto the second stream joins back before the last kernel.
-static int capture_body(lbm_ctx* c, int steps) {
+static int capture_body(lbm_ctx* c, int steps, float* keep_base = nullptr,
+                        unsigned* keep_ctr = nullptr) {
   int nl = 0;
   for (int k = 0; k < steps; ++k) {
     const int par = k & 1;
@@ -476,6 +477,10 @@ static int capture_body(lbm_ctx* c, int steps) {
     lbm::launch_enthalpy_solve(c->d, par, c->cap);
     lbm::launch_enthalpy_commit(c->d, par, c->cap);
     nl += 2;
+    if (keep_base) {
+      lbm::adj_save(c->d, keep_base, keep_ctr, c->cap);   // f_l after the step
+      nl += 1;
+    }
   }
   return nl;
 }
@@ -913,6 +918,23 @@ struct DevMem {
 
 }  // namespace
 
+// A graph of `steps` (even) steps from parity 0 like capture(), each step
+// followed by lbm::adj_save of f_l.
+static cudaGraphExec_t capture_keep(lbm_ctx* c, int steps, float* base, unsigned* ctr) {
+  if (!capture_streams(c)) return nullptr;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  capture_body(c, steps, base, ctr);
+  if (cudaStreamEndCapture(c->cap, &g) != cudaSuccess || !g) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return instantiate(g);
+}
+
 int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32_t mu_sweeps,
                      float* d_phi, float* d_wall_T_left, double* J, int device_ptrs) {
   if (!c || nsteps < 1 || checkpoint_every < 0 || mu_sweeps < 0 || !d_phi || !d_wall_T_left || !J)
@@ -920,21 +942,26 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
   const lbm_params& p = c->p;
   if (p.flow || c->timing || p.storage != LBM_STORAGE_FP32 || c->d.alpha_var) return LBM_ERR_INVALID_ARG;
   if (!c->d.per_y || c->d.per_x || p.bc[0] != LBM_BC_DIRICHLET) return LBM_ERR_INVALID_ARG;
-  const int64_t K = checkpoint_every > 0 ? checkpoint_every
-                                         : (int64_t)ceil(sqrt((double)nsteps));
   const int sweeps = mu_sweeps > 0 ? mu_sweeps : 64;
   const size_t n = (size_t)c->d.n, st = 6 * n;   // a checkpoint: g (5 planes) and f_l
-  const int64_t ncp = nsteps / K + 1;
   if (!lbm::adj_init()) return LBM_ERR_CUDA;
+  // Keep f_l of every step when that takes at most half the free memory;
+  // otherwise (or when asked for a spacing) keep the whole state every K steps
+  // and recompute the steps between.
+  size_t free_b = 0, total_b = 0;
+  LBM_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  const bool keep_all =
+      checkpoint_every == 0 && (double)(nsteps + 1) * n * sizeof(float) <= 0.5 * (double)free_b;
+  const int64_t K = keep_all ? nsteps
+                    : checkpoint_every > 0 ? checkpoint_every
+                                           : (int64_t)ceil(sqrt((double)nsteps));
+  const int64_t ncp = keep_all ? 1 : nsteps / K + 1;
   DevMem mem;
-  float* cps = mem.get((size_t)ncp * st);
-  // per step of a segment (index m: the state after its m-th step): f_l (m = 0:
-  // the segment's start), the clamp state c, the band list and its length
-  float* segF = mem.get((size_t)(K + 1) * n);
-  float* segC = mem.get((size_t)(K + 1) * n);
-  int* segL = reinterpret_cast<int*>(mem.get((size_t)(K + 1) * n));
-  int* segN = reinterpret_cast<int*>(mem.get((size_t)(K + 1)));
-  float* fin = mem.get(st);
+  // f_l per step: all of them (keep_all), else those of one segment (index m:
+  // after the segment's m-th step; m = 0: its start)
+  float* flS = mem.get((size_t)((keep_all ? nsteps : K) + 1) * n);
+  float* cps = keep_all ? nullptr : mem.get((size_t)ncp * st);
+  float* fin = keep_all ? nullptr : mem.get(st);
   lbm::AdjBuffers b;
   b.a = mem.get(n);
   b.lamg = mem.get(5 * n);
@@ -948,9 +975,13 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
   b.lamtw = mem.get((size_t)c->d.ny);
   b.At = mem.get(25);
   b.pos = reinterpret_cast<int*>(mem.get(n));
+  int* lists[2] = {reinterpret_cast<int*>(mem.get(n)), reinterpret_cast<int*>(mem.get(n))};
+  int* counts = reinterpret_cast<int*>(mem.get(2));
+  unsigned* ctr = reinterpret_cast<unsigned*>(mem.get(2));
   double* dJ = reinterpret_cast<double*>(mem.get(2 * 129));
-  if (!cps || !segF || !segC || !segL || !segN || !fin || !b.a || !b.lamg || !b.lamf || !b.nu ||
-      !b.rhs || !b.mu0 || !b.mu1 || !b.lamgpre || !b.lama || !b.lamtw || !b.At || !b.pos || !dJ)
+  if (!flS || (!keep_all && (!cps || !fin)) || !b.a || !b.lamg || !b.lamf || !b.nu || !b.rhs ||
+      !b.mu0 || !b.mu1 || !b.lamgpre || !b.lama || !b.lamtw || !b.At || !b.pos || !lists[0] ||
+      !lists[1] || !counts || !ctr || !dJ)
     return LBM_ERR_OOM;
   // transposed collision matrix with u = 0: g+ = A g,
   // A = N^-1 [(I - Theta) N + Theta e 1^T], e = (1, 0, 0, varpi, 0), Eq. (32)-(37)
@@ -981,94 +1012,141 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
     LBM_TRY(lbm_set_state(c, nullptr, src, src + 5 * n, 1));
     return LBM_OK;
   };
-  const int64_t steps0 = c->steps;
-  // forward, keeping a state every K steps
-  LBM_TRY(save(cps));
-  for (int64_t j = 1; j < ncp; ++j) {
-    LBM_TRY(lbm_step(c, K));
-    LBM_TRY(save(cps + (size_t)j * st));
-  }
-  const int64_t done = (ncp - 1) * K;
-  if (nsteps > done) LBM_TRY(lbm_step(c, nsteps - done));
-  LBM_TRY(save(fin));
-  lbm::adj_objective(c->d, fin + 5 * n, dJ, c->stream);
-  // reverse sweep, one segment at a time, its states recomputed from the checkpoint
-  lbm::adj_seed(c->d, b.lamf, b.lamg, b.a, c->stream);
-  LBM_CUDA(cudaMemsetAsync(b.lama, 0, n * sizeof(float), c->stream));
-  LBM_CUDA(cudaMemsetAsync(b.lamtw, 0, c->d.ny * sizeof(float), c->stream));
-  LBM_CUDA(cudaMemsetAsync(b.mu0, 0, n * sizeof(float), c->stream));
-  LBM_CUDA(cudaMemsetAsync(b.mu1, 0, n * sizeof(float), c->stream));
-  // One segment after its checkpoint is restored (parity 0): the len steps
-  // forward, each state kept, then the len reverse steps; the same launches
-  // for every whole segment, so they are captured once per (len, buffer
-  // parity) and replayed.
-  auto record_segment = [&](cudaStream_t sm, int64_t len) {
-    int par = 0;
-    cudaMemsetAsync(segN, 0, (size_t)(K + 1) * sizeof(int), sm);
-    for (int64_t m = 1; m <= len; ++m) {
-      lbm::launch_fused(c->d, c->tma(), par, 0, sm);
-      lbm::launch_enthalpy_solve(c->d, par, sm);
-      lbm::launch_enthalpy_commit(c->d, par, sm);
-      par ^= 1;
-      lbm::adj_clamp(c->d, par, b.a, segC + (size_t)m * n, segL + (size_t)m * n, segN + m, sm);
-      cudaMemcpyAsync(segF + (size_t)m * n, c->d.fl, n * sizeof(float), cudaMemcpyDeviceToDevice,
-                      sm);
-    }
-    for (int64_t m = len - 1; m >= 0; --m) {
-      const size_t o = (size_t)(m + 1) * n;
-      lbm::adj_step(c->d, b, segC + o, segL + o, segN + m + 1, segF + (size_t)m * n, segF + o,
-                    sweeps, sm);
-      std::swap(b.lamg, b.lamgpre);
-    }
-  };
-  struct SegGraph {
-    int64_t len;
-    float* lamg;
-    cudaGraphExec_t ex;
-  };
-  struct SegGraphs {
-    std::vector<SegGraph> v;
-    ~SegGraphs() {
-      for (SegGraph& g : v) cudaGraphExecDestroy(g.ex);
+  struct Graphs {
+    std::vector<cudaGraphExec_t> v;
+    ~Graphs() {
+      for (cudaGraphExec_t g : v) cudaGraphExecDestroy(g);
     }
   } graphs;
-  const bool can_capture = capture_streams(c);
-  for (int64_t j = ncp - 1; j >= 0; --j) {
-    const int64_t first = j * K;
-    const int64_t len = (j == ncp - 1) ? nsteps - first : K;
-    if (len <= 0) continue;
-    LBM_TRY(restore(cps + (size_t)j * st));
-    LBM_CUDA(cudaMemcpyAsync(segF, cps + (size_t)j * st + 5 * n, n * sizeof(float),
-                             cudaMemcpyDeviceToDevice, c->stream));
-    float* const lamg0 = b.lamg;
-    float* const lamgpre0 = b.lamgpre;
-    cudaGraphExec_t ex = nullptr;
-    for (const SegGraph& g : graphs.v)
-      if (g.len == len && g.lamg == lamg0) ex = g.ex;
-    if (!ex && can_capture && len == K) {
-      cudaGraph_t gr = nullptr;
-      if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-        record_segment(c->cap, len);
-        if (cudaStreamEndCapture(c->cap, &gr) == cudaSuccess && gr) {
-          ex = instantiate(gr);
-          if (ex) graphs.v.push_back({len, lamg0, ex});
-        }
+  const int64_t steps0 = c->steps;
+  lbm::adj_seed(c->d, b.lamf, b.lamg, b.a, c->stream);   // a is needed from here on
+  if (keep_all) {
+    // forward, f_l after every step into flS (its start at index 0)
+    LBM_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), c->stream));
+    lbm::adj_save(c->d, flS, ctr, c->stream);
+    const bool use_graphs = !c->graphs_off;
+    int64_t left = nsteps;
+    auto direct = [&]() -> int {
+      LBM_TRY(step_direct(c));
+      lbm::adj_save(c->d, flS, ctr, c->stream);
+      --left;
+      return LBM_OK;
+    };
+    while (left > 0 && (c->parity != 0 || !use_graphs || left < 2)) LBM_TRY(direct());
+    for (int len : {GRAPH_STEPS, 2}) {
+      if (left < len) continue;
+      cudaGraphExec_t g = capture_keep(c, len, flS, ctr);
+      if (!g) break;
+      graphs.v.push_back(g);
+      while (left >= len) {
+        LBM_CUDA(cudaGraphLaunch(g, c->stream));
+        left -= len;
+        c->steps += len;
       }
-      cudaGetLastError();
-      b.lamg = lamg0;
-      b.lamgpre = lamgpre0;
     }
-    if (ex) {
-      LBM_CUDA(cudaGraphLaunch(ex, c->stream));
-      if (len & 1) std::swap(b.lamg, b.lamgpre);
-    } else {
-      record_segment(c->stream, len);
+    while (left > 0) LBM_TRY(direct());
+  } else {
+    // forward, keeping the whole state every K steps
+    LBM_TRY(save(cps));
+    for (int64_t j = 1; j < ncp; ++j) {
+      LBM_TRY(lbm_step(c, K));
+      LBM_TRY(save(cps + (size_t)j * st));
     }
-    LBM_CUDA(cudaGetLastError());
+    const int64_t done = (ncp - 1) * K;
+    if (nsteps > done) LBM_TRY(lbm_step(c, nsteps - done));
+    LBM_TRY(save(fin));
   }
-  // back to where the forward run ended
-  LBM_TRY(restore(fin));
-  c->steps = steps0 + nsteps;
+  const float* fl_end = keep_all ? flS + (size_t)nsteps * n : fin + 5 * n;
+  lbm::adj_objective(c->d, fl_end, dJ, c->stream);
+  // reverse sweep
+  LBM_CUDA(cudaMemsetAsync(b.lama, 0, n * sizeof(float), c->stream));
+  LBM_CUDA(cudaMemsetAsync(b.lamtw, 0, c->d.ny * sizeof(float), c->stream));
+  LBM_CUDA(cudaMemsetAsync(b.nu, 0, n * sizeof(float), c->stream));
+  LBM_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(int), c->stream));
+  lbm::adj_list(c->d, fl_end, lists[0], counts, c->stream);
+  int cur = 0;
+  // reversed steps m = hi - 1 .. lo, f_l of step m at F + (m - lo) n
+  auto reverse = [&](cudaStream_t sm, const float* F, int64_t lo, int64_t hi) {
+    for (int64_t m = hi - 1; m >= lo; --m) {
+      const float* f0 = F + (size_t)(m - lo) * n;
+      lbm::adj_step(c->d, b, f0, f0 + n, lists[cur], counts + cur, lists[1 - cur],
+                    counts + 1 - cur, sweeps, sm);
+      std::swap(b.lamg, b.lamgpre);
+      cur ^= 1;
+    }
+  };
+  if (keep_all) {
+    reverse(c->stream, flS, 0, nsteps);
+  } else {
+    // One segment after its checkpoint is restored (parity 0): the len steps
+    // forward, f_l of each kept, then the len reverse steps; the same
+    // launches for every whole segment, so they are captured once per
+    // (len, buffer parity) and replayed.
+    auto record_segment = [&](cudaStream_t sm, int64_t len) {
+      int par = 0;
+      for (int64_t m = 1; m <= len; ++m) {
+        lbm::launch_fused(c->d, c->tma(), par, 0, sm);
+        lbm::launch_enthalpy_solve(c->d, par, sm);
+        lbm::launch_enthalpy_commit(c->d, par, sm);
+        par ^= 1;
+        cudaMemcpyAsync(flS + (size_t)m * n, c->d.fl, n * sizeof(float),
+                        cudaMemcpyDeviceToDevice, sm);
+      }
+      reverse(sm, flS, 0, len);
+    };
+    struct SegGraph {
+      int64_t len;
+      float* lamg;
+      cudaGraphExec_t ex;
+    };
+    std::vector<SegGraph> seg_graphs;
+    const bool can_capture = capture_streams(c);
+    for (int64_t j = ncp - 1; j >= 0; --j) {
+      const int64_t first = j * K;
+      const int64_t len = (j == ncp - 1) ? nsteps - first : K;
+      if (len <= 0) continue;
+      LBM_TRY(restore(cps + (size_t)j * st));
+      LBM_CUDA(cudaMemcpyAsync(flS, cps + (size_t)j * st + 5 * n, n * sizeof(float),
+                               cudaMemcpyDeviceToDevice, c->stream));
+      float* const lamg0 = b.lamg;
+      float* const lamgpre0 = b.lamgpre;
+      const int cur0 = cur;
+      cudaGraphExec_t ex = nullptr;
+      for (const SegGraph& g : seg_graphs)
+        if (g.len == len && g.lamg == lamg0) ex = g.ex;
+      if (!ex && can_capture && len == K) {
+        cudaGraph_t gr = nullptr;
+        if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+          record_segment(c->cap, len);
+          if (cudaStreamEndCapture(c->cap, &gr) == cudaSuccess && gr) {
+            ex = instantiate(gr);
+            if (ex) {
+              seg_graphs.push_back({len, lamg0, ex});
+              graphs.v.push_back(ex);
+            }
+          }
+        }
+        cudaGetLastError();
+        b.lamg = lamg0;
+        b.lamgpre = lamgpre0;
+        cur = cur0;
+      }
+      if (ex) {
+        LBM_CUDA(cudaGraphLaunch(ex, c->stream));
+        if (len & 1) {
+          std::swap(b.lamg, b.lamgpre);
+          cur ^= 1;
+        }
+      } else {
+        record_segment(c->stream, len);
+      }
+      LBM_CUDA(cudaGetLastError());
+    }
+    // back to where the forward run ended
+    LBM_TRY(restore(fin));
+    c->steps = steps0 + nsteps;
+  }
+  LBM_CUDA(cudaGetLastError());
   // d J / d phi = (dT / (sigma St)) d J / d a
   std::vector<float> la(n), lt(c->d.ny);
   LBM_CUDA(cudaMemcpyAsync(la.data(), b.lama, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));

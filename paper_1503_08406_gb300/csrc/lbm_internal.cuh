@@ -338,7 +338,7 @@ struct AdjBuffers {
   float* a;          // a = phi dT / (sigma St)
   float* lamg;       // 5 n: adjoint of the populations after the step being reversed
   float* lamf;       // adjoint of f_l after the step (in), before it (out)
-  float* nu;         // band nodes: c mu, mu the fixed point's adjoint
+  float* nu;         // c mu on the band, mu the fixed point's adjoint; 0 elsewhere
   float* rhs;        // band nodes (wide bands): right-hand side of mu's equation
   float* mu0;        // mu in global memory (wide bands), ping-pong
   float* mu1;
@@ -351,16 +351,18 @@ struct AdjBuffers {
 void adj_seed(const Dev& d, float* lamf, float* lamg, float* a, cudaStream_t s);
 // J into out[0]; out holds 129 doubles (the rest: partial sums)
 void adj_objective(const Dev& d, const float* fl, double* out, cudaStream_t s);
-// after a recomputed step, populations in `layout`: c = 1/(T_l - T_s + a) on
-// the unclamped non-wall nodes (0 elsewhere) and their list, appended at
-// list[*count] (count zeroed by the caller)
-void adj_clamp(const Dev& d, int layout, const float* a, float* cinv, int* list, int* count,
-               cudaStream_t s);
-// one step of the reverse sweep, given that step's clamp state and f_l before
-// and after it: from b.lamg / b.lamf (after the step) to b.lamgpre / b.lamf
-// (before it); the caller swaps b.lamg and b.lamgpre
-void adj_step(const Dev& d, const AdjBuffers& b, const float* cinv, const int* list,
-              const int* count, const float* f0, const float* f1, int mu_sweeps, cudaStream_t s);
+// the band (non-wall nodes with 0 < f < 1), appended at list[*count]
+void adj_list(const Dev& d, const float* f, int* list, int* count, cudaStream_t s);
+// d.fl to base + k n, k = ctr[0], which then advances (ctr[1]: scratch, 0)
+void adj_save(const Dev& d, float* base, unsigned* ctr, cudaStream_t s);
+// One step of the reverse sweep, given f_l before (f0) and after (f1) it and
+// the band after it (list, count): from b.lamg / b.lamf (after the step) to
+// b.lamgpre / b.lamf (before it).  old_list / old_count hold the band the
+// previous call solved on; they are emptied and refilled with the band before
+// this step, for the next call.  The caller swaps b.lamg and b.lamgpre and the
+// two lists.
+void adj_step(const Dev& d, const AdjBuffers& b, const float* f0, const float* f1, int* list,
+              int* count, int* old_list, int* old_count, int mu_sweeps, cudaStream_t s);
 // once per process before adj_step: the band kernel's shared-memory opt-in
 bool adj_init();
 void launch_validate(const Dev& d, const float* phi, const float* K, const float* T0,

@@ -73,13 +73,26 @@ def test_checkpoint_spacing_does_not_change_the_gradient(lbm):
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
 
 
-def test_context_ends_where_the_forward_run_does(lbm):
+def test_keeping_every_step_matches_recomputation(lbm):
+    """checkpoint_every = 0 keeps f_l of every step from a graph-replayed
+    forward run; K > 0 recomputes from checkpoints step by step."""
+    w, params, Tw, phi = _case()
+    a = _lattice(lbm, w, params, phi, Tw).adjoint_melt(STEPS)
+    b = _lattice(lbm, w, params, phi, Tw).adjoint_melt(STEPS, checkpoint_every=37)
+    assert a[0] == b[0]
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+@pytest.mark.parametrize("K", [0, 37])
+def test_context_ends_where_the_forward_run_does(lbm, K):
     w, params, Tw, phi = _case()
     lat = _lattice(lbm, w, params, phi, Tw)
-    lat.adjoint_melt(STEPS)
+    lat.step(3)   # an odd start: the forward run begins with a single step
+    lat.adjoint_melt(STEPS, checkpoint_every=K)
     plain = _lattice(lbm, w, params, phi, Tw)
+    plain.step(3)
     plain.step(STEPS)
-    assert lat.steps_done() == STEPS
+    assert lat.steps_done() == STEPS + 3
     ma, mb = lat.macros(), plain.macros()
     for k in ("T", "fl"):
         np.testing.assert_array_equal(ma[k], mb[k])
