@@ -71,9 +71,12 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--storage", choices=("fp32", "fp16", "bf16"), default="fp32",
                     help="population storage (arithmetic is FP32 in every case)")
-    ap.add_argument("--workload", choices=("cavity", "batched"), default="cavity",
+    ap.add_argument("--workload", choices=("cavity", "batched", "adjoint"), default="cavity",
                     help="cavity: the 2048^2 heterogeneous cavity (default); batched: 64 "
-                         "uneven cavities advanced together through one CUDA graph")
+                         "uneven cavities advanced together through one CUDA graph; adjoint: "
+                         "melted fraction and its gradients on an n x ny conduction slab, "
+                         "timed against the forward run alone")
+    ap.add_argument("--ny", type=int, default=512, help="adjoint workload: slab height")
     ap.add_argument("--autotune", action="store_true",
                     help="batched workload: tune each cavity's stream-collide kernel first")
     return ap.parse_args(argv)
@@ -330,6 +333,58 @@ def batched(args, torch):
     return 0
 
 
+def adjoint(args, torch):
+    """The conduction slab (lbm_workloads.adjoint_slab, n x ny): `steps` steps
+    forward alone, then the same steps with the adjoint (lbm_adjoint_melt:
+    forward, reverse sweep, gradients back on the host), both from the same
+    state; one JSON line, value = adjoint time / forward time."""
+    import lbm_workloads as W
+    from paper_1503_08406_gb300 import Lattice
+    w = W.adjoint_slab(args.n, args.ny)
+    stream = torch.cuda.current_stream()
+    lat = Lattice(w.nx, w.ny, stream=stream, **w.params)
+
+    def reset():
+        lat.set_fields(w.phi, w.K, w.T0, w.fl0, w.wall_T_left)
+        torch.cuda.synchronize()
+
+    reset()
+    lat.step(args.warmup)                       # graphs captured, clocks up
+    reset()
+    lat.adjoint_melt(max(args.warmup, 2))       # allocations and kernels warmed
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reset()
+    e0.record(stream)
+    lat.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_fwd = e0.elapsed_time(e1)
+    reset()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    with ClockSampler(vis.split(",")[0] if vis else "0") as clk:
+        t0 = time.perf_counter()
+        J, dphi, dtw = lat.adjoint_melt(args.steps)
+        ms_adj = (time.perf_counter() - t0) * 1e3
+    line = {
+        "metric": "adjoint time / forward time, melted fraction and its gradients",
+        "value": ms_adj / ms_fwd, "unit": "x", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_adj / args.steps, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "lattice": [w.nx, w.ny],
+                   "memory": "f_l of every step kept (%.2f GB)" % (
+                       (args.steps + 1) * w.cells * 4 / 1e9)},
+        "forward": {"ms": ms_fwd, "MLUPS": w.cells * args.steps / (ms_fwd * 1e-3) / 1e6,
+                    "timing": "CUDA events on the lattice's stream"},
+        "adjoint": {"ms": ms_adj, "timing": "host wall clock around lbm_adjoint_melt "
+                    "(forward run, reverse sweep, gradients copied to the host)",
+                    "J": J, "dJ_dTw_max": float(abs(dtw).max()),
+                    "dJ_dphi_max": float(abs(dphi).max())},
+        "status": lat.status(), "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse(argv)
     if args.impl == "reference":
@@ -339,12 +394,12 @@ def main(argv=None):
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device (there is no CPU path)")
     torch.cuda.set_device(local)
-    if args.workload == "batched":
+    if args.workload in ("batched", "adjoint"):
         if world > 1:
-            raise SystemExit("the batched workload runs on one GPU")
+            raise SystemExit("the %s workload runs on one GPU" % args.workload)
         import __graft_entry__
         __graft_entry__.build()
-        return batched(args, torch)
+        return batched(args, torch) if args.workload == "batched" else adjoint(args, torch)
     dist = init_dist(world, "nccl")
     device = torch.device("cuda", local)
     if local == 0:

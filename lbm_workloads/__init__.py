@@ -275,3 +275,19 @@ def two_phase_slab(ratio: float = 10.0, nx: int = 200, ny: int = 6, alpha_s: flo
     return Workload("two_phase_slab_%dx%d_ratio%g" % (nx, ny, ratio), nx, ny, params,
                     np.ones((ny, nx)), np.full((ny, nx), 1e3), T0, fl0,
                     meta=dict(alpha_s=alpha_s, alpha_l=alpha_l, T_b=1.0, T_i=-1.0, T_m=0.0))
+
+
+def adjoint_slab(nx: int = 2048, ny: int = 512, seed: int = 0) -> Workload:
+    """The conduction slab of two_phase_slab (ratio 1) set up for gradients:
+    a wide mushy band T_s / T_l = -/+0.3 (fronts stay off the clamps),
+    porosity 0.6 + 0.2 U(0, 1) per node (seeded) and the left wall profile
+    T_w(y) = 1 + 0.2 sin(2 pi y / ny) in `wall_T_left`."""
+    w = two_phase_slab(1.0, nx=nx, ny=ny)
+    params = dict(w.params)
+    params.pop("alpha_ratio")
+    params.update(T_s=-0.3, T_l=0.3)
+    phi = 0.6 + 0.2 * np.random.default_rng(seed).random((ny, nx))
+    tw = 1.0 + 0.2 * np.sin(2 * np.pi * np.arange(ny) / ny)
+    return Workload("adjoint_slab_%dx%d_seed%d" % (nx, ny, seed), nx, ny, params, phi, w.K,
+                    w.T0, w.fl0, wall_T_left=tw, meta=dict(w.meta))
+

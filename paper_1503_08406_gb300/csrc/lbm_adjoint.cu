@@ -41,8 +41,8 @@ __device__ __forceinline__ float wt(const Dev& d, int i) { return i == 0 ? d.wt0
 
 // Each reversed step is two kernels.  adj_band_kernel (one CTA) solves the
 // fixed point's adjoint on the unclamped nodes, a band along the front, and
-// leaves nu = c mu there (0 elsewhere).  adj_full_kernel passes over the whole
-// lattice once: with lam_g+_i(x) = lam_g'_i(x + e_i) + nu(x + e_i) and
+// adds nu = c mu there to lam_g' (nu is 0 elsewhere).  adj_full_kernel passes
+// over the whole lattice once: with lam_g+_i(x) = lam_g'_i(x + e_i) + nu(x + e_i) and
 // S(y) = sum_i w~_i lam_g+_i(y) (the source adjoint of step F, the fixed
 // point's share included),
 //   lam_gpre = A^T lam_g+ per node
@@ -77,8 +77,8 @@ __global__ void adj_list_kernel(Dev d, const float* f, int* list, int* count) {
 // its value or after max_sweeps.  Up to BAND_CAP band nodes sweep in shared
 // memory (each node's coefficients and its neighbours' places in the list
 // staged once); a wider band sweeps in global memory.  Jacobi makes the
-// result independent of the list's order.  First clears nu on the previous
-// band (old_list) and empties that list for the full pass to refill.
+// result independent of the list's order.  Empties the previous band's list
+// (old_count) for the full pass to refill.
 constexpr float MU_RTOL = 4e-7f;
 constexpr int BAND_CAP = 4096;
 constexpr int BAND_THREADS = 1024;
@@ -97,14 +97,19 @@ __device__ __forceinline__ float band_rhs(const Dev& d, const AdjBuffers& b, int
   return b.lamf[s] - b.a[s] * L;
 }
 
+// nu = c mu at band node s joins every lam_g'_i there (lam_g+_i(x) takes
+// lam_g'_i + nu at x + e_i; nothing else reads lam_g' after this kernel)
+__device__ __forceinline__ void add_nu(const Dev& d, const AdjBuffers& b, int s, float v) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) b.lamg[i * (long long)d.n + s] += v;
+}
+
 __global__ void __launch_bounds__(BAND_THREADS) adj_band_kernel(Dev d, AdjBuffers b,
                                                                 const float* f1, const int* list,
-                                                                const int* count,
-                                                                const int* old_list,
-                                                                int* old_count, int max_sweeps) {
+                                                                const int* count, int* old_count,
+                                                                int max_sweeps) {
   extern __shared__ float4 band_smem[];
-  const int cnt = *count, ocnt = *old_count;
-  for (int j = threadIdx.x; j < ocnt; j += blockDim.x) b.nu[old_list[j]] = 0.f;
+  const int cnt = *count;
   if (cnt <= BAND_CAP) {
     float4* ct = band_smem;                                    // c of the 4 neighbours
     ushort4* ix = reinterpret_cast<ushort4*>(ct + BAND_CAP);   // their places in the list
@@ -154,7 +159,7 @@ __global__ void __launch_bounds__(BAND_THREADS) adj_band_kernel(Dev d, AdjBuffer
     }
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
       const int s = list[j];
-      b.nu[s] = mu[j] / (d.dTt + b.a[s]);
+      add_nu(d, b, s, mu[j] / (d.dTt + b.a[s]));
     }
   } else {
     float* mu = b.mu0;
@@ -190,71 +195,78 @@ __global__ void __launch_bounds__(BAND_THREADS) adj_band_kernel(Dev d, AdjBuffer
     }
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
       const int s = list[j];
-      b.nu[s] = mu[s] / (d.dTt + b.a[s]);
+      add_nu(d, b, s, mu[s] / (d.dTt + b.a[s]));
     }
   }
   __syncthreads();
   if (threadIdx.x == 0) *old_count = 0;
 }
 
-// lam_g+ of node (x, y) and A^T of it
-__device__ __forceinline__ void pre_pops(const Dev& d, const AdjBuffers& b, int x, int y,
-                                         float lp[5], float out[5]) {
+// lam_g+ of node (x, y) (rows yu = y + 1, yd = y - 1, periodic) and A^T of it
+__device__ __forceinline__ void pre_pops(const Dev& d, const AdjBuffers& b, const Mat5& At, int x,
+                                         int y, int yu, int yd, float lp[5], float out[5]) {
   const int n = (int)d.n;
+  const int s = y * d.nx + x;
+  const int t[5] = {s, x + 1 < d.nx ? s + 1 : -1, yu * d.nx + x, x > 0 ? s - 1 : -1,
+                    yd * d.nx + x};
 #pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const int t = adj_nb(d, x, y, ex9(i), ey9(i));
-    lp[i] = (t >= 0) ? b.lamg[i * n + t] + b.nu[t] : 0.f;
-  }
+  for (int i = 0; i < 5; ++i)
+    lp[i] = (t[i] >= 0) ? __ldg(b.lamg + i * n + t[i]) : 0.f;
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     float v = 0.f;
 #pragma unroll
-    for (int i = 0; i < 5; ++i) v += b.At[k * 5 + i] * lp[i];
+    for (int i = 0; i < 5; ++i) v += At.m[k * 5 + i] * lp[i];
     out[k] = v;
   }
 }
 
-__global__ void adj_full_kernel(Dev d, AdjBuffers b, const float* f0, const float* f1,
-                                int* next_list, int* next_count) {
-  const int s = blockIdx.x * AB + threadIdx.x;
-  if (s >= (int)d.n) return;
-  const int y = s / d.nx, x = s - y * d.nx;
+// one row segment per block (x along threads, y = blockIdx.y + k gridDim.y)
+__global__ void __launch_bounds__(AB) adj_full_kernel(Dev d, AdjBuffers b, Mat5 At,
+                                                      const float* __restrict__ f0,
+                                                      const float* __restrict__ f1,
+                                                      int* next_list, int* next_count) {
+  const int x = blockIdx.x * AB + threadIdx.x;
+  if (x >= d.nx) return;
   const int n = (int)d.n;
-  float lp[5], pre[5];
-  pre_pops(d, b, x, y, lp, pre);
-  if (x == 0 || x == d.nx - 1) {
-    if (x == 0 && d.bc[0] == 1) {
+  for (int y = blockIdx.y; y < d.ny; y += gridDim.y) {
+    const int yu = y + 1 == d.ny ? 0 : y + 1, yd = y == 0 ? d.ny - 1 : y - 1;
+    const int s = y * d.nx + x;
+    float lp[5], pre[5];
+    pre_pops(d, b, At, x, y, yu, yd, lp, pre);
+    if (x == 0 || x == d.nx - 1) {
+      if (x == 0 && d.bc[0] == 1) {
+        float wl = 0.f;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) wl += wt(d, i) * pre[i];
+        b.lamtw[y] += wl;
+      }
+#pragma unroll
+      for (int k = 0; k < 5; ++k) b.lamgpre[k * n + s] = 0.f;
+      continue;   // a wall node keeps f_l(n): lam_f unchanged, no share of a
+    }
+    // an inward column also takes its wall node's adjoint
+    for (int side = 0; side < 2; ++side) {
+      if (x != (side ? d.nx - 2 : 1)) continue;
+      float lw[5], pw[5];
+      pre_pops(d, b, At, side ? d.nx - 1 : 0, y, yu, yd, lw, pw);
       float wl = 0.f;
 #pragma unroll
-      for (int i = 0; i < 5; ++i) wl += wt(d, i) * pre[i];
-      b.lamtw[y] += wl;
+      for (int i = 0; i < 5; ++i) wl += wt(d, i) * pw[i];
+      if (d.bc[side] != 1) wl = 0.f;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) pre[k] += pw[k] - wl;
     }
 #pragma unroll
-    for (int k = 0; k < 5; ++k) b.lamgpre[k * n + s] = 0.f;
-    return;   // a wall node keeps f_l(n): lam_f unchanged, no share of a
+    for (int k = 0; k < 5; ++k) b.lamgpre[k * n + s] = pre[k];
+    float S = 0.f;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) S += wt(d, i) * lp[i];
+    const float fa = f0[s], fb = f1[s];
+    b.lamf[s] = __ldg(b.a + s) * S;
+    if (fb != fa) b.lama[s] += -(fb - fa) * S;   // (adds 0 elsewhere)
+    if (fa > 0.f && fa < 1.f) next_list[atomicAdd(next_count, 1)] = s;
   }
-  // an inward column also takes its wall node's adjoint
-  for (int side = 0; side < 2; ++side) {
-    if (x != (side ? d.nx - 2 : 1)) continue;
-    float lw[5], pw[5];
-    pre_pops(d, b, side ? d.nx - 1 : 0, y, lw, pw);
-    float wl = 0.f;
-#pragma unroll
-    for (int i = 0; i < 5; ++i) wl += wt(d, i) * pw[i];
-    if (d.bc[side] != 1) wl = 0.f;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) pre[k] += pw[k] - wl;
-  }
-#pragma unroll
-  for (int k = 0; k < 5; ++k) b.lamgpre[k * n + s] = pre[k];
-  float S = 0.f;
-#pragma unroll
-  for (int i = 0; i < 5; ++i) S += wt(d, i) * lp[i];
-  const float fa = f0[s];
-  b.lamf[s] = b.a[s] * S;
-  b.lama[s] += -(f1[s] - fa) * S;
-  if (fa > 0.f && fa < 1.f) next_list[atomicAdd(next_count, 1)] = s;
 }
 
 // Forward runs that keep every step's f_l: copies d.fl to base + k n, k the
@@ -343,9 +355,12 @@ void adj_save(const Dev& d, float* base, unsigned* ctr, cudaStream_t s) {
 
 void adj_step(const Dev& d, const AdjBuffers& b, const float* f0, const float* f1, int* list,
               int* count, int* old_list, int* old_count, int mu_sweeps, cudaStream_t s) {
-  adj_band_kernel<<<1, BAND_THREADS, BAND_SMEM, s>>>(d, b, f1, list, count, old_list, old_count,
+  adj_band_kernel<<<1, BAND_THREADS, BAND_SMEM, s>>>(d, b, f1, list, count, old_count,
                                                      mu_sweeps);
-  adj_full_kernel<<<blocks(d.n), AB, 0, s>>>(d, b, f0, f1, old_list, old_count);
+  Mat5 At;
+  for (int k = 0; k < 25; ++k) At.m[k] = b.At_host[k];
+  const dim3 grid((d.nx + AB - 1) / AB, d.ny < 65535 ? d.ny : 65535);
+  adj_full_kernel<<<grid, AB, 0, s>>>(d, b, At, f0, f1, old_list, old_count);
 }
 
 }  // namespace lbm

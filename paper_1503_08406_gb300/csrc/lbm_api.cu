@@ -966,7 +966,6 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
   b.a = mem.get(n);
   b.lamg = mem.get(5 * n);
   b.lamf = mem.get(n);
-  b.nu = mem.get(n);
   b.rhs = mem.get(n);
   b.mu0 = mem.get(n);
   b.mu1 = mem.get(n);
@@ -979,7 +978,7 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
   int* counts = reinterpret_cast<int*>(mem.get(2));
   unsigned* ctr = reinterpret_cast<unsigned*>(mem.get(2));
   double* dJ = reinterpret_cast<double*>(mem.get(2 * 129));
-  if (!flS || (!keep_all && (!cps || !fin)) || !b.a || !b.lamg || !b.lamf || !b.nu || !b.rhs ||
+  if (!flS || (!keep_all && (!cps || !fin)) || !b.a || !b.lamg || !b.lamf || !b.rhs ||
       !b.mu0 || !b.mu1 || !b.lamgpre || !b.lama || !b.lamtw || !b.At || !b.pos || !lists[0] ||
       !lists[1] || !counts || !ctr || !dJ)
     return LBM_ERR_OOM;
@@ -1003,6 +1002,7 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
         At[j * 5 + i] = (float)a;
       }
     LBM_CUDA(cudaMemcpyAsync(b.At, At, sizeof At, cudaMemcpyHostToDevice, c->stream));
+    memcpy(b.At_host, At, sizeof At);
   }
   auto save = [&](float* dst) -> int {
     LBM_TRY(lbm_get_state(c, nullptr, dst, dst + 5 * n, 1));
@@ -1061,7 +1061,6 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
   // reverse sweep
   LBM_CUDA(cudaMemsetAsync(b.lama, 0, n * sizeof(float), c->stream));
   LBM_CUDA(cudaMemsetAsync(b.lamtw, 0, c->d.ny * sizeof(float), c->stream));
-  LBM_CUDA(cudaMemsetAsync(b.nu, 0, n * sizeof(float), c->stream));
   LBM_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(int), c->stream));
   lbm::adj_list(c->d, fl_end, lists[0], counts, c->stream);
   int cur = 0;

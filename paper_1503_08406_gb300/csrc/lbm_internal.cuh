@@ -338,7 +338,6 @@ struct AdjBuffers {
   float* a;          // a = phi dT / (sigma St)
   float* lamg;       // 5 n: adjoint of the populations after the step being reversed
   float* lamf;       // adjoint of f_l after the step (in), before it (out)
-  float* nu;         // c mu on the band, mu the fixed point's adjoint; 0 elsewhere
   float* rhs;        // band nodes (wide bands): right-hand side of mu's equation
   float* mu0;        // mu in global memory (wide bands), ping-pong
   float* mu1;
@@ -347,6 +346,10 @@ struct AdjBuffers {
   float* lamtw;      // ny: accumulated adjoint of the left wall profile
   float* At;         // 25: transposed collision matrix (u = 0)
   int* pos;          // n: a band node's place in the band list
+  float At_host[25]; // the same, passed to kernels by value
+};
+struct Mat5 {
+  float m[25];
 };
 void adj_seed(const Dev& d, float* lamf, float* lamg, float* a, cudaStream_t s);
 // J into out[0]; out holds 129 doubles (the rest: partial sums)
