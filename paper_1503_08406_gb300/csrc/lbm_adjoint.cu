@@ -22,7 +22,7 @@
 // 4 w~_1 a / (T_l - T_s + w~_0 a) <= 2/3).
 // At the fixed point z = f on those nodes, which removes the direct term of
 // d z / d a.
-#include "lbm_internal.cuh"
+#include "lbm_adjoint.cuh"
 
 namespace lbm {
 

@@ -1,0 +1,43 @@
+// Host entry points of the adjoint of the conduction step (lbm_adjoint.cu).
+#pragma once
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+// all buffers n floats unless noted
+struct AdjBuffers {
+  float* a;          // a = phi dT / (sigma St)
+  float* lamg;       // 5 n: adjoint of the populations after the step being reversed
+  float* lamf;       // adjoint of f_l after the step (in), before it (out)
+  float* rhs;        // band nodes (wide bands): right-hand side of mu's equation
+  float* mu0;        // mu in global memory (wide bands), ping-pong
+  float* mu1;
+  float* lamgpre;    // 5 n: adjoint of the populations before the step
+  float* lama;       // accumulated adjoint of a
+  float* lamtw;      // ny: accumulated adjoint of the left wall profile
+  float* At;         // 25: transposed collision matrix (u = 0)
+  int* pos;          // n: a band node's place in the band list
+  float At_host[25]; // the same, passed to kernels by value
+};
+struct Mat5 {
+  float m[25];
+};
+void adj_seed(const Dev& d, float* lamf, float* lamg, float* a, cudaStream_t s);
+// J into out[0]; out holds 129 doubles (the rest: partial sums)
+void adj_objective(const Dev& d, const float* fl, double* out, cudaStream_t s);
+// the band (non-wall nodes with 0 < f < 1), appended at list[*count]
+void adj_list(const Dev& d, const float* f, int* list, int* count, cudaStream_t s);
+// d.fl to base + k n, k = ctr[0], which then advances (ctr[1]: scratch, 0)
+void adj_save(const Dev& d, float* base, unsigned* ctr, cudaStream_t s);
+// One step of the reverse sweep, given f_l before (f0) and after (f1) it and
+// the band after it (list, count): from b.lamg / b.lamf (after the step) to
+// b.lamgpre / b.lamf (before it).  old_list / old_count hold the band the
+// previous call solved on; they are emptied and refilled with the band before
+// this step, for the next call.  The caller swaps b.lamg and b.lamgpre and the
+// two lists.
+void adj_step(const Dev& d, const AdjBuffers& b, const float* f0, const float* f1, int* list,
+              int* count, int* old_list, int* old_count, int mu_sweeps, cudaStream_t s);
+// once per process before adj_step: the band kernel's shared-memory opt-in
+bool adj_init();
+
+}  // namespace lbm

@@ -9,7 +9,7 @@
 #include <vector>
 
 #include "lbm.h"
-#include "lbm_internal.cuh"
+#include "lbm_adjoint.cuh"
 
 using lbm::Dev;
 

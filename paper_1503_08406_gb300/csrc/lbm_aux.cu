@@ -10,6 +10,21 @@ __device__ __forceinline__ bool flow_active(const Dev& d, int x, int y) {
   return !is_wall(d, x, y) && d.fl[(long long)y * d.nx + x] >= d.f_act;
 }
 
+// g_i of non-wall node (x, y) in the given layout
+__device__ __forceinline__ void gather_g(const Dev& d, int x, int y, int layout, float g[5]) {
+  const long long n = d.n, s = (long long)y * d.nx + x;
+  (void)n;
+  g[0] = ld_g(d, 0, s);
+  for (int i = 1; i < 5; ++i) {
+    if (layout == 0) {
+      g[i] = ld_g(d, i, s);
+    } else {
+      const int sx = wrapx(d, x - ex9(i)), sy = wrapy(d, y - ey9(i));
+      g[i] = ld_g(d, opp5(i), (long long)sy * d.nx + sx);
+    }
+  }
+}
+
 // f_i of node (x, y): nodes without flow hold theirs in their own slots
 __device__ __forceinline__ void gather_f(const Dev& d, int x, int y, int layout, float f[9]) {
   const long long n = d.n, s = (long long)y * d.nx + x;
@@ -154,9 +169,8 @@ __global__ void reduce_final_kernel(const double* partials, int nblocks, double*
   out[3] = t[5] > 0 ? t[4] / t[5] : 0.0;
 }
 
-// f (9 planes), g (5 planes) and T = sum_i g_i (one plane) in the natural
-// layout; each output is optional
-__global__ void get_state_kernel(Dev d, int layout, float* f, float* g, float* T) {
+// f (9 planes) and g (5 planes) in the natural layout; each output is optional
+__global__ void get_state_kernel(Dev d, int layout, float* f, float* g) {
   const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= d.n) return;
   const int y = (int)(s / d.nx), x = (int)(s - (long long)y * d.nx);
@@ -170,19 +184,13 @@ __global__ void get_state_kernel(Dev d, int layout, float* f, float* g, float* T
       gather_f(d, x, y, layout, fv);
     for (int i = 0; i < 9; ++i) f[i * n + s] = fv[i];
   }
-  if (g || T) {
+  if (g) {
     float gv[5];
     if (wall)
       for (int i = 0; i < 5; ++i) gv[i] = ld_g(d, i, s);
     else
       gather_g(d, x, y, layout, gv);
-    if (g)
-      for (int i = 0; i < 5; ++i) g[i * n + s] = gv[i];
-    if (T) {
-      float t = 0.f;
-      for (int i = 0; i < 5; ++i) t += gv[i];
-      T[s] = t;
-    }
+    for (int i = 0; i < 5; ++i) g[i * n + s] = gv[i];
   }
 }
 
@@ -225,10 +233,7 @@ void launch_reduce(const Dev& d, int layout, double* partials, double* out, int 
   reduce_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, out);
 }
 void launch_get_state(const Dev& d, int layout, float* f, float* g, cudaStream_t s) {
-  get_state_kernel<<<grid1(d.n, 256), 256, 0, s>>>(d, layout, f, g, nullptr);
-}
-void launch_temperature(const Dev& d, int layout, float* T, cudaStream_t s) {
-  get_state_kernel<<<grid1(d.n, 256), 256, 0, s>>>(d, layout, nullptr, nullptr, T);
+  get_state_kernel<<<grid1(d.n, 256), 256, 0, s>>>(d, layout, f, g);
 }
 void launch_set_state(const Dev& d, const float* f, const float* g, cudaStream_t s) {
   set_state_kernel<<<grid1(d.n, 256), 256, 0, s>>>(d, f, g);

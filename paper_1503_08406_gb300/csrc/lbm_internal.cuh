@@ -256,21 +256,6 @@ __device__ __forceinline__ int wrapy(const Dev& d, int y) {
   y %= d.ny;
   return y < 0 ? y + d.ny : y;
 }
-
-// g_i of non-wall node (x, y) in the given layout (AA pattern: after an odd
-// step a node's populations sit in its upstream neighbours' opposite slots)
-__device__ __forceinline__ void gather_g(const Dev& d, int x, int y, int layout, float g[5]) {
-  const long long s = (long long)y * d.nx + x;
-  g[0] = ld_g(d, 0, s);
-  for (int i = 1; i < 5; ++i) {
-    if (layout == 0) {
-      g[i] = ld_g(d, i, s);
-    } else {
-      const int sx = wrapx(d, x - ex9(i)), sy = wrapy(d, y - ey9(i));
-      g[i] = ld_g(d, opp5(i), (long long)sy * d.nx + sx);
-    }
-  }
-}
 __device__ __forceinline__ bool is_wall(const Dev& d, int x, int y) {
   return (d.wall_l && x == 0) || (d.wall_r && x == d.nx - 1) || (d.wall_b && y == 0) ||
          (d.wall_t && y == d.ny - 1);
@@ -330,44 +315,7 @@ void launch_reduce(const Dev& d, int parity, double* partials, double* out, int 
                    cudaStream_t s);
 int reduce_blocks(const Dev& d);
 void launch_get_state(const Dev& d, int parity, float* f, float* g, cudaStream_t s);
-// T = sum_i g_i per node, natural layout
-void launch_temperature(const Dev& d, int parity, float* T, cudaStream_t s);
 void launch_set_state(const Dev& d, const float* f, const float* g, cudaStream_t s);
-// Adjoint of the conduction step (lbm_adjoint.cu); all buffers n floats unless noted
-struct AdjBuffers {
-  float* a;          // a = phi dT / (sigma St)
-  float* lamg;       // 5 n: adjoint of the populations after the step being reversed
-  float* lamf;       // adjoint of f_l after the step (in), before it (out)
-  float* rhs;        // band nodes (wide bands): right-hand side of mu's equation
-  float* mu0;        // mu in global memory (wide bands), ping-pong
-  float* mu1;
-  float* lamgpre;    // 5 n: adjoint of the populations before the step
-  float* lama;       // accumulated adjoint of a
-  float* lamtw;      // ny: accumulated adjoint of the left wall profile
-  float* At;         // 25: transposed collision matrix (u = 0)
-  int* pos;          // n: a band node's place in the band list
-  float At_host[25]; // the same, passed to kernels by value
-};
-struct Mat5 {
-  float m[25];
-};
-void adj_seed(const Dev& d, float* lamf, float* lamg, float* a, cudaStream_t s);
-// J into out[0]; out holds 129 doubles (the rest: partial sums)
-void adj_objective(const Dev& d, const float* fl, double* out, cudaStream_t s);
-// the band (non-wall nodes with 0 < f < 1), appended at list[*count]
-void adj_list(const Dev& d, const float* f, int* list, int* count, cudaStream_t s);
-// d.fl to base + k n, k = ctr[0], which then advances (ctr[1]: scratch, 0)
-void adj_save(const Dev& d, float* base, unsigned* ctr, cudaStream_t s);
-// One step of the reverse sweep, given f_l before (f0) and after (f1) it and
-// the band after it (list, count): from b.lamg / b.lamf (after the step) to
-// b.lamgpre / b.lamf (before it).  old_list / old_count hold the band the
-// previous call solved on; they are emptied and refilled with the band before
-// this step, for the next call.  The caller swaps b.lamg and b.lamgpre and the
-// two lists.
-void adj_step(const Dev& d, const AdjBuffers& b, const float* f0, const float* f1, int* list,
-              int* count, int* old_list, int* old_count, int mu_sweeps, cudaStream_t s);
-// once per process before adj_step: the band kernel's shared-memory opt-in
-bool adj_init();
 void launch_validate(const Dev& d, const float* phi, const float* K, const float* T0,
                      const float* fl0, int* bad, cudaStream_t s);
 
