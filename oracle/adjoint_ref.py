@@ -58,6 +58,8 @@ class ConductionRef:
         self.lat = float(params.get("dT", 1.0)) / (float(params.get("sigma", 1.0))
                                                     * float(params["St"]))
         self.T_s, self.T_l = float(params.get("T_s", 0.0)), float(params.get("T_l", 0.0))
+        self.dT = float(params.get("dT", 1.0))
+        self.H = float(params.get("H", 0.0)) or float(ny)   # the oracle's default
         self.tol = 1e-13
         wall = torch.zeros(ny, nx, dtype=torch.bool)
         wall[:, 0] = True
@@ -136,12 +138,32 @@ class ConductionRef:
     def melted_fraction(self, fl):
         return fl[~self.wall].mean()
 
-    def gradients(self, steps, T0, fl0, phi, Tw_left):
-        """Melted fraction after `steps` steps and its gradient with respect to
-        the porosity field and the left-wall temperature profile."""
+    def nusselt_hot(self, g, Tw_left):
+        """Left-wall Nusselt number of a state: -H/dT times the second-order
+        one-sided gradient (-3 T_0 + 4 T_1 - T_2)/2, T_0 the wall's imposed
+        temperature and T_1, T_2 the sums of g at x = 1, 2, averaged over the
+        rows (the oracle's reduce, fourth output)."""
+        T1 = g[:, :, 1].sum(dim=0)
+        T2 = g[:, :, 2].sum(dim=0)
+        return (-(-3.0 * Tw_left + 4.0 * T1 - T2) / 2.0 * self.H / self.dT).mean()
+
+    def gradients(self, steps, T0, fl0, phi, Tw_left, objective: str = "melt"):
+        """The objective and its gradient with respect to the porosity field
+        and the left-wall temperature profile.  objective "melt": the melted
+        fraction after `steps` steps; "nusselt": the left-wall Nusselt number
+        after each of the `steps` steps, averaged over them."""
+        if objective not in ("melt", "nusselt"):
+            raise ValueError(objective)
         phi_t = torch.tensor(np.asarray(phi, dtype=np.float64), requires_grad=True)
         tw_t = torch.tensor(np.asarray(Tw_left, dtype=np.float64), requires_grad=True)
-        _, fl = self.run(steps, T0, fl0, phi_t, tw_t)
-        J = self.melted_fraction(fl)
+        g = self.initial(T0)
+        fl = torch.as_tensor(np.asarray(fl0, dtype=np.float64))
+        a = phi_t * self.lat
+        nu = 0.0
+        for _ in range(steps):
+            g, fl = self.step(g, fl, a, tw_t)
+            if objective == "nusselt":
+                nu = nu + self.nusselt_hot(g, tw_t)
+        J = self.melted_fraction(fl) if objective == "melt" else nu / steps
         d_phi, d_tw = torch.autograd.grad(J, (phi_t, tw_t))
         return float(J.detach()), d_phi.numpy(), d_tw.numpy()
