@@ -77,6 +77,9 @@ def parse(argv=None):
                          "melted fraction and its gradients on an n x ny conduction slab, "
                          "timed against the forward run alone")
     ap.add_argument("--ny", type=int, default=512, help="adjoint workload: slab height")
+    ap.add_argument("--objective", choices=("melt", "nusselt"), default="melt",
+                    help="adjoint workload: melted fraction at the end, or the left-wall "
+                         "Nusselt number averaged over the steps")
     ap.add_argument("--autotune", action="store_true",
                     help="batched workload: tune each cavity's stream-collide kernel first")
     return ap.parse_args(argv)
@@ -335,7 +338,7 @@ def batched(args, torch):
 
 def adjoint(args, torch):
     """The conduction slab (lbm_workloads.adjoint_slab, n x ny): `steps` steps
-    forward alone, then the same steps with the adjoint (lbm_adjoint_melt:
+    forward alone, then the same steps with the adjoint (lbm_adjoint:
     forward, reverse sweep, gradients back on the host), both from the same
     state; one JSON line, value = adjoint time / forward time."""
     import lbm_workloads as W
@@ -351,7 +354,7 @@ def adjoint(args, torch):
     reset()
     lat.step(args.warmup)                       # graphs captured, clocks up
     reset()
-    lat.adjoint_melt(max(args.warmup, 2))       # allocations and kernels warmed
+    lat.adjoint(max(args.warmup, 2), args.objective)   # allocations and kernels warmed
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reset()
     e0.record(stream)
@@ -363,10 +366,11 @@ def adjoint(args, torch):
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     with ClockSampler(vis.split(",")[0] if vis else "0") as clk:
         t0 = time.perf_counter()
-        J, dphi, dtw = lat.adjoint_melt(args.steps)
+        J, dphi, dtw = lat.adjoint(args.steps, args.objective)
         ms_adj = (time.perf_counter() - t0) * 1e3
     line = {
-        "metric": "adjoint time / forward time, melted fraction and its gradients",
+        "metric": "adjoint time / forward time, %s and its gradients" % (
+            "melted fraction" if args.objective == "melt" else "time-averaged hot-wall Nusselt"),
         "value": ms_adj / ms_fwd, "unit": "x", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_adj / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

@@ -192,6 +192,19 @@ int lbm_autotune(lbm_ctx* c, int trial_steps, int32_t* variant, int32_t* tiles_p
 int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32_t mu_sweeps,
                      float* d_phi, float* d_wall_T_left, double* J, int device_ptrs);
 
+/* Objectives of lbm_adjoint. */
+enum { LBM_OBJ_MELT = 0, LBM_OBJ_NUSSELT = 1 };
+
+/* lbm_adjoint_melt for a chosen objective: LBM_OBJ_MELT as there;
+ * LBM_OBJ_NUSSELT: the left-wall Nusselt number (lbm_reduce's out[3]: the
+ * second-order one-sided gradient -(-3 T_w + 4 T_1 - T_2)/2 times H/dT,
+ * averaged over the rows) after each of the nsteps steps, averaged over them;
+ * its gradient has a direct term in the wall profile.  The Nusselt objective
+ * needs nx >= 5.  Everything else as for lbm_adjoint_melt. */
+int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_every,
+                int32_t mu_sweeps, float* d_phi, float* d_wall_T_left, double* J,
+                int device_ptrs);
+
 /* Batches.  A batch advances several contexts together: each
  * lbm_batch_step replays one CUDA graph holding LBM_BATCH_STEPS steps of every
  * context, each context's kernels on its own branch, so small lattices fill the

@@ -1,5 +1,5 @@
-"""torch.autograd.Function for the melted fraction of a conduction run, its
-gradient from the CUDA adjoint (lbm_adjoint_melt)."""
+"""torch.autograd.Functions for objectives of a conduction run, their
+gradients from the CUDA adjoint (lbm_adjoint)."""
 import torch
 
 
@@ -16,6 +16,31 @@ class MeltedFraction(torch.autograd.Function):
         lattice.set_fields(phi.detach().cpu().numpy(), K, T0, fl0,
                            wall_T_left.detach().cpu().numpy())
         J, dphi, dtw = lattice.adjoint_melt(int(nsteps), int(checkpoint_every))
+        ctx.save_for_backward(torch.as_tensor(dphi, device=phi.device),
+                              torch.as_tensor(dtw, device=wall_T_left.device))
+        return torch.tensor(J, dtype=torch.float64, device=phi.device)
+
+    @staticmethod
+    def backward(ctx, grad_J):
+        dphi, dtw = ctx.saved_tensors
+        g = grad_J.to(dphi.dtype)
+        return g * dphi, g * dtw, None, None, None, None, None, None
+
+
+class HotWallNusselt(torch.autograd.Function):
+    """J = the left-wall Nusselt number after each of `nsteps` steps of
+    `lattice`, averaged over them, started from (T0, fl0) with the porosity
+    field phi and the left wall profile wall_T_left; backward returns dJ/dphi
+    and dJ/dwall_T_left from the adjoint.
+
+    Usage: J = HotWallNusselt.apply(phi, wall_T_left, lattice, K, T0, fl0, nsteps)
+    """
+
+    @staticmethod
+    def forward(ctx, phi, wall_T_left, lattice, K, T0, fl0, nsteps, checkpoint_every=0):
+        lattice.set_fields(phi.detach().cpu().numpy(), K, T0, fl0,
+                           wall_T_left.detach().cpu().numpy())
+        J, dphi, dtw = lattice.adjoint(int(nsteps), "nusselt", int(checkpoint_every))
         ctx.save_for_backward(torch.as_tensor(dphi, device=phi.device),
                               torch.as_tensor(dtw, device=wall_T_left.device))
         return torch.tensor(J, dtype=torch.float64, device=phi.device)

@@ -48,6 +48,8 @@ __device__ __forceinline__ float wt(const Dev& d, int i) { return i == 0 ? d.wt0
 //   lam_gpre = A^T lam_g+ per node
 //   lam_f(n)(y) = a(y) S(y)                       (wall: lam_f')
 //   lam_a(y) += -(f(n+1) - f(n))(y) S(y)
+//   plus the objective's direct terms in the state before the step (the
+//   Nusselt number's T_1, T_2 and T_w)
 //   walls: lam_g(x_f) += lam_gpre(x_b) - (sum_i w~_i lam_gpre_i(x_b)), and the
 //          Dirichlet value's adjoint is sum_i w~_i lam_gpre_i(x_b); the wall
 //          nodes' own populations do not reach the next step (the
@@ -222,7 +224,7 @@ __device__ __forceinline__ void pre_pops(const Dev& d, const AdjBuffers& b, cons
 }
 
 // one row segment per block (x along threads, y = blockIdx.y + k gridDim.y)
-__global__ void __launch_bounds__(AB) adj_full_kernel(Dev d, AdjBuffers b, Mat5 At,
+__global__ void __launch_bounds__(AB) adj_full_kernel(Dev d, AdjBuffers b, Mat5 At, NuSrc nu,
                                                       const float* __restrict__ f0,
                                                       const float* __restrict__ f1,
                                                       int* next_list, int* next_count) {
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(AB) adj_full_kernel(Dev d, AdjBuffers b, Mat5 
         float wl = 0.f;
 #pragma unroll
         for (int i = 0; i < 5; ++i) wl += wt(d, i) * pre[i];
-        b.lamtw[y] += wl;
+        b.lamtw[y] += wl + nu.tw;
       }
 #pragma unroll
       for (int k = 0; k < 5; ++k) b.lamgpre[k * n + s] = 0.f;
@@ -257,8 +259,9 @@ __global__ void __launch_bounds__(AB) adj_full_kernel(Dev d, AdjBuffers b, Mat5 
 #pragma unroll
       for (int k = 0; k < 5; ++k) pre[k] += pw[k] - wl;
     }
+    const float src = x == 1 ? nu.g1 : x == 2 ? nu.g2 : 0.f;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) b.lamgpre[k * n + s] = pre[k];
+    for (int k = 0; k < 5; ++k) b.lamgpre[k * n + s] = pre[k] + src;
     float S = 0.f;
 #pragma unroll
     for (int i = 0; i < 5; ++i) S += wt(d, i) * lp[i];
@@ -311,12 +314,13 @@ __global__ void adj_objective_kernel(Dev d, const double* part, int nparts, doub
   *out = acc / ((double)(d.nx - 2) * d.ny);
 }
 
-__global__ void adj_seed_kernel(Dev d, float* lamf, float* lamg) {
+__global__ void adj_seed_kernel(Dev d, float* lamf, float* lamg, bool melt, NuSrc nu) {
   const int s = blockIdx.x * AB + threadIdx.x;
   if (s >= (int)d.n) return;
   const int x = s % d.nx;
-  lamf[s] = (x != 0 && x != d.nx - 1) ? 1.f / ((float)(d.nx - 2) * d.ny) : 0.f;
-  for (int i = 0; i < 5; ++i) lamg[i * (int)d.n + s] = 0.f;
+  lamf[s] = (melt && x != 0 && x != d.nx - 1) ? 1.f / ((float)(d.nx - 2) * d.ny) : 0.f;
+  const float src = x == 1 ? nu.g1 : x == 2 ? nu.g2 : 0.f;
+  for (int i = 0; i < 5; ++i) lamg[i * (int)d.n + s] = src;
 }
 
 __global__ void adj_a_kernel(Dev d, float* a) {
@@ -327,8 +331,9 @@ __global__ void adj_a_kernel(Dev d, float* a) {
 
 static unsigned blocks(long long n) { return (unsigned)((n + AB - 1) / AB); }
 
-void adj_seed(const Dev& d, float* lamf, float* lamg, float* a, cudaStream_t s) {
-  adj_seed_kernel<<<blocks(d.n), AB, 0, s>>>(d, lamf, lamg);
+void adj_seed(const Dev& d, float* lamf, float* lamg, float* a, bool melt, NuSrc nu,
+              cudaStream_t s) {
+  adj_seed_kernel<<<blocks(d.n), AB, 0, s>>>(d, lamf, lamg, melt, nu);
   adj_a_kernel<<<blocks(d.n), AB, 0, s>>>(d, a);
 }
 
@@ -354,13 +359,14 @@ void adj_save(const Dev& d, float* base, unsigned* ctr, cudaStream_t s) {
 }
 
 void adj_step(const Dev& d, const AdjBuffers& b, const float* f0, const float* f1, int* list,
-              int* count, int* old_list, int* old_count, int mu_sweeps, cudaStream_t s) {
+              int* count, int* old_list, int* old_count, int mu_sweeps, NuSrc nu,
+              cudaStream_t s) {
   adj_band_kernel<<<1, BAND_THREADS, BAND_SMEM, s>>>(d, b, f1, list, count, old_count,
                                                      mu_sweeps);
   Mat5 At;
   for (int k = 0; k < 25; ++k) At.m[k] = b.At_host[k];
   const dim3 grid((d.nx + AB - 1) / AB, d.ny < 65535 ? d.ny : 65535);
-  adj_full_kernel<<<grid, AB, 0, s>>>(d, b, At, f0, f1, old_list, old_count);
+  adj_full_kernel<<<grid, AB, 0, s>>>(d, b, At, nu, f0, f1, old_list, old_count);
 }
 
 }  // namespace lbm

@@ -22,7 +22,21 @@ struct AdjBuffers {
 struct Mat5 {
   float m[25];
 };
-void adj_seed(const Dev& d, float* lamf, float* lamg, float* a, cudaStream_t s);
+// Objective terms the reverse sweep adds per state: the adjoint of the
+// populations at x = 1 and x = 2 (all five planes) and of the left wall
+// profile (the time-averaged left-wall Nusselt number: -2, 1/2 and 3/2 times
+// H / (dT rows N)); zero for the melted fraction.
+struct NuSrc {
+  float g1, g2, tw;
+};
+// the left-wall Nusselt number of the current state (lbm_reduce's out[3]),
+// added to acc[0] (lbm_aux.cu)
+void launch_wall_nusselt(const Dev& d, int layout, double* acc, cudaStream_t s);
+// a = phi dT / (sigma St); lam_g = the Nusselt terms of the last state; lam_f
+// = 1 / (non-wall nodes) on non-wall nodes for the melted fraction (melt),
+// else 0
+void adj_seed(const Dev& d, float* lamf, float* lamg, float* a, bool melt, NuSrc nu,
+              cudaStream_t s);
 // J into out[0]; out holds 129 doubles (the rest: partial sums)
 void adj_objective(const Dev& d, const float* fl, double* out, cudaStream_t s);
 // the band (non-wall nodes with 0 < f < 1), appended at list[*count]
@@ -31,12 +45,14 @@ void adj_list(const Dev& d, const float* f, int* list, int* count, cudaStream_t 
 void adj_save(const Dev& d, float* base, unsigned* ctr, cudaStream_t s);
 // One step of the reverse sweep, given f_l before (f0) and after (f1) it and
 // the band after it (list, count): from b.lamg / b.lamf (after the step) to
-// b.lamgpre / b.lamf (before it).  old_list / old_count hold the band the
+// b.lamgpre / b.lamf (before it), the Nusselt terms (nu) of the state before
+// it included.  old_list / old_count hold the band the
 // previous call solved on; they are emptied and refilled with the band before
 // this step, for the next call.  The caller swaps b.lamg and b.lamgpre and the
 // two lists.
 void adj_step(const Dev& d, const AdjBuffers& b, const float* f0, const float* f1, int* list,
-              int* count, int* old_list, int* old_count, int mu_sweeps, cudaStream_t s);
+              int* count, int* old_list, int* old_count, int mu_sweeps, NuSrc nu,
+              cudaStream_t s);
 // once per process before adj_step: the band kernel's shared-memory opt-in
 bool adj_init();
 

@@ -456,7 +456,7 @@ static bool capture_streams(lbm_ctx* c) {
 // listed tile); the tiles near the front run after the commit.  Everything
 // forked onto the second stream joins back before the last kernel.
 static int capture_body(lbm_ctx* c, int steps, float* keep_base = nullptr,
-                        unsigned* keep_ctr = nullptr) {
+                        unsigned* keep_ctr = nullptr, double* nu_acc = nullptr) {
   int nl = 0;
   for (int k = 0; k < steps; ++k) {
     const int par = k & 1;
@@ -479,6 +479,10 @@ static int capture_body(lbm_ctx* c, int steps, float* keep_base = nullptr,
     nl += 2;
     if (keep_base) {
       lbm::adj_save(c->d, keep_base, keep_ctr, c->cap);   // f_l after the step
+      nl += 1;
+    }
+    if (nu_acc) {
+      lbm::launch_wall_nusselt(c->d, 1 - par, nu_acc, c->cap);   // Nu after the step
       nl += 1;
     }
   }
@@ -919,15 +923,17 @@ struct DevMem {
 }  // namespace
 
 // A graph of `steps` (even) steps from parity 0 like capture(), each step
-// followed by lbm::adj_save of f_l.
-static cudaGraphExec_t capture_keep(lbm_ctx* c, int steps, float* base, unsigned* ctr) {
+// followed by lbm::adj_save of f_l (base non-null) and the Nusselt sum (nu_acc
+// non-null).
+static cudaGraphExec_t capture_keep(lbm_ctx* c, int steps, float* base, unsigned* ctr,
+                                    double* nu_acc) {
   if (!capture_streams(c)) return nullptr;
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
-  capture_body(c, steps, base, ctr);
+  capture_body(c, steps, base, ctr, nu_acc);
   if (cudaStreamEndCapture(c->cap, &g) != cudaSuccess || !g) {
     cudaGetLastError();
     return nullptr;
@@ -935,13 +941,66 @@ static cudaGraphExec_t capture_keep(lbm_ctx* c, int steps, float* base, unsigned
   return instantiate(g);
 }
 
+// Steps `steps` steps like lbm_step (graphs from parity 0, single steps
+// around them), each followed by the hooks of capture_keep; graphs kept in
+// `cache` for later calls with the same hooks.
+struct HookGraphs {
+  cudaGraphExec_t g[2] = {nullptr, nullptr};   // GRAPH_STEPS and 2 steps
+  ~HookGraphs() {
+    for (cudaGraphExec_t x : g)
+      if (x) cudaGraphExecDestroy(x);
+  }
+};
+
+static int step_hooked(lbm_ctx* c, int64_t steps, float* base, unsigned* ctr, double* nu_acc,
+                       HookGraphs& cache) {
+  auto direct = [&]() -> int {
+    LBM_TRY(step_direct(c));
+    if (base) lbm::adj_save(c->d, base, ctr, c->stream);
+    if (nu_acc) lbm::launch_wall_nusselt(c->d, c->parity, nu_acc, c->stream);
+    --steps;
+    return LBM_OK;
+  };
+  while (steps > 0 && (c->parity != 0 || c->graphs_off || steps < 2)) LBM_TRY(direct());
+  const int lens[2] = {GRAPH_STEPS, 2};
+  for (int k = 0; k < 2; ++k) {
+    if (steps < lens[k]) continue;
+    if (!cache.g[k]) cache.g[k] = capture_keep(c, lens[k], base, ctr, nu_acc);
+    if (!cache.g[k]) break;
+    while (steps >= lens[k]) {
+      LBM_CUDA(cudaGraphLaunch(cache.g[k], c->stream));
+      steps -= lens[k];
+      c->steps += lens[k];
+    }
+  }
+  while (steps > 0) LBM_TRY(direct());
+  return LBM_OK;
+}
+
 int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32_t mu_sweeps,
                      float* d_phi, float* d_wall_T_left, double* J, int device_ptrs) {
+  return lbm_adjoint(c, LBM_OBJ_MELT, nsteps, checkpoint_every, mu_sweeps, d_phi, d_wall_T_left,
+                     J, device_ptrs);
+}
+
+int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_every,
+                int32_t mu_sweeps, float* d_phi, float* d_wall_T_left, double* J,
+                int device_ptrs) {
   if (!c || nsteps < 1 || checkpoint_every < 0 || mu_sweeps < 0 || !d_phi || !d_wall_T_left || !J)
     return LBM_ERR_INVALID_ARG;
+  if (objective != LBM_OBJ_MELT && objective != LBM_OBJ_NUSSELT) return LBM_ERR_INVALID_ARG;
   const lbm_params& p = c->p;
   if (p.flow || c->timing || p.storage != LBM_STORAGE_FP32 || c->d.alpha_var) return LBM_ERR_INVALID_ARG;
   if (!c->d.per_y || c->d.per_x || p.bc[0] != LBM_BC_DIRICHLET) return LBM_ERR_INVALID_ARG;
+  const bool melt = objective == LBM_OBJ_MELT;
+  if (!melt && c->d.nx < 5) return LBM_ERR_INVALID_ARG;   // x = 1, 2 interior
+  // Nusselt objective: J = (1/N) sum over the states after steps 1..N of
+  // -(-3 T_w + 4 T_1 - T_2)/2 H/dT averaged over the ny rows
+  lbm::NuSrc nu{0.f, 0.f, 0.f};
+  if (!melt) {
+    const double k = (double)c->d.H_over_dT / ((double)c->d.ny * (double)nsteps);
+    nu = {(float)(-2.0 * k), (float)(0.5 * k), (float)(1.5 * k)};
+  }
   const int sweeps = mu_sweeps > 0 ? mu_sweeps : 64;
   const size_t n = (size_t)c->d.n, st = 6 * n;   // a checkpoint: g (5 planes) and f_l
   if (!lbm::adj_init()) return LBM_ERR_CUDA;
@@ -977,10 +1036,11 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
   int* lists[2] = {reinterpret_cast<int*>(mem.get(n)), reinterpret_cast<int*>(mem.get(n))};
   int* counts = reinterpret_cast<int*>(mem.get(2));
   unsigned* ctr = reinterpret_cast<unsigned*>(mem.get(2));
+  double* nu_acc = reinterpret_cast<double*>(mem.get(2));
   double* dJ = reinterpret_cast<double*>(mem.get(2 * 129));
   if (!flS || (!keep_all && (!cps || !fin)) || !b.a || !b.lamg || !b.lamf || !b.rhs ||
       !b.mu0 || !b.mu1 || !b.lamgpre || !b.lama || !b.lamtw || !b.At || !b.pos || !lists[0] ||
-      !lists[1] || !counts || !ctr || !dJ)
+      !lists[1] || !counts || !ctr || !nu_acc || !dJ)
     return LBM_ERR_OOM;
   // transposed collision matrix with u = 0: g+ = A g,
   // A = N^-1 [(I - Theta) N + Theta e 1^T], e = (1, 0, 0, varpi, 0), Eq. (32)-(37)
@@ -1018,46 +1078,29 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
       for (cudaGraphExec_t g : v) cudaGraphExecDestroy(g);
     }
   } graphs;
+  HookGraphs fwd_graphs;
   const int64_t steps0 = c->steps;
-  lbm::adj_seed(c->d, b.lamf, b.lamg, b.a, c->stream);   // a is needed from here on
+  lbm::adj_seed(c->d, b.lamf, b.lamg, b.a, melt, nu, c->stream);   // a is needed from here on
+  LBM_CUDA(cudaMemsetAsync(nu_acc, 0, sizeof(double), c->stream));
+  double* const acc = melt ? nullptr : nu_acc;
   if (keep_all) {
     // forward, f_l after every step into flS (its start at index 0)
     LBM_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), c->stream));
     lbm::adj_save(c->d, flS, ctr, c->stream);
-    const bool use_graphs = !c->graphs_off;
-    int64_t left = nsteps;
-    auto direct = [&]() -> int {
-      LBM_TRY(step_direct(c));
-      lbm::adj_save(c->d, flS, ctr, c->stream);
-      --left;
-      return LBM_OK;
-    };
-    while (left > 0 && (c->parity != 0 || !use_graphs || left < 2)) LBM_TRY(direct());
-    for (int len : {GRAPH_STEPS, 2}) {
-      if (left < len) continue;
-      cudaGraphExec_t g = capture_keep(c, len, flS, ctr);
-      if (!g) break;
-      graphs.v.push_back(g);
-      while (left >= len) {
-        LBM_CUDA(cudaGraphLaunch(g, c->stream));
-        left -= len;
-        c->steps += len;
-      }
-    }
-    while (left > 0) LBM_TRY(direct());
+    LBM_TRY(step_hooked(c, nsteps, flS, ctr, acc, fwd_graphs));
   } else {
     // forward, keeping the whole state every K steps
     LBM_TRY(save(cps));
     for (int64_t j = 1; j < ncp; ++j) {
-      LBM_TRY(lbm_step(c, K));
+      LBM_TRY(step_hooked(c, K, nullptr, nullptr, acc, fwd_graphs));
       LBM_TRY(save(cps + (size_t)j * st));
     }
     const int64_t done = (ncp - 1) * K;
-    if (nsteps > done) LBM_TRY(lbm_step(c, nsteps - done));
+    if (nsteps > done) LBM_TRY(step_hooked(c, nsteps - done, nullptr, nullptr, acc, fwd_graphs));
     LBM_TRY(save(fin));
   }
   const float* fl_end = keep_all ? flS + (size_t)nsteps * n : fin + 5 * n;
-  lbm::adj_objective(c->d, fl_end, dJ, c->stream);
+  if (melt) lbm::adj_objective(c->d, fl_end, dJ, c->stream);
   // reverse sweep
   LBM_CUDA(cudaMemsetAsync(b.lama, 0, n * sizeof(float), c->stream));
   LBM_CUDA(cudaMemsetAsync(b.lamtw, 0, c->d.ny * sizeof(float), c->stream));
@@ -1069,7 +1112,7 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
     for (int64_t m = hi - 1; m >= lo; --m) {
       const float* f0 = F + (size_t)(m - lo) * n;
       lbm::adj_step(c->d, b, f0, f0 + n, lists[cur], counts + cur, lists[1 - cur],
-                    counts + 1 - cur, sweeps, sm);
+                    counts + 1 - cur, sweeps, nu, sm);
       std::swap(b.lamg, b.lamgpre);
       cur ^= 1;
     }
@@ -1151,8 +1194,13 @@ int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32
   LBM_CUDA(cudaMemcpyAsync(la.data(), b.lama, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
   LBM_CUDA(cudaMemcpyAsync(lt.data(), b.lamtw, c->d.ny * sizeof(float), cudaMemcpyDeviceToHost,
                            c->stream));
-  LBM_CUDA(cudaMemcpyAsync(J, dJ, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(cudaMemcpyAsync(J, melt ? dJ : nu_acc, sizeof(double), cudaMemcpyDeviceToHost,
+                           c->stream));
   LBM_CUDA(cudaStreamSynchronize(c->stream));
+  // (the reverse sweep added the Nusselt number's direct term in T_w once per
+  // reversed step, for the states 0..N-1 instead of 1..N: the same constant
+  // N times)
+  if (!melt) *J /= (double)nsteps;
   for (size_t s = 0; s < n; ++s) la[s] *= c->d.lat;
   const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
   LBM_CUDA(cudaMemcpy(d_phi, la.data(), n * sizeof(float), kind));

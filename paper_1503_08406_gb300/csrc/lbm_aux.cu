@@ -1,6 +1,6 @@
 // Utility kernels: initial equilibria, macroscopic outputs, FP64 reductions,
 // checkpoint gather/scatter and input validation.
-#include "lbm_internal.cuh"
+#include "lbm_adjoint.cuh"
 
 namespace lbm {
 
@@ -158,6 +158,28 @@ __global__ void __launch_bounds__(RB) reduce_kernel(Dev d, int layout, double* p
     for (int k = 0; k < 6; ++k) partials[blockIdx.x * 6 + k] = sh[k][0];
 }
 
+// The left-wall Nusselt number of the current state (the rows and the
+// formula of reduce_kernel), added to acc[0]; one block, fixed summation order.
+__global__ void __launch_bounds__(RB) wall_nusselt_kernel(Dev d, int layout, double* acc) {
+  __shared__ double sh[RB];
+  const int tid = threadIdx.x;
+  const int y0 = d.wall_b ? 1 : 0, y1 = d.wall_t ? d.ny - 1 : d.ny;
+  double v = 0.0;
+  if (d.wall_l && d.nx >= 3)
+    for (int y = y0 + tid; y < y1; y += RB) {
+      const double T0 = node_T(d, 0, y, layout), T1 = node_T(d, 1, y, layout),
+                   T2 = node_T(d, 2, y, layout);
+      v += -(-3.0 * T0 + 4.0 * T1 - T2) * 0.5 * (double)d.H_over_dT;
+    }
+  sh[tid] = v;
+  __syncthreads();
+  for (int w = RB / 2; w > 0; w >>= 1) {
+    if (tid < w) sh[tid] += sh[tid + w];
+    __syncthreads();
+  }
+  if (tid == 0 && d.wall_l && d.nx >= 3 && y1 > y0) acc[0] += sh[0] / (double)(y1 - y0);
+}
+
 __global__ void reduce_final_kernel(const double* partials, int nblocks, double* out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double t[6] = {0, 0, 0, 0, 0, 0};
@@ -231,6 +253,9 @@ void launch_reduce(const Dev& d, int layout, double* partials, double* out, int 
                    cudaStream_t s) {
   reduce_kernel<<<nblocks, RB, 0, s>>>(d, layout, partials);
   reduce_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, out);
+}
+void launch_wall_nusselt(const Dev& d, int layout, double* acc, cudaStream_t s) {
+  wall_nusselt_kernel<<<1, RB, 0, s>>>(d, layout, acc);
 }
 void launch_get_state(const Dev& d, int layout, float* f, float* g, cudaStream_t s) {
   get_state_kernel<<<grid1(d.n, 256), 256, 0, s>>>(d, layout, f, g);

@@ -133,6 +133,8 @@ def load():
                                      ctypes.POINTER(ctypes.c_int32)]
         lib.lbm_adjoint_melt.argtypes = [_VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                          _VP, _VP, _DP, ctypes.c_int]
+        lib.lbm_adjoint.argtypes = [_VP, ctypes.c_int, ctypes.c_int64, ctypes.c_int32,
+                                    ctypes.c_int32, _VP, _VP, _DP, ctypes.c_int]
         lib.lbm_batch_create.argtypes = [ctypes.POINTER(_VP), ctypes.c_int, _VP,
                                          ctypes.POINTER(_VP)]
         lib.lbm_batch_step.argtypes = [_VP, ctypes.c_int64]
@@ -276,10 +278,26 @@ class Lattice:
                "lbm_autotune")
         return v.value, t.value
 
+    OBJECTIVES = {"melt": 0, "nusselt": 1}
+
+    def adjoint(self, nsteps: int, objective: str = "melt", checkpoint_every: int = 0,
+                mu_sweeps: int = 0):
+        """Run nsteps steps; return the objective and its gradient with respect
+        to the porosity field ([ny, nx]) and the left wall's temperature
+        profile ([ny]) (lbm_adjoint in include/lbm.h).  objective "melt": the
+        melted fraction after the steps; "nusselt": the left-wall Nusselt
+        number after each step, averaged over the steps."""
+        dphi = np.zeros((self.ny, self.nx), dtype=np.float32)
+        dtw = np.zeros(self.ny, dtype=np.float32)
+        J = ctypes.c_double()
+        _check(self.lib.lbm_adjoint(self._h, self.OBJECTIVES[objective], int(nsteps),
+                                    int(checkpoint_every), int(mu_sweeps), dphi.ctypes.data,
+                                    dtw.ctypes.data, ctypes.byref(J), 0), "lbm_adjoint")
+        return J.value, dphi, dtw
+
     def adjoint_melt(self, nsteps: int, checkpoint_every: int = 0, mu_sweeps: int = 0):
-        """Run nsteps steps; return the melted fraction after them and its
-        gradient with respect to the porosity field ([ny, nx]) and the left
-        wall's temperature profile ([ny]) (lbm_adjoint_melt in include/lbm.h)."""
+        """The melted fraction after nsteps steps and its gradients
+        (lbm_adjoint_melt in include/lbm.h)."""
         dphi = np.zeros((self.ny, self.nx), dtype=np.float32)
         dtw = np.zeros(self.ny, dtype=np.float32)
         J = ctypes.c_double()

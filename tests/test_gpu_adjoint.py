@@ -112,9 +112,53 @@ def test_autograd_function(lbm, reference):
     assert np.abs(phi_t.grad.numpy() - 2 * dphi_ref).max() < 2e-3 * np.abs(dphi_ref).max()
 
 
+@pytest.fixture(scope="module")
+def reference_nu(oracle_mod):
+    from oracle.adjoint_ref import ConductionRef
+    w, params, Tw, phi = _case()
+    return ConductionRef(w.nx, w.ny, params).gradients(STEPS, w.T0, w.fl0, phi, Tw,
+                                                        objective="nusselt")
+
+
+def test_nusselt_adjoint_matches_fp64_reference(lbm, reference_nu):
+    w, params, Tw, phi = _case()
+    J_ref, dphi_ref, dtw_ref = reference_nu
+    lat = _lattice(lbm, w, params, phi, Tw)
+    J, dphi, dtw = lat.adjoint(STEPS, "nusselt")
+    assert lat.status() == 0
+    assert abs(J - J_ref) < 1e-5 * abs(J_ref), (J, J_ref)
+    assert np.abs(dtw - dtw_ref).max() < 1e-3 * np.abs(dtw_ref).max(), (dtw, dtw_ref)
+    assert np.abs(dphi - dphi_ref).max() < 1e-3 * np.abs(dphi_ref).max(), \
+        (np.abs(dphi - dphi_ref).max(), np.abs(dphi_ref).max())
+    # the same run through the checkpointed path, bit for bit
+    again = _lattice(lbm, w, params, phi, Tw).adjoint(STEPS, "nusselt", checkpoint_every=37)
+    assert again[0] == J and np.array_equal(again[1], dphi) and np.array_equal(again[2], dtw)
+
+
+def test_nusselt_autograd_function(lbm, reference_nu):
+    import torch
+    from paper_1503_08406_gb300.autograd import HotWallNusselt
+    w, params, Tw, phi = _case()
+    lat = lbm.Lattice(w.nx, w.ny, **params)
+    phi_t = torch.tensor(phi, dtype=torch.float32, requires_grad=True)
+    tw_t = torch.tensor(Tw, dtype=torch.float32, requires_grad=True)
+    (0.5 * HotWallNusselt.apply(phi_t, tw_t, lat, w.K, w.T0, w.fl0, STEPS)).backward()
+    _, dphi_ref, dtw_ref = reference_nu
+    assert np.abs(tw_t.grad.numpy() - 0.5 * dtw_ref).max() < 2e-3 * np.abs(dtw_ref).max()
+    assert np.abs(phi_t.grad.numpy() - 0.5 * dphi_ref).max() < 2e-3 * np.abs(dphi_ref).max()
+
+
 def test_unsupported_configuration_rejected(lbm):
     w = W.melted_cavity(48)   # flow on, walls on all sides
     lat = lbm.Lattice(w.nx, w.ny, **w.params)
     lat.set_fields(w.phi, w.K, w.T0, w.fl0)
     with pytest.raises(lbm.LBMError):
         lat.adjoint_melt(10)
+    w, params, Tw, phi = _case()
+    narrow = W.two_phase_slab(1.0, nx=4, ny=4)
+    p4 = dict(narrow.params)
+    p4.pop("alpha_ratio")
+    lat = lbm.Lattice(4, 4, **p4)
+    lat.set_fields(narrow.phi, narrow.K, narrow.T0, narrow.fl0)
+    with pytest.raises(lbm.LBMError):
+        lat.adjoint(10, "nusselt")   # x = 2 would be the right wall
