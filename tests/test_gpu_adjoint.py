@@ -162,3 +162,24 @@ def test_unsupported_configuration_rejected(lbm):
     lat.set_fields(narrow.phi, narrow.K, narrow.T0, narrow.fl0)
     with pytest.raises(lbm.LBMError):
         lat.adjoint(10, "nusselt")   # x = 2 would be the right wall
+
+
+@pytest.mark.parametrize("objective", ["melt", "nusselt"])
+def test_adjoint_64x64_against_fp64_reference(lbm, oracle_mod, objective):
+    """A 64 x 64 slab with seeded porosity and a varying wall profile, 400
+    steps: the FP64 reference (autograd through every step and inner
+    iteration) against the CUDA adjoint, both objectives."""
+    from oracle.adjoint_ref import ConductionRef
+    w = W.adjoint_slab(64, 64, seed=1)
+    phi = w.phi.astype(np.float32).astype(np.float64)
+    tw = w.wall_T_left.astype(np.float32).astype(np.float64)
+    J_ref, dphi_ref, dtw_ref = ConductionRef(w.nx, w.ny, w.params).gradients(
+        400, w.T0, w.fl0, phi, tw, objective=objective)
+    lat = lbm.Lattice(w.nx, w.ny, **w.params)
+    lat.set_fields(phi, w.K, w.T0, w.fl0, tw)
+    J, dphi, dtw = lat.adjoint(400, objective)
+    assert lat.status() == 0
+    assert abs(J - J_ref) < 1e-5 * abs(J_ref), (J, J_ref)
+    assert np.abs(dtw - dtw_ref).max() < 1e-3 * np.abs(dtw_ref).max()
+    assert np.abs(dphi - dphi_ref).max() < 1e-3 * np.abs(dphi_ref).max()
+    assert (np.abs(dphi_ref) > 0).sum() > 64   # the front has crossed several columns
