@@ -1,5 +1,7 @@
 // Adjoint of the conduction step (flow lattice off): the reverse sweep of one
-// time step for the gradient of an objective of the final liquid fraction.
+// time step for the gradient of an objective (the final melted fraction, or
+// the left-wall Nusselt number averaged over the steps) with respect to the
+// porosity field and the left wall's temperature profile.
 //
 // Forward map of one step, natural layout (population i of node x at slot
 // (x, i)), written as the composition the adjoint reverses:
@@ -323,6 +325,11 @@ __global__ void adj_seed_kernel(Dev d, float* lamf, float* lamg, bool melt, NuSr
   for (int i = 0; i < 5; ++i) lamg[i * (int)d.n + s] = src;
 }
 
+__global__ void adj_scale_kernel(long long n, float* v, float k) {
+  const long long s = blockIdx.x * (long long)AB + threadIdx.x;
+  if (s < n) v[s] *= k;
+}
+
 __global__ void adj_a_kernel(Dev d, float* a) {
   const int s = blockIdx.x * AB + threadIdx.x;
   if (s >= (int)d.n) return;
@@ -335,6 +342,10 @@ void adj_seed(const Dev& d, float* lamf, float* lamg, float* a, bool melt, NuSrc
               cudaStream_t s) {
   adj_seed_kernel<<<blocks(d.n), AB, 0, s>>>(d, lamf, lamg, melt, nu);
   adj_a_kernel<<<blocks(d.n), AB, 0, s>>>(d, a);
+}
+
+void adj_scale(long long n, float* v, float k, cudaStream_t s) {
+  adj_scale_kernel<<<(unsigned)((n + AB - 1) / AB), AB, 0, s>>>(n, v, k);
 }
 
 void adj_objective(const Dev& d, const float* fl, double* out, cudaStream_t s) {

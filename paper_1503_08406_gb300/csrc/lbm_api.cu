@@ -1189,11 +1189,11 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
     c->steps = steps0 + nsteps;
   }
   LBM_CUDA(cudaGetLastError());
-  // d J / d phi = (dT / (sigma St)) d J / d a
-  std::vector<float> la(n), lt(c->d.ny);
-  LBM_CUDA(cudaMemcpyAsync(la.data(), b.lama, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
-  LBM_CUDA(cudaMemcpyAsync(lt.data(), b.lamtw, c->d.ny * sizeof(float), cudaMemcpyDeviceToHost,
-                           c->stream));
+  // d J / d phi = (dT / (sigma St)) d J / d a, straight into the caller's arrays
+  lbm::adj_scale((long long)n, b.lama, c->d.lat, c->stream);
+  const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  LBM_CUDA(cudaMemcpyAsync(d_phi, b.lama, n * sizeof(float), kind, c->stream));
+  LBM_CUDA(cudaMemcpyAsync(d_wall_T_left, b.lamtw, c->d.ny * sizeof(float), kind, c->stream));
   LBM_CUDA(cudaMemcpyAsync(J, melt ? dJ : nu_acc, sizeof(double), cudaMemcpyDeviceToHost,
                            c->stream));
   LBM_CUDA(cudaStreamSynchronize(c->stream));
@@ -1201,9 +1201,5 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
   // reversed step, for the states 0..N-1 instead of 1..N: the same constant
   // N times)
   if (!melt) *J /= (double)nsteps;
-  for (size_t s = 0; s < n; ++s) la[s] *= c->d.lat;
-  const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
-  LBM_CUDA(cudaMemcpy(d_phi, la.data(), n * sizeof(float), kind));
-  LBM_CUDA(cudaMemcpy(d_wall_T_left, lt.data(), c->d.ny * sizeof(float), kind));
   return LBM_OK;
 }
