@@ -166,6 +166,23 @@ def test_parity_cavity_10000_steps(lbm, oracle_mod):
     assert abs(r_g["nu_hot"] / r_o["nu_hot"] - 1) < 1e-4
 
 
+def test_porous_gallium_cavity_matches_oracle(lbm, oracle_mod):
+    """Sec. 4.3's parameter set (200^2, Ra = 8.409e5, Pr = 0.0208,
+    tau_nu = 0.5054, St = 0.1241): u, T and f_l within 1e-4 of the FP64
+    oracle after 4,000 steps, the melted fraction and hot-wall Nusselt number
+    too."""
+    w = _f32(W.porous_gallium_cavity(200))
+    steps = 4000
+    lat = _gpu(lbm, w, steps)
+    o = _ora(oracle_mod, w, steps)
+    err = _errors(lat.macros(), o.macros())
+    assert max(err.values()) < 1e-4, err
+    r_g, r_o = lat.reduce(), o.reduce()
+    assert r_o["melt_frac"] > 0.005   # the front has left the wall
+    assert abs(r_g["melt_frac"] / r_o["melt_frac"] - 1) < 1e-4
+    assert abs(r_g["nu_hot"] / r_o["nu_hot"] - 1) < 1e-4
+
+
 def test_full_size_cavity_matches_oracle(lbm, oracle_mod):
     """2048^2 (the benchmark size), left third melted so flow runs on a
     third of the lattice: full-field comparison after 3 steps."""

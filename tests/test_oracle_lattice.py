@@ -253,3 +253,20 @@ def test_theta_follows_liquid_fraction(oracle_mod):
     o = oracle_mod.Oracle(w.nx, w.ny, **w.params)
     for fl, alpha in ((0.0, 0.02), (1.0, 0.2), (0.25, 0.25 * 0.2 + 0.75 * 0.02)):
         assert abs(o.theta_T(fl) - 1.0 / (0.5 + alpha / 0.2)) < 1e-14
+
+
+def test_porous_gallium_cavity_relaxation_times(oracle_mod):
+    """Sec. 4.3's parameter set through the oracle's derivation of tau_nu and
+    tau_T (Ma = 0.1, J = 1, H = 200, Pr = 0.0208, Ra = 8.409e5,
+    lambda = 0.2719, sigma = 0.8604, c_s^2 = 1/3, c_sT^2 = 1/5): worked out by
+    hand from the section's two formulas, tau_nu = 0.5054482 and
+    tau_T = 0.6379572; the thermal diffusivity alpha_l = nu_l / Pr = 0.0873103
+    and the latent coefficient a = phi / (sigma St) = 3.605691."""
+    w = W.porous_gallium_cavity(200)
+    o = oracle_mod.Oracle(w.nx, w.ny, **w.params)
+    d = o.derived()
+    assert abs(d["tau_nu"] - 0.5054482) < 1e-7
+    assert abs(d["tau_T"] - 0.6379572) < 1e-7
+    assert abs(d["nu_l"] / 0.0208 - 0.0873103) < 1e-7
+    assert abs(0.385 * d["lat"] - 3.605691) < 1e-6
+    assert abs(w.params["T_s"] - 0.3712) < 1e-12 and abs(w.params["T_l"] - 0.4112) < 1e-12
