@@ -32,6 +32,13 @@
  *  - with alpha_l != alpha_s (Sec. 4.1), tau_T = 1/2 + alpha_e/(sigma c_sT^2),
  *    alpha_e = alpha_l f_l + alpha_s (1 - f_l), per node; a wall node relaxes
  *    at the rate of the inward neighbour it extrapolates from.
+ *  - with sigma_solid set, sigma follows Eq. (7), linear in f_l:
+ *    sigma(f_l) = sigma_s + f_l (sigma_l - sigma_s), evaluated at f_l(n) per
+ *    node for the step, in tau_T, in n^eq of Eq. (34) and in the latent
+ *    coefficient a = phi dT / (sigma St) of Eq. (38); the given tau_T (or the
+ *    one derived from lambda) belongs to the liquid, alpha_l = sigma_l c_sT^2
+ *    (tau_T - 1/2).  A wall node takes its inward neighbour's sigma, as for
+ *    tau_T.
  */
 #include "lbm_oracle.h"
 
@@ -86,8 +93,9 @@ struct ora_ctx {
   double *phi, *K, *wallTl;
   double *f, *fpost, *fnew; /* [9][n] */
   double *g, *gpre, *gpost, *gstar, *gtmp; /* [5][n] */
-  double *fl, *fk, *fk1, *ux, *uy, *T, *Tk, *a;
+  double *fl, *fk, *fk1, *ux, *uy, *T, *Tk, *a; /* a: of the step under way */
   unsigned char *wall, *active;
+  int sigma_var; /* sigma follows f_l (sigma_solid set and != sigma) */
   int64_t inner_total;
 };
 
@@ -170,23 +178,36 @@ void ora_force_moments(const ora_ctx* c, double ux, double uy, double Fx, double
   out[8] = rho0 * (ux * Fy + uy * Fx) / varphi;
 }
 
+/* sigma of a node with liquid fraction fl: Eq. (7) is linear in f_l */
+static double sigma_of(const ora_ctx* c, double fl) {
+  if (!c->sigma_var) return c->p.sigma;
+  return c->p.sigma_solid + fl * (c->p.sigma - c->p.sigma_solid);
+}
+
 /* Eq. (39), with the convective term switched by vartheta as in Eq. (34) */
-void ora_geq(const ora_ctx* c, double T, double ux, double uy, double out[5]) {
+static void geq_s(const ora_ctx* c, double T, double ux, double uy, double sig, double out[5]) {
   double th = c->p.flow ? 1.0 : 0.0;
   for (int i = 0; i < 5; ++i) {
     double eu = EX5[i] * ux + EY5[i] * uy;
-    out[i] = c->wt[i] * T * (1 + th * eu / (c->p.sigma * c->csT2));
+    out[i] = c->wt[i] * T * (1 + th * eu / (sig * c->csT2));
   }
+}
+void ora_geq(const ora_ctx* c, double T, double ux, double uy, double out[5]) {
+  geq_s(c, T, ux, uy, c->p.sigma, out);
 }
 
 /* Eq. (34) */
-void ora_thermal_meq(const ora_ctx* c, double T, double ux, double uy, double out[5]) {
+static void thermal_meq_s(const ora_ctx* c, double T, double ux, double uy, double sig,
+                          double out[5]) {
   double th = c->p.flow ? 1.0 : 0.0;
   out[0] = T;
-  out[1] = th * ux * T / c->p.sigma;
-  out[2] = th * uy * T / c->p.sigma;
+  out[1] = th * ux * T / sig;
+  out[2] = th * uy * T / sig;
   out[3] = c->p.varpi * T;
   out[4] = 0;
+}
+void ora_thermal_meq(const ora_ctx* c, double T, double ux, double uy, double out[5]) {
+  thermal_meq_s(c, T, ux, uy, c->p.sigma, out);
 }
 
 /* Permeability and inertial coefficient at varphi = phi f_l, Eq. (6). */
@@ -268,22 +289,27 @@ void ora_collide_flow(const ora_ctx* c, const double f[9], double T, double fl, 
 /* Eq. (35), (38): collision with the latent source S~ = (S0, 0, 0, varpi S0, 0). */
 double ora_theta_T(const ora_ctx* c, double fl) {
   const double r = c->p.alpha_ratio;
-  if (!(r > 0) || r == 1.0) return c->theta[1];
-  /* alpha_e / alpha_l = fl + (1 - fl) alpha_s / alpha_l */
-  return 1.0 / (0.5 + (c->tau_T - 0.5) * (fl + (1.0 - fl) / r));
+  const int two_alpha = (r > 0) && r != 1.0;
+  if (!two_alpha && !c->sigma_var) return c->theta[1];
+  /* alpha_e / alpha_l = fl + (1 - fl) alpha_s / alpha_l; tau_T - 1/2 =
+   * alpha_e / (sigma(fl) c_sT^2) with alpha_l = sigma_l c_sT^2 (tau_T,l - 1/2) */
+  const double ae = two_alpha ? fl + (1.0 - fl) / r : 1.0;
+  if (!c->sigma_var) return 1.0 / (0.5 + (c->tau_T - 0.5) * ae);
+  return 1.0 / (0.5 + (c->tau_T - 0.5) * ae * (c->p.sigma / sigma_of(c, fl)));
 }
 
-/* Eq. (35), (38) with the diffusivity rate za for the two flux moments */
+/* Eq. (35), (38) with the diffusivity rate za for the two flux moments and the
+ * node's sigma in n^eq */
 static void collide_thermal(const ora_ctx* c, const double g[5], double ux, double uy,
-                            double src0, double za, double gpost[5]);
+                            double src0, double za, double sig, double gpost[5]);
 
 void ora_collide_thermal(const ora_ctx* c, const double g[5], double ux, double uy, double src0,
                          double gpost[5]) {
-  collide_thermal(c, g, ux, uy, src0, c->theta[1], gpost);
+  collide_thermal(c, g, ux, uy, src0, c->theta[1], c->p.sigma, gpost);
 }
 
 static void collide_thermal(const ora_ctx* c, const double g[5], double ux, double uy,
-                            double src0, double za, double gpost[5]) {
+                            double src0, double za, double sig, double gpost[5]) {
   double T = 0;
   for (int i = 0; i < 5; ++i) T += g[i];
   double n[5], neq[5], np[5];
@@ -291,7 +317,7 @@ static void collide_thermal(const ora_ctx* c, const double g[5], double ux, doub
     n[k] = 0;
     for (int i = 0; i < 5; ++i) n[k] += N5[k][i] * g[i];
   }
-  ora_thermal_meq(c, T, ux, uy, neq);
+  thermal_meq_s(c, T, ux, uy, sig, neq);
   double St[5] = {src0, 0, 0, c->p.varpi * src0, 0};
   const double th[5] = {c->theta[0], za, za, c->theta[3], c->theta[4]};
   for (int k = 0; k < 5; ++k) np[k] = n[k] - th[k] * (n[k] - neq[k]) + St[k];
@@ -334,6 +360,8 @@ static int derive(ora_ctx* c) {
   if (p->J <= 0) p->J = 1;
   if (p->lambda_ <= 0) p->lambda_ = 1;
   if (p->sigma <= 0) return ORA_ERR_INVALID_ARG;
+  if (p->sigma_solid < 0) return ORA_ERR_INVALID_ARG;
+  c->sigma_var = p->sigma_solid > 0 && p->sigma_solid != p->sigma;
   if (p->St <= 0) return ORA_ERR_INVALID_ARG;
   if (!(p->varpi > -4 && p->varpi < 1)) return ORA_ERR_INVALID_ARG;
   c->csT2 = (4 + p->varpi) / 10.0; /* Eq. (39) */
@@ -479,6 +507,7 @@ int ora_set_fields(ora_ctx* c, const double* phi, const double* K, const double*
     c->K[s] = K[s];
     c->fl[s] = fl0[s];
     c->a[s] = phi[s] * c->lat; /* a = phi L/(sigma c_pl), Eq. (38), in temperature units */
+    if (c->sigma_var) c->a[s] = phi[s] * c->p.dT / (sigma_of(c, fl0[s]) * c->p.St);
     double feq[9], geq[5];
     ora_feq(c, c->p.rho0, 0, 0, 1, feq);
     ora_geq(c, T0[s], 0, 0, geq);
@@ -601,8 +630,9 @@ static void thermal_walls(ora_ctx* c) {
         double Tf = sum5(c->gpre, n, sf);
         double Tw = wall_temperature(c, x, y, Tf);
         double eqw[5], eqf[5];
-        ora_geq(c, Tw, 0, 0, eqw);
-        ora_geq(c, Tf, c->ux[sf], c->uy[sf], eqf);
+        const double sig = sigma_of(c, c->fl[sf]);
+        geq_s(c, Tw, 0, 0, sig, eqw);
+        geq_s(c, Tf, c->ux[sf], c->uy[sf], sig, eqf);
         for (int i = 0; i < 5; ++i) c->gpre[i * n + s] = eqw[i] + c->gpre[i * n + sf] - eqf[i];
       }
   }
@@ -623,7 +653,7 @@ static void thermal_collide_stream(ora_ctx* c, const double* src, double* out) {
       /* tau_T from f_l(n); a wall node, whose populations the extrapolation
        * took from its inward neighbour, relaxes at that neighbour's rate */
       const double flt = c->wall[s] ? c->fl[inward(c, x, y)] : c->fl[s];
-      collide_thermal(c, gin, ux, uy, s0, ora_theta_T(c, flt), gout);
+      collide_thermal(c, gin, ux, uy, s0, ora_theta_T(c, flt), sigma_of(c, flt), gout);
       for (int i = 0; i < 5; ++i) c->gpost[i * n + s] = gout[i];
     }
   /* streaming, Eq. (36); populations leaving the domain are dropped and the
@@ -642,6 +672,9 @@ static void thermal_collide_stream(ora_ctx* c, const double* src, double* out) {
 
 static int thermal_step(ora_ctx* c, int literal) {
   const int n = c->n, nx = c->nx, ny = c->ny;
+  if (c->sigma_var) /* a = phi dT / (sigma(f_l(n)) St) for this step, Eq. (38) */
+    for (int s = 0; s < n; ++s)
+      c->a[s] = c->phi[s] * c->p.dT / (sigma_of(c, c->fl[s]) * c->p.St);
   memcpy(c->gpre, c->g, sizeof(double) * 5 * (size_t)n);
   thermal_walls(c);
   /* source-free collision and streaming */
@@ -781,7 +814,9 @@ void ora_reduce(const ora_ctx* c, double out[4]) {
     if (c->wall[s]) continue;
     double T = sum5(c->g, n, s);
     for (int i = 0; i < 9; ++i) mass += c->f[i * n + s];
-    ent += T + c->a[s] * c->fl[s];
+    const double a = c->sigma_var ? c->phi[s] * c->p.dT / (sigma_of(c, c->fl[s]) * c->p.St)
+                                  : c->a[s];
+    ent += T + a * c->fl[s];
     melt += c->fl[s];
     cnt++;
   }

@@ -50,12 +50,15 @@ typedef struct {
   int32_t max_inner_iters;
   double  inner_tol;
   double  alpha_ratio;  /* alpha_l / alpha_s (Sec. 4.1); 0 or 1: one diffusivity */
+  double  sigma_solid;  /* sigma at f_l = 0, Eq. (7) (sigma above is its value at
+                           f_l = 1); 0: sigma everywhere */
 } ora_params;
 
 typedef struct ora_ctx ora_ctx;
 
 /* Relaxation rate zeta_alpha = 1/tau_T of a node with liquid fraction fl (Sec. 4.1):
- * alpha_e = alpha_l fl + alpha_s (1 - fl), tau_T = 1/2 + alpha_e / (sigma c_sT^2). */
+ * alpha_e = alpha_l fl + alpha_s (1 - fl), tau_T = 1/2 + alpha_e / (sigma c_sT^2),
+ * sigma = sigma(fl) of Eq. (7) when sigma_solid is set. */
 double ora_theta_T(const ora_ctx* c, double fl);
 
 int  ora_create(const ora_params* p, ora_ctx** out);

@@ -270,3 +270,68 @@ def test_porous_gallium_cavity_relaxation_times(oracle_mod):
     assert abs(d["nu_l"] / 0.0208 - 0.0873103) < 1e-7
     assert abs(0.385 * d["lat"] - 3.605691) < 1e-6
     assert abs(w.params["T_s"] - 0.3712) < 1e-12 and abs(w.params["T_l"] - 0.4112) < 1e-12
+
+
+# ---- Eq. (7): heat capacity ratio following the liquid fraction ---------------
+
+def _neumann_front(k_l, D_l, k_s, D_s, latent, T_b=1.0, T_m=0.0, T_i=-1.0):
+    """lambda of the front x_m = 2 lambda sqrt(t) of a two-phase Neumann
+    problem: dT/dt = D d2T/dx2 in each phase, and at the front
+    latent dx_m/dt = -k_l dT_l/dx + k_s dT_s/dx."""
+    f = lambda L: (k_l * (T_b - T_m) * np.exp(-L * L / D_l)
+                   / (np.sqrt(np.pi * D_l) * erf(L / np.sqrt(D_l)))
+                   - k_s * (T_m - T_i) * np.exp(-L * L / D_s)
+                   / (np.sqrt(np.pi * D_s) * erfc(L / np.sqrt(D_s))) - latent * L)
+    return brentq(f, 1e-9, 0.5)
+
+
+def test_theta_follows_heat_capacity(oracle_mod):
+    """tau_T(f_l) = 1/2 + alpha_e(f_l) / (sigma(f_l) c_sT^2) with sigma linear in
+    f_l (Eq. (7)) and alpha_l = sigma_l c_sT^2 (tau_T - 1/2): for the Sec. 4.1 slab
+    with alpha_l / alpha_s = 10 (alpha_s = 0.02, tau_T = 1.5, c_sT^2 = 0.2,
+    sigma_l = 1) and sigma_s = 0.5, worked by hand: f_l = 0: 0.5 + 0.02 / 0.1 =
+    0.7; f_l = 1: 0.5 + 0.2 / 0.2 = 1.5; f_l = 0.5: alpha_e = 0.11, sigma = 0.75,
+    0.5 + 0.11 / 0.15."""
+    w = W.two_phase_slab(10.0)
+    o = oracle_mod.Oracle(w.nx, w.ny, **{**w.params, "sigma_solid": 0.5})
+    for fl, tau in ((0.0, 0.7), (1.0, 1.5), (0.5, 0.5 + 0.11 / 0.15)):
+        assert abs(1.0 / o.theta_T(fl) - tau) < 1e-13, (fl, 1.0 / o.theta_T(fl), tau)
+
+
+@pytest.mark.parametrize("sigma_s", [0.5, 2.0])
+def test_two_phase_melting_with_solid_heat_capacity(oracle_mod, sigma_s):
+    """The Sec. 4.1 slab (alpha_l = alpha_s = 0.02, sigma_l = 1) with a different
+    solid heat capacity: after 20,000 steps the front sits within 2% of the
+    Neumann front of the scheme's continuum problem (D = alpha / sigma per
+    phase, latent = int_0^1 phi / (St sigma(f)) df = ln(sigma_l / sigma_s) /
+    (sigma_l - sigma_s)).  The physical problem (fluxes alpha dT/dx, latent
+    phi / St) puts the front 27% (sigma_s = 0.5) and 41% (sigma_s = 2)
+    elsewhere: with sigma varying in space the scheme carries D dT/dx across
+    the front, not alpha dT/dx."""
+    w = W.two_phase_slab(1.0)
+    o = oracle_mod.Oracle(w.nx, w.ny, **{**w.params, "sigma_solid": sigma_s})
+    o.set_fields(w.phi, w.K, w.T0, w.fl0)
+    t = 20000
+    o.step(t)
+    fl = o.macros()["fl"].mean(axis=0)
+    x_m = 0.5 * fl[0] + fl[1:].sum()
+    D_l, D_s = 0.02, 0.02 / sigma_s
+    latent = np.log(1.0 / sigma_s) / (1.0 - sigma_s)
+    x_an = 2 * _neumann_front(D_l, D_l, D_s, D_s, latent) * np.sqrt(t)
+    assert abs(x_m / x_an - 1) < 0.02, (x_m, x_an)
+    # the physical problem: fluxes alpha dT/dx, latent phi / St = 1
+    x_phys = 2 * _neumann_front(0.02, D_l, 0.02, D_s, 1.0) * np.sqrt(t)
+    assert abs(x_m / x_phys - 1) > 0.15, (x_m, x_phys)
+
+
+def test_sigma_solid_equal_to_sigma_is_constant_sigma(oracle_mod):
+    """sigma_solid = sigma is the constant-sigma model, bit for bit, on a
+    convecting cavity."""
+    w = W.melted_cavity(32)
+    a = oracle_mod.Oracle(w.nx, w.ny, **w.params)
+    b = oracle_mod.Oracle(w.nx, w.ny, **{**w.params, "sigma_solid": w.params.get("sigma", 1.0)})
+    for o in (a, b):
+        o.set_fields(w.phi, w.K, w.T0, w.fl0)
+        o.step(20)
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(x, y)
