@@ -94,3 +94,42 @@ def test_gradients_equal_finite_differences(oracle_mod, objective):
     # the permeability matters where the liquid moves, not in the far solid
     assert np.abs(d_lnK[:, 1:10]).max() > 1e-8
     assert np.abs(d_lnK[:, 14:]).max() == 0.0
+
+
+def test_gradients_on_64x64_cavity(oracle_mod):
+    """The same reference on a 64^2 melting cavity (100 steps, the hot-wall
+    Nusselt number averaged over them): ln K gradients at two cells near the
+    hot wall (about -1.7e-6 and -3.9e-7) and a wall row (about 0.66), against
+    finite differences of the oracle."""
+    from oracle.coupled_ref import CoupledRef
+    w = W.melted_cavity(64)
+    params = dict(w.params)
+    params.update(T_s=0.1, T_l=0.4)
+    tw = 1.0 + 0.1 * np.sin(2 * np.pi * np.arange(w.ny) / w.ny)
+    steps = 100
+
+    def J(K=None, t=None):
+        o = oracle_mod.Oracle(w.nx, w.ny, **params)
+        o.set_fields(w.phi, w.K if K is None else K, w.T0, w.fl0, tw if t is None else t)
+        acc = 0.0
+        for _ in range(steps):
+            o.step(1)
+            acc += o.reduce()["nu_hot"]
+        return acc / steps
+
+    _, _, d_lnK, d_tw = CoupledRef(w.nx, w.ny, params).gradients(
+        steps, w.T0, w.fl0, w.phi, w.K, tw, "nusselt")
+    h = 1e-6
+    for yy, xx in ((3, 4), (10, 5)):
+        Kp, Km = w.K.copy(), w.K.copy()
+        Kp[yy, xx] *= np.exp(h)
+        Km[yy, xx] *= np.exp(-h)
+        fd = (J(K=Kp) - J(K=Km)) / (2 * h)
+        assert abs(fd) > 1e-7
+        assert abs(d_lnK[yy, xx] - fd) <= 2e-3 * abs(fd) + 5e-9, (yy, xx, d_lnK[yy, xx], fd)
+    tp, tm = tw.copy(), tw.copy()
+    tp[20] += h
+    tm[20] -= h
+    fd = (J(t=tp) - J(t=tm)) / (2 * h)
+    assert abs(d_tw[20] - fd) <= 2e-3 * abs(fd) + 5e-9, (d_tw[20], fd)
+    assert (np.abs(d_lnK) > 0).sum() > 500
