@@ -375,7 +375,7 @@ void adj_step(const Dev& d, const AdjBuffers& b, const float* f0, const float* f
   adj_band_kernel<<<1, BAND_THREADS, BAND_SMEM, s>>>(d, b, f1, list, count, old_count,
                                                      mu_sweeps);
   Mat5 At;
-  for (int k = 0; k < 25; ++k) At.m[k] = b.At_host[k];
+  for (int k = 0; k < 25; ++k) At.m[k] = b.At[k];
   const dim3 grid((d.nx + AB - 1) / AB, d.ny < 65535 ? d.ny : 65535);
   adj_full_kernel<<<grid, AB, 0, s>>>(d, b, At, nu, f0, f1, old_list, old_count);
 }

@@ -15,9 +15,8 @@ struct AdjBuffers {
   float* lamgpre;    // 5 n: adjoint of the populations before the step
   float* lama;       // accumulated adjoint of a
   float* lamtw;      // ny: accumulated adjoint of the left wall profile
-  float* At;         // 25: transposed collision matrix (u = 0)
   int* pos;          // n: a band node's place in the band list
-  float At_host[25]; // the same, passed to kernels by value
+  float At[25];      // transposed collision matrix (u = 0), passed to kernels by value
 };
 struct Mat5 {
   float m[25];

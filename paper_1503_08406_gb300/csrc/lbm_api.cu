@@ -1031,7 +1031,6 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
   b.lamgpre = mem.get(5 * n);
   b.lama = mem.get(n);
   b.lamtw = mem.get((size_t)c->d.ny);
-  b.At = mem.get(25);
   b.pos = reinterpret_cast<int*>(mem.get(n));
   int* lists[2] = {reinterpret_cast<int*>(mem.get(n)), reinterpret_cast<int*>(mem.get(n))};
   int* counts = reinterpret_cast<int*>(mem.get(2));
@@ -1039,7 +1038,7 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
   double* nu_acc = reinterpret_cast<double*>(mem.get(2));
   double* dJ = reinterpret_cast<double*>(mem.get(2 * 129));
   if (!flS || (!keep_all && (!cps || !fin)) || !b.a || !b.lamg || !b.lamf || !b.rhs ||
-      !b.mu0 || !b.mu1 || !b.lamgpre || !b.lama || !b.lamtw || !b.At || !b.pos || !lists[0] ||
+      !b.mu0 || !b.mu1 || !b.lamgpre || !b.lama || !b.lamtw || !b.pos || !lists[0] ||
       !lists[1] || !counts || !ctr || !nu_acc || !dJ)
     return LBM_ERR_OOM;
   // transposed collision matrix with u = 0: g+ = A g,
@@ -1049,7 +1048,7 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
                                     {-4, 1, 1, 1, 1}, {0, 1, -1, 1, -1}};
     const double th[5] = {1.0, c->d.z_a, c->d.z_a, c->d.z_e, c->d.z_nu};
     const double eq[5] = {1.0, 0.0, 0.0, p.varpi, 0.0};
-    float At[25];
+    float* At = b.At;
     for (int i = 0; i < 5; ++i)
       for (int j = 0; j < 5; ++j) {
         double a = 0.0;
@@ -1061,8 +1060,6 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
         }
         At[j * 5 + i] = (float)a;
       }
-    LBM_CUDA(cudaMemcpyAsync(b.At, At, sizeof At, cudaMemcpyHostToDevice, c->stream));
-    memcpy(b.At_host, At, sizeof At);
   }
   auto save = [&](float* dst) -> int {
     LBM_TRY(lbm_get_state(c, nullptr, dst, dst + 5 * n, 1));
