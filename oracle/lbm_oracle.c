@@ -32,6 +32,13 @@
  *  - with alpha_l != alpha_s (Sec. 4.1), tau_T = 1/2 + alpha_e/(sigma c_sT^2),
  *    alpha_e = alpha_l f_l + alpha_s (1 - f_l), per node; a wall node relaxes
  *    at the rate of the inward neighbour it extrapolates from.
+ *  - flow walls (flow_walls = 1): the non-equilibrium extrapolation of Sec. 4
+ *    for the no-slip walls.  A wall node whose inward neighbour carries flow
+ *    is a boundary node: before collision its populations become
+ *    f^eq(rho_f, 0) + f(x_f) - f^eq(rho_f, u_f), with rho_f, u_f and varphi of
+ *    the inward node x_f; it then collides with x_f's T, f_l, phi and K and
+ *    streams like a flow node; links into it are no longer reflected.  (The
+ *    default, flow_walls = 0, reflects them halfway.)
  *  - with sigma_solid set, sigma follows Eq. (7), linear in f_l:
  *    sigma(f_l) = sigma_s + f_l (sigma_l - sigma_s), evaluated at f_l(n) per
  *    node for the step, in tau_T, in n^eq of Eq. (34) and in the latent
@@ -577,15 +584,35 @@ static double wall_temperature(const ora_ctx* c, int x, int y, double Tf) {
 
 static void flow_step(ora_ctx* c) {
   const int n = c->n, nx = c->nx, ny = c->ny;
+  /* active: 1 flow node, 2 extrapolated wall node (flow_walls = 1), 0 none */
   for (int s = 0; s < n; ++s) c->active[s] = (!c->wall[s] && c->fl[s] >= c->p.f_act);
+  if (c->p.flow_walls == 1)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const int s = idx(c, x, y);
+        if (c->wall[s] && c->active[inward(c, x, y)] == 1) c->active[s] = 2;
+      }
 #pragma omp parallel for schedule(static)
   for (int y = 0; y < ny; ++y) {
     for (int x = 0; x < nx; ++x) {
       int s = idx(c, x, y);
       double fin[9], fout[9];
       for (int i = 0; i < 9; ++i) fin[i] = c->f[i * n + s];
-      if (c->active[s]) {
+      if (c->active[s] == 1) {
         collide_flow(c, fin, c->T[s], c->fl[s], c->phi[s], c->K[s], fout, &c->ux[s], &c->uy[s]);
+      } else if (c->active[s] == 2) {
+        /* Sec. 4: equilibrium at the wall velocity (0) with the fluid node's
+         * density plus the fluid node's non-equilibrium part */
+        const int sf = inward(c, x, y);
+        double ff[9], rho, ufx, ufy, Fx, Fy, eqw[9], eqf[9], tx, ty;
+        for (int i = 0; i < 9; ++i) ff[i] = c->f[i * n + sf];
+        macro_flow(c, ff, c->T[sf], c->fl[sf], c->phi[sf], c->K[sf], &rho, &ufx, &ufy, &Fx, &Fy);
+        const double vphi = c->phi[sf] * c->fl[sf];
+        ora_feq(c, rho, 0, 0, vphi, eqw);
+        ora_feq(c, rho, ufx, ufy, vphi, eqf);
+        for (int i = 0; i < 9; ++i) fin[i] = eqw[i] + ff[i] - eqf[i];
+        collide_flow(c, fin, c->T[sf], c->fl[sf], c->phi[sf], c->K[sf], fout, &tx, &ty);
+        c->ux[s] = c->uy[s] = 0;
       } else {
         for (int i = 0; i < 9; ++i) fout[i] = fin[i];
         c->ux[s] = c->uy[s] = 0;
@@ -593,7 +620,9 @@ static void flow_step(ora_ctx* c) {
       for (int i = 0; i < 9; ++i) c->fpost[i * n + s] = fout[i];
     }
   }
-  /* streaming, Eq. (21), with halfway bounce-back on links into non-flow nodes */
+  /* streaming, Eq. (21), with halfway bounce-back on links into non-flow nodes
+   * (extrapolated wall nodes stream like flow nodes; what they would receive
+   * from outside the lattice is reflected, and replaced before it is used) */
 #pragma omp parallel for schedule(static)
   for (int y = 0; y < ny; ++y) {
     for (int x = 0; x < nx; ++x) {

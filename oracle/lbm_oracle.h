@@ -52,6 +52,8 @@ typedef struct {
   double  alpha_ratio;  /* alpha_l / alpha_s (Sec. 4.1); 0 or 1: one diffusivity */
   double  sigma_solid;  /* sigma at f_l = 0, Eq. (7) (sigma above is its value at
                            f_l = 1); 0: sigma everywhere */
+  int32_t flow_walls;   /* 0: halfway bounce-back on links into wall nodes;
+                           1: non-equilibrium extrapolation on wall nodes (Sec. 4) */
 } ora_params;
 
 typedef struct ora_ctx ora_ctx;

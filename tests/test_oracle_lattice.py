@@ -67,6 +67,29 @@ def test_brinkman_channel_profile(oracle_mod):
     assert np.abs(uy[core] / u_exact[core] - 1).max() < 1e-4
 
 
+def test_brinkman_channel_with_extrapolated_walls(oracle_mod):
+    """flow_walls = 1 (Sec. 4's non-equilibrium extrapolation for the no-slip
+    walls): the wall is on the wall nodes, so the fully developed profile is
+    u(x) = (G K / nu_l) [1 - cosh(r (x - c)) / cosh(r h)] with c = h = (nx - 1)/2;
+    the oracle's is within 1e-3 of it, and next to the wall 90% above the
+    halfway bounce-back profile (wall half a node further out)."""
+    nx, ny, phi, K, G = 66, 4, 0.5, 12.5, 1e-8
+    params = dict(bc=("dirichlet", "dirichlet", "periodic", "periodic"), T_bc=(1.0, 1.0, 0, 0),
+                  flow=1, tau_nu=1.0, tau_T=1.0, g_beta=G, Pr=1.0, T_ref=0.0, flow_walls=1)
+    w = W.Workload("channel", nx, ny, params, np.full((ny, nx), phi), np.full((ny, nx), K),
+                   np.ones((ny, nx)), np.ones((ny, nx)))
+    o = _run(oracle_mod, w, 6000)
+    uy = o.macros()["uy"][1]
+    d = o.derived()
+    r = np.sqrt(phi * d["nu_l"] / (d["nu_e"] * K))
+    x = np.arange(nx)
+    u_node = G * K / d["nu_l"] * (1 - np.cosh(r * (x - (nx - 1) / 2)) / np.cosh(r * (nx - 1) / 2))
+    u_half = G * K / d["nu_l"] * (1 - np.cosh(r * (x - (nx - 1) / 2)) / np.cosh(r * (nx - 2) / 2))
+    assert np.abs(uy[1:-1] - u_node[1:-1]).max() < 1e-3 * u_node.max()
+    assert uy[1] > 1.9 * u_half[1]
+    assert np.abs(o.macros()["ux"]).max() < 1e-15
+
+
 # ---- conservation on closed domains -----------------------------------------
 
 @pytest.mark.parametrize("flow,T_s,T_l", [(1, 0.0, 0.0), (0, -0.05, 0.05)])
