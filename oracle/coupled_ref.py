@@ -179,6 +179,20 @@ class CoupledRef:
         """Collide and stream; returns f(n+1) and the velocity (0 off flow)."""
         active = (~self.wall) & (fl >= self.f_act)
         fls = torch.where(active, fl, torch.ones_like(fl))    # safe where unused
+        fpost, ux, uy = self.collide_flow(f, T, fls, phi, K)
+        fpost = torch.where(active[None], fpost, f)
+        out = []
+        for i in range(9):
+            from_up = self._shift(fpost[i], EX9[i], EY9[i])
+            up_active = self._shift(active, EX9[i], EY9[i], fill=False)
+            v = torch.where(up_active, from_up, fpost[OPP9[i]])
+            out.append(torch.where(active, v, f[i]))
+        zero = torch.zeros_like(ux)
+        return torch.stack(out), torch.where(active, ux, zero), torch.where(active, uy, zero)
+
+    def collide_flow(self, f, T, fls, phi, K):
+        """The flow collision of every node (f: [9, ...], the rest [...]):
+        post-collision populations and the velocity of Eq. (26)."""
         rho0 = self.rho0
         rho = f.sum(dim=0)
         jx = sum(EX9[i] * f[i] for i in range(9))
@@ -207,19 +221,11 @@ class CoupledRef:
                          rho0 * Fx, -rho0 * Fx, rho0 * Fy, -rho0 * Fy,
                          2 * rho0 * (ux * Fx - uy * Fy) / vphi,
                          rho0 * (ux * Fy + uy * Fx) / vphi])
-        m = torch.einsum("ki,iyx->kyx", M9, f)
-        lam = self.lam[:, None, None]
+        m = torch.einsum("ki,i...->k...", M9, f)
+        lam = self.lam.reshape(9, *([1] * (f.dim() - 1)))
         mp = m - lam * (m - meq) + (1 - 0.5 * lam) * S
-        fpost = torch.einsum("ik,kyx->iyx", self.Minv, mp)
-        fpost = torch.where(active[None], fpost, f)
-        out = []
-        for i in range(9):
-            from_up = self._shift(fpost[i], EX9[i], EY9[i])
-            up_active = self._shift(active, EX9[i], EY9[i], fill=False)
-            v = torch.where(up_active, from_up, fpost[OPP9[i]])
-            out.append(torch.where(active, v, f[i]))
-        zero = torch.zeros_like(ux)
-        return torch.stack(out), torch.where(active, ux, zero), torch.where(active, uy, zero)
+        fpost = torch.einsum("ik,k...->i...", self.Minv, mp)
+        return fpost, ux, uy
 
     # ---- thermal -----------------------------------------------------------
     def _geq(self, T, ux, uy):

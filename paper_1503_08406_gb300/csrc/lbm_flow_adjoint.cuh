@@ -1,0 +1,263 @@
+// Adjoint of the flow collision at one node (Sec. 3.1), written out by hand for
+// the reverse sweep of the coupled step: the vector-Jacobian product of the map
+// (f, T, f_l, phi, K) -> (f+, u) of
+//   rho = sum f, j = sum e f                                   Eq. (24)
+//   varphi = phi f_l, G = g beta (T - T_0)                     Eq. (5)
+//   K_eff = K f_l^3 ((1 - phi) / (1 - varphi))^2,
+//   C_F = 1.75 / sqrt(175 varphi^3)                            Eq. (6), f_l-scaled
+//   v = j / rho0 + varphi G e_y / 2                            Eq. (27)
+//   l0 = (1 + varphi nu / (2 K_eff)) / 2, l1 = varphi C_F / (2 sqrt(K_eff))   Eq. (28)
+//   u = v / (l0 + sqrt(l0^2 + l1 |v|))                        Eq. (26)
+//   F = -varphi nu / K_eff u - varphi C_F / sqrt(K_eff) |u| u + varphi G e_y   Eq. (4)
+//   m+ = m - Lambda (m - m^eq(rho, u, varphi)) + (I - Lambda/2) S(u, F, varphi),
+//   m = M f, f+ = M^-1 m+                                      Eq. (16)-(23)
+// Given the adjoints of f+ and of u (the velocity the thermal collision and
+// the wall extrapolation use), it returns those of f, T, f_l, phi and K.
+// Square roots of speeds carry a floor (FlowNode::eps) so that a node at rest
+// has a finite derivative.  M has orthogonal rows: M^-1 = M^T D^-1 with
+// D = diag(9, 36, 36, 6, 12, 6, 12, 4, 4).
+//
+// Header-only and templated on the real type; LBM_HD marks the functions for
+// both the host (float64 checks) and the device.
+#pragma once
+
+#include <math.h>
+
+#ifndef LBM_HD
+#ifdef __CUDACC__
+#define LBM_HD __host__ __device__ __forceinline__
+#else
+#define LBM_HD inline
+#endif
+#endif
+
+namespace lbm {
+
+template <typename R>
+struct FlowNode {
+  R rho0, nu_l, g_beta, T_ref;
+  R lam[9];   // diagonal of Lambda, Eq. (23)
+  R eps;      // floor under the squared speeds
+};
+
+template <typename R>
+LBM_HD void mrt_M(const R f[9], R m[9]) {
+  const R c = f[5] + f[6] + f[7] + f[8];
+  const R a = f[1] + f[2] + f[3] + f[4];
+  m[0] = f[0] + a + c;
+  m[1] = -4 * f[0] - a + 2 * c;
+  m[2] = 4 * f[0] - 2 * a + c;
+  m[3] = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+  m[4] = -2 * f[1] + 2 * f[3] + f[5] - f[6] - f[7] + f[8];
+  m[5] = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+  m[6] = -2 * f[2] + 2 * f[4] + f[5] + f[6] - f[7] - f[8];
+  m[7] = f[1] - f[2] + f[3] - f[4];
+  m[8] = f[5] - f[6] + f[7] - f[8];
+}
+
+// out = M^T l
+template <typename R>
+LBM_HD void mrt_MT(const R l[9], R o[9]) {
+  const R e = l[0] - l[1] - 2 * l[2], d = l[0] + 2 * l[1] + l[2];
+  o[0] = l[0] - 4 * l[1] + 4 * l[2];
+  o[1] = e + l[3] - 2 * l[4] + l[7];
+  o[2] = e + l[5] - 2 * l[6] - l[7];
+  o[3] = e - l[3] + 2 * l[4] + l[7];
+  o[4] = e - l[5] + 2 * l[6] - l[7];
+  o[5] = d + l[3] + l[4] + l[5] + l[6] + l[8];
+  o[6] = d - l[3] - l[4] + l[5] + l[6] - l[8];
+  o[7] = d - l[3] - l[4] - l[5] - l[6] + l[8];
+  o[8] = d + l[3] + l[4] - l[5] - l[6] - l[8];
+}
+
+template <typename R>
+LBM_HD R mrt_D(int k) {
+  return k == 0 ? R(9) : (k == 1 || k == 2) ? R(36) : (k == 3 || k == 5) ? R(6)
+         : (k == 4 || k == 6) ? R(12) : R(4);
+}
+
+// Forward intermediates of one node, kept for the reverse pass.
+template <typename R>
+struct FlowFwd {
+  R rho, jx, jy, vp, G, q, r, Keff, CF, sK, vx, vy, l0, l1, vm, s2, den, ux, uy, um, a1, a2;
+  R Fx, Fy, uu, uF;
+};
+
+template <typename R>
+LBM_HD void flow_node_forward(const FlowNode<R>& p, const R f[9], R T, R fl, R phi, R K,
+                              FlowFwd<R>& w) {
+  w.rho = 0;
+  w.jx = 0;
+  w.jy = 0;
+  const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  for (int i = 0; i < 9; ++i) {
+    w.rho += f[i];
+    w.jx += ex[i] * f[i];
+    w.jy += ey[i] * f[i];
+  }
+  w.vp = phi * fl;
+  w.G = p.g_beta * (T - p.T_ref);
+  w.q = 1 - w.vp;
+  w.r = (1 - phi) / w.q;
+  w.Keff = K * fl * fl * fl * w.r * w.r;
+  w.CF = R(1.75) / sqrt(R(175) * w.vp * w.vp * w.vp);
+  w.sK = sqrt(w.Keff);
+  w.vx = w.jx / p.rho0;
+  w.vy = w.jy / p.rho0 + R(0.5) * w.vp * w.G;
+  w.l0 = R(0.5) * (1 + w.vp * R(0.5) * p.nu_l / w.Keff);
+  w.l1 = w.vp * R(0.5) * w.CF / w.sK;
+  w.vm = sqrt(w.vx * w.vx + w.vy * w.vy + p.eps);
+  w.s2 = sqrt(w.l0 * w.l0 + w.l1 * w.vm);
+  w.den = w.l0 + w.s2;
+  w.ux = w.vx / w.den;
+  w.uy = w.vy / w.den;
+  w.um = sqrt(w.ux * w.ux + w.uy * w.uy + p.eps);
+  w.a1 = w.vp * p.nu_l / w.Keff;
+  w.a2 = w.vp * w.CF / w.sK;
+  w.Fx = -w.a1 * w.ux - w.a2 * w.um * w.ux;
+  w.Fy = -w.a1 * w.uy - w.a2 * w.um * w.uy + w.vp * w.G;
+  w.uu = w.ux * w.ux + w.uy * w.uy;
+  w.uF = w.ux * w.Fx + w.uy * w.Fy;
+}
+
+// m^eq of Eq. (19) and S of Eq. (22) from the intermediates
+template <typename R>
+LBM_HD void flow_node_meq_S(const FlowNode<R>& p, const FlowFwd<R>& w, R meq[9], R S[9]) {
+  const R r0 = p.rho0, vp = w.vp;
+  meq[0] = w.rho;
+  meq[1] = -2 * w.rho + 3 * r0 * w.uu / vp;
+  meq[2] = w.rho - 3 * r0 * w.uu / vp;
+  meq[3] = r0 * w.ux;
+  meq[4] = -r0 * w.ux;
+  meq[5] = r0 * w.uy;
+  meq[6] = -r0 * w.uy;
+  meq[7] = r0 * (w.ux * w.ux - w.uy * w.uy) / vp;
+  meq[8] = r0 * w.ux * w.uy / vp;
+  S[0] = 0;
+  S[1] = 6 * r0 * w.uF / vp;
+  S[2] = -6 * r0 * w.uF / vp;
+  S[3] = r0 * w.Fx;
+  S[4] = -r0 * w.Fx;
+  S[5] = r0 * w.Fy;
+  S[6] = -r0 * w.Fy;
+  S[7] = 2 * r0 * (w.ux * w.Fx - w.uy * w.Fy) / vp;
+  S[8] = r0 * (w.ux * w.Fy + w.uy * w.Fx) / vp;
+}
+
+// The collision itself (for checks of the forward map): f+ and u.
+template <typename R>
+LBM_HD void flow_node_collide(const FlowNode<R>& p, const R f[9], R T, R fl, R phi, R K,
+                              R fpost[9], R* ux, R* uy) {
+  FlowFwd<R> w;
+  flow_node_forward(p, f, T, fl, phi, K, w);
+  R m[9], meq[9], S[9], mp[9];
+  mrt_M(f, m);
+  flow_node_meq_S(p, w, meq, S);
+  for (int k = 0; k < 9; ++k)
+    mp[k] = (m[k] - p.lam[k] * (m[k] - meq[k]) + (1 - R(0.5) * p.lam[k]) * S[k]) / mrt_D<R>(k);
+  mrt_MT(mp, fpost);
+  *ux = w.ux;
+  *uy = w.uy;
+}
+
+// The reverse of flow_node_collide: lf = adjoint of f+, (lux, luy) = adjoint
+// of u; out: lfin = adjoint of f, and of T, f_l, phi and K.
+template <typename R>
+LBM_HD void flow_node_adjoint(const FlowNode<R>& p, const R f[9], R T, R fl, R phi, R K,
+                              const R lf[9], R lux, R luy, R lfin[9], R* lT, R* lfl, R* lphi,
+                              R* lK) {
+  FlowFwd<R> w;
+  flow_node_forward(p, f, T, fl, phi, K, w);
+  const R r0 = p.rho0, vp = w.vp;
+  // f+ = M^T D^-1 m+  ->  lm+ = D^-1 M lf
+  R lmp[9];
+  mrt_M(lf, lmp);
+  for (int k = 0; k < 9; ++k) lmp[k] /= mrt_D<R>(k);
+  R lm[9], lmeq[9], lS[9];
+  for (int k = 0; k < 9; ++k) {
+    lm[k] = (1 - p.lam[k]) * lmp[k];
+    lmeq[k] = p.lam[k] * lmp[k];
+    lS[k] = (1 - R(0.5) * p.lam[k]) * lmp[k];
+  }
+  mrt_MT(lm, lfin);   // m = M f
+  R lrho = lmeq[0] - 2 * lmeq[1] + lmeq[2];
+  R lvp = 0, lFx = 0, lFy = 0, lG = 0;
+  // m^eq
+  {
+    const R W = 3 * r0 * (lmeq[1] - lmeq[2]);   // adjoint of uu / varphi
+    lux += W * 2 * w.ux / vp + lmeq[7] * 2 * r0 * w.ux / vp + lmeq[8] * r0 * w.uy / vp +
+           r0 * (lmeq[3] - lmeq[4]);
+    luy += W * 2 * w.uy / vp - lmeq[7] * 2 * r0 * w.uy / vp + lmeq[8] * r0 * w.ux / vp +
+           r0 * (lmeq[5] - lmeq[6]);
+    lvp += -(W * w.uu + lmeq[7] * r0 * (w.ux * w.ux - w.uy * w.uy) +
+             lmeq[8] * r0 * w.ux * w.uy) / (vp * vp);
+  }
+  // S
+  {
+    const R P = 6 * r0 * (lS[1] - lS[2]);   // adjoint of uF / varphi
+    const R S7 = 2 * r0 * (w.ux * w.Fx - w.uy * w.Fy) / vp;
+    const R S8 = r0 * (w.ux * w.Fy + w.uy * w.Fx) / vp;
+    lux += (P * w.Fx + lS[7] * 2 * r0 * w.Fx + lS[8] * r0 * w.Fy) / vp;
+    luy += (P * w.Fy - lS[7] * 2 * r0 * w.Fy + lS[8] * r0 * w.Fx) / vp;
+    lFx += r0 * (lS[3] - lS[4]) + (P * w.ux + lS[7] * 2 * r0 * w.ux + lS[8] * r0 * w.uy) / vp;
+    lFy += r0 * (lS[5] - lS[6]) + (P * w.uy - lS[7] * 2 * r0 * w.uy + lS[8] * r0 * w.ux) / vp;
+    lvp += -(P * w.uF / vp + lS[7] * S7 + lS[8] * S8) / vp;
+  }
+  // F
+  R la1, la2, lum;
+  {
+    const R t = lFx * w.ux + lFy * w.uy;
+    la1 = -t;
+    la2 = -w.um * t;
+    lum = -w.a2 * t;
+    lux += lFx * (-w.a1 - w.a2 * w.um);
+    luy += lFy * (-w.a1 - w.a2 * w.um);
+    lvp += lFy * w.G;
+    lG += lFy * vp;
+  }
+  lux += lum * w.ux / w.um;
+  luy += lum * w.uy / w.um;
+  R lKeff = 0, lCF = 0, lsK = 0;
+  lvp += la1 * p.nu_l / w.Keff;
+  lKeff += -la1 * vp * p.nu_l / (w.Keff * w.Keff);
+  lvp += la2 * w.CF / w.sK;
+  lCF += la2 * vp / w.sK;
+  lsK += -la2 * vp * w.CF / (w.sK * w.sK);
+  // u = v / den
+  R lvx = lux / w.den, lvy = luy / w.den;
+  const R lden = -(lux * w.ux + luy * w.uy) / w.den;
+  const R ll0 = lden * (1 + w.l0 / w.s2);
+  const R ll1 = lden * w.vm / (2 * w.s2);
+  const R lvm = lden * w.l1 / (2 * w.s2);
+  lvx += lvm * w.vx / w.vm;
+  lvy += lvm * w.vy / w.vm;
+  // l1, l0
+  lvp += ll1 * R(0.5) * w.CF / w.sK;
+  lCF += ll1 * R(0.5) * vp / w.sK;
+  lsK += -ll1 * R(0.5) * vp * w.CF / (w.sK * w.sK);
+  lvp += ll0 * R(0.25) * p.nu_l / w.Keff;
+  lKeff += -ll0 * R(0.25) * vp * p.nu_l / (w.Keff * w.Keff);
+  // v
+  const R ljx = lvx / r0, ljy = lvy / r0;
+  lvp += lvy * R(0.5) * w.G;
+  lG += lvy * R(0.5) * vp;
+  // sqrt(K_eff), C_F, K_eff
+  lKeff += lsK / (2 * w.sK);
+  lvp += lCF * (R(-1.5) * w.CF / vp);
+  *lK = lKeff * w.Keff / K;
+  R lflv = lKeff * 3 * w.Keff / fl;
+  const R lr = lKeff * 2 * w.Keff / w.r;
+  R lphiv = -lr / w.q;
+  lvp += lr * w.r / w.q;
+  *lT = lG * p.g_beta;
+  lphiv += lvp * fl;
+  lflv += lvp * phi;
+  *lfl = lflv;
+  *lphi = lphiv;
+  const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  for (int i = 0; i < 9; ++i) lfin[i] += lrho + ex[i] * ljx + ey[i] * ljy;
+}
+
+}  // namespace lbm

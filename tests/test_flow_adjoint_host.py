@@ -1,0 +1,100 @@
+"""The flow collision's adjoint written for the reverse-sweep kernels
+(paper_1503_08406_gb300/csrc/lbm_flow_adjoint.cuh), built for the host in
+float64 and checked against the FP64 reference (oracle/coupled_ref.py): its
+forward map equals the reference's collision, and its vector-Jacobian
+product equals torch.autograd's through that collision, on random nodes
+(liquid fractions from near f_act to 1, speeds from rest to the lattice's
+usual range, porosity, permeability and temperature spread)."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import lbm_workloads as W
+
+torch = pytest.importorskip("torch")
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_1503_08406_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    out = str(tmp_path_factory.mktemp("flowadj") / "libflowadj.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-I", CSRC, "-o", out,
+                    os.path.join(HERE, "native", "flow_adjoint_host.cpp")], check=True)
+    return ctypes.CDLL(out)
+
+
+def _P(a):
+    return np.ascontiguousarray(a, dtype=np.float64).ctypes.data_as(ctypes.c_void_p)
+
+
+def _nodes(n, seed):
+    rng = np.random.default_rng(seed)
+    w9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    rho = 1 + 0.01 * rng.standard_normal(n)
+    u = 0.02 * rng.standard_normal((2, n)) * (rng.random(n) > 0.1)   # some at rest
+    ex = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+    ey = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+    eu = ex[:, None] * u[0] + ey[:, None] * u[1]
+    f = w9[:, None] * (rho + 3 * eu + 4.5 * eu ** 2 - 1.5 * (u ** 2).sum(0))
+    f += 1e-4 * rng.standard_normal(f.shape)
+    T = rng.uniform(-0.5, 1.5, n)
+    fl = np.concatenate([[1.0, 1e-3 * 1.01], rng.uniform(0.002, 1.0, n - 2)])
+    phi = rng.uniform(0.3, 0.7, n)
+    K = np.exp(rng.uniform(np.log(0.1), np.log(1e3), n))
+    return f, T, fl, phi, K
+
+
+def _ref():
+    from oracle.coupled_ref import CoupledRef
+    w = W.melted_cavity(24)
+    return CoupledRef(w.nx, w.ny, w.params)
+
+
+def _prm(ref):
+    return np.concatenate([[ref.rho0, ref.nu_l, ref.g_beta, ref.T_ref], ref.lam.numpy(),
+                           [1e-300]])
+
+
+def test_forward_equals_reference_collision(lib):
+    ref = _ref()
+    n = 256
+    f, T, fl, phi, K = _nodes(n, 0)
+    fpost, ux, uy = np.zeros((n, 9)), np.zeros(n), np.zeros(n)
+    lib.flow_collide_f64(_P(_prm(ref)), n, _P(f.T.copy()), _P(T), _P(fl), _P(phi), _P(K),
+                         fpost.ctypes.data_as(ctypes.c_void_p), ux.ctypes.data_as(ctypes.c_void_p),
+                         uy.ctypes.data_as(ctypes.c_void_p))
+    t = lambda a: torch.tensor(a, dtype=torch.float64)
+    fp_r, ux_r, uy_r = ref.collide_flow(t(f), t(T), t(fl), t(phi), t(K))
+    assert np.abs(fpost.T - fp_r.numpy()).max() < 1e-13
+    assert np.abs(ux - ux_r.numpy()).max() < 1e-15 and np.abs(uy - uy_r.numpy()).max() < 1e-15
+
+
+def test_adjoint_equals_autograd(lib):
+    ref = _ref()
+    n = 256
+    f, T, fl, phi, K = _nodes(n, 1)
+    rng = np.random.default_rng(2)
+    lf = rng.standard_normal((n, 9))
+    lux, luy = rng.standard_normal(n), rng.standard_normal(n)
+    outs = {k: np.zeros(s) for k, s in (("lfin", (n, 9)), ("lT", n), ("lfl", n), ("lphi", n),
+                                         ("lK", n))}
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    lib.flow_adjoint_f64(_P(_prm(ref)), n, _P(f.T.copy()), _P(T), _P(fl), _P(phi), _P(K),
+                         _P(lf), _P(lux), _P(luy), vp(outs["lfin"]), vp(outs["lT"]),
+                         vp(outs["lfl"]), vp(outs["lphi"]), vp(outs["lK"]))
+    ins = [torch.tensor(a, dtype=torch.float64, requires_grad=True) for a in (f, T, fl, phi, K)]
+    fp, ux, uy = ref.collide_flow(*ins)
+    J = (torch.tensor(lf.T) * fp).sum() + (torch.tensor(lux) * ux).sum() + \
+        (torch.tensor(luy) * uy).sum()
+    g = torch.autograd.grad(J, ins)
+    exp = {"lfin": g[0].numpy().T, "lT": g[1].numpy(), "lfl": g[2].numpy(),
+           "lphi": g[3].numpy(), "lK": g[4].numpy()}
+    for k in exp:
+        scale = np.abs(exp[k]).max()
+        err = np.abs(outs[k] - exp[k]).max() / scale
+        assert err < 1e-11, (k, err, scale)
