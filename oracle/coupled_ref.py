@@ -269,11 +269,7 @@ class CoupledRef:
         # collision, Eq. (35), source-free part
         uxc = torch.where(self.wall, zero, ux)
         uyc = torch.where(self.wall, zero, uy)
-        nmom = torch.einsum("ki,iyx->kyx", N5, gpre)
-        T = nmom[0]
-        neq = torch.stack([T, uxc * T / self.sigma, uyc * T / self.sigma, self.varpi * T, zero])
-        npost = nmom - self.theta[:, None, None] * (nmom - neq)
-        gpost = torch.einsum("ik,kyx->iyx", self.Ninv, npost)
+        gpost = self.collide_thermal(gpre, uxc, uyc)
         gstar = torch.stack([self._shift(gpost[i], EX5[i], EY5[i]) for i in range(5)])
         # the iterative enthalpy method with the streamed latent source
         base = gstar.sum(dim=0)
@@ -292,6 +288,25 @@ class CoupledRef:
         gnew = torch.stack([gstar[i] + self.w5[i] * self._shift(src, EX5[i], EY5[i])
                             for i in range(5)])
         return gnew, fk
+
+    def collide_thermal(self, g, ux, uy):
+        """The source-free D2Q5 collision of Eq. (35) with n^eq of Eq. (34) of
+        every node (g: [5, ...], u: [...])."""
+        nmom = torch.einsum("ki,i...->k...", N5, g)
+        T = nmom[0]
+        neq = torch.stack([T, ux * T / self.sigma, uy * T / self.sigma, self.varpi * T,
+                           torch.zeros_like(T)])
+        th = self.theta.reshape(5, *([1] * (g.dim() - 1)))
+        npost = nmom - th * (nmom - neq)
+        return torch.einsum("ik,k...->i...", self.Ninv, npost)
+
+    def extrapolate_wall(self, gf, Tw, uxf, uyf):
+        """Populations a wall node takes before collision from its inward
+        node's (gf: [5, ...]), the imposed temperature Tw and the inward node's
+        velocity: g^eq(Tw, 0) + gf - g^eq(T_f, u_f)."""
+        Tf = gf.sum(dim=0)
+        zero = torch.zeros_like(Tf)
+        return self._geq(Tw, zero, zero) + gf - self._geq(Tf, uxf, uyf)
 
     # ---- steps -------------------------------------------------------------
     def step(self, f, g, fl, phi, K, Tw_left):

@@ -260,4 +260,96 @@ LBM_HD void flow_node_adjoint(const FlowNode<R>& p, const R f[9], R T, R fl, R p
   for (int i = 0; i < 9; ++i) lfin[i] += lrho + ex[i] * ljx + ey[i] * ljy;
 }
 
+// ---- the thermal collision and wall extrapolation with the flow's velocity ----
+// D2Q5: N of Eq. (32) has orthogonal rows, N^-1 = N^T D5^-1, D5 = diag(5, 2, 2, 20, 4).
+
+template <typename R>
+struct ThermalNode {
+  R sigma, csT2, varpi;
+  R theta[5];   // diagonal of Theta, Eq. (37)
+  R w0, w1;     // D2Q5 weights of Eq. (39)
+};
+
+template <typename R>
+LBM_HD void d2q5_N(const R g[5], R n[5]) {
+  n[0] = g[0] + g[1] + g[2] + g[3] + g[4];
+  n[1] = g[1] - g[3];
+  n[2] = g[2] - g[4];
+  n[3] = -4 * g[0] + g[1] + g[2] + g[3] + g[4];
+  n[4] = g[1] - g[2] + g[3] - g[4];
+}
+
+// out = N^T l
+template <typename R>
+LBM_HD void d2q5_NT(const R l[5], R o[5]) {
+  o[0] = l[0] - 4 * l[3];
+  o[1] = l[0] + l[1] + l[3] + l[4];
+  o[2] = l[0] + l[2] + l[3] - l[4];
+  o[3] = l[0] - l[1] + l[3] + l[4];
+  o[4] = l[0] - l[2] + l[3] - l[4];
+}
+
+template <typename R>
+LBM_HD R d2q5_D(int k) {
+  return k == 0 ? R(5) : (k == 1 || k == 2) ? R(2) : k == 3 ? R(20) : R(4);
+}
+
+// g+ = N^-1 [n - Theta (n - n^eq)], n = N g, n^eq = (T, u_x T/sigma,
+// u_y T/sigma, varpi T, 0) of Eq. (34), T = n_0
+template <typename R>
+LBM_HD void thermal_node_collide(const ThermalNode<R>& p, const R g[5], R ux, R uy, R gpost[5]) {
+  R n[5], np[5];
+  d2q5_N(g, n);
+  const R T = n[0];
+  const R neq[5] = {T, ux * T / p.sigma, uy * T / p.sigma, p.varpi * T, R(0)};
+  for (int k = 0; k < 5; ++k) np[k] = (n[k] - p.theta[k] * (n[k] - neq[k])) / d2q5_D<R>(k);
+  d2q5_NT(np, gpost);
+}
+
+// its reverse: lg = adjoint of g+; out: adjoint of g (lgin) and of u
+template <typename R>
+LBM_HD void thermal_node_adjoint(const ThermalNode<R>& p, const R g[5], R ux, R uy, const R lg[5],
+                                 R lgin[5], R* lux, R* luy) {
+  R n[5], lnp[5], ln[5];
+  d2q5_N(g, n);
+  const R T = n[0];
+  d2q5_N(lg, lnp);
+  for (int k = 0; k < 5; ++k) lnp[k] /= d2q5_D<R>(k);
+  R lneq[5];
+  for (int k = 0; k < 5; ++k) {
+    ln[k] = (1 - p.theta[k]) * lnp[k];
+    lneq[k] = p.theta[k] * lnp[k];
+  }
+  ln[0] += lneq[0] + (lneq[1] * ux + lneq[2] * uy) / p.sigma + p.varpi * lneq[3];
+  *lux = lneq[1] * T / p.sigma;
+  *luy = lneq[2] * T / p.sigma;
+  d2q5_NT(ln, lgin);
+}
+
+// Wall extrapolation g_b = g^eq(T_w, 0) + g_f - g^eq(T_f, u_f), T_f = sum g_f,
+// g^eq_i(T, u) = w~_i T (1 + e_i . u / (sigma c_sT^2)) of Eq. (39): given the
+// adjoint of g_b, adds that of g_f to lgf and returns those of T_w and u_f
+// (an adiabatic wall, T_w = T_f, adds lTw to every lgf_i itself).
+template <typename R>
+LBM_HD void wall_extrapolation_adjoint(const ThermalNode<R>& p, const R gf[5], R uxf, R uyf,
+                                       const R lgb[5], R lgf[5], R* lTw, R* luxf, R* luyf) {
+  const int ex[5] = {0, 1, 0, -1, 0};
+  const int ey[5] = {0, 0, 1, 0, -1};
+  const R Tf = gf[0] + gf[1] + gf[2] + gf[3] + gf[4];
+  const R c = p.sigma * p.csT2;
+  R lTf = 0, lw = 0, lx = 0, ly = 0;
+  for (int j = 0; j < 5; ++j) {
+    const R wj = j == 0 ? p.w0 : p.w1;
+    const R t = lgb[j] * wj;
+    lw += t;
+    lTf -= t * (1 + (ex[j] * uxf + ey[j] * uyf) / c);
+    lx -= t * Tf * ex[j] / c;
+    ly -= t * Tf * ey[j] / c;
+  }
+  for (int i = 0; i < 5; ++i) lgf[i] += lgb[i] + lTf;
+  *lTw = lw;
+  *luxf = lx;
+  *luyf = ly;
+}
+
 }  // namespace lbm

@@ -98,3 +98,54 @@ def test_adjoint_equals_autograd(lib):
         scale = np.abs(exp[k]).max()
         err = np.abs(outs[k] - exp[k]).max() / scale
         assert err < 1e-11, (k, err, scale)
+
+
+def _tprm(ref):
+    return np.concatenate([[ref.sigma, ref.csT2, ref.varpi], ref.theta.numpy(),
+                           [ref.w5[0].item(), ref.w5[1].item()]])
+
+
+def _thermal_nodes(n, seed):
+    rng = np.random.default_rng(seed)
+    g = np.array([0.6] + [0.1] * 4)[:, None] * rng.uniform(-0.5, 1.5, n) \
+        + 0.01 * rng.standard_normal((5, n))
+    ux, uy = 0.03 * rng.standard_normal(n), 0.03 * rng.standard_normal(n)
+    return g, ux, uy
+
+
+def test_thermal_collision_and_its_adjoint(lib):
+    ref = _ref()
+    n = 256
+    g, ux, uy = _thermal_nodes(n, 3)
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    gpost = np.zeros((n, 5))
+    lib.thermal_collide_f64(_P(_tprm(ref)), n, _P(g.T.copy()), _P(ux), _P(uy), vp(gpost))
+    ins = [torch.tensor(a, dtype=torch.float64, requires_grad=True) for a in (g, ux, uy)]
+    gp = ref.collide_thermal(*ins)
+    assert np.abs(gpost.T - gp.detach().numpy()).max() < 1e-14
+    lg = np.random.default_rng(4).standard_normal((n, 5))
+    lgin, lux, luy = np.zeros((n, 5)), np.zeros(n), np.zeros(n)
+    lib.thermal_adjoint_f64(_P(_tprm(ref)), n, _P(g.T.copy()), _P(ux), _P(uy), _P(lg), vp(lgin),
+                            vp(lux), vp(luy))
+    d = torch.autograd.grad((torch.tensor(lg.T) * gp).sum(), ins)
+    for got, exp in ((lgin.T, d[0]), (lux, d[1]), (luy, d[2])):
+        exp = exp.numpy()
+        assert np.abs(got - exp).max() < 1e-12 * np.abs(exp).max()
+
+
+def test_wall_extrapolation_adjoint(lib):
+    ref = _ref()
+    n = 128
+    g, ux, uy = _thermal_nodes(n, 5)
+    Tw = np.random.default_rng(6).uniform(0, 1, n)
+    lgb = np.random.default_rng(7).standard_normal((n, 5))
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    lgf, lTw, lux, luy = np.zeros((n, 5)), np.zeros(n), np.zeros(n), np.zeros(n)
+    lib.wall_adjoint_f64(_P(_tprm(ref)), n, _P(g.T.copy()), _P(ux), _P(uy), _P(lgb), vp(lgf),
+                         vp(lTw), vp(lux), vp(luy))
+    ins = [torch.tensor(a, dtype=torch.float64, requires_grad=True) for a in (g, Tw, ux, uy)]
+    gb = ref.extrapolate_wall(ins[0], ins[1], ins[2], ins[3])
+    d = torch.autograd.grad((torch.tensor(lgb.T) * gb).sum(), ins)
+    for got, exp in ((lgf.T, d[0]), (lTw, d[1]), (lux, d[2]), (luy, d[3])):
+        exp = exp.numpy()
+        assert np.abs(got - exp).max() < 1e-12 * np.abs(exp).max()
