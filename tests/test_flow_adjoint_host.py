@@ -149,3 +149,80 @@ def test_wall_extrapolation_adjoint(lib):
     for got, exp in ((lgf.T, d[0]), (lTw, d[1]), (lux, d[2]), (luy, d[3])):
         exp = exp.numpy()
         assert np.abs(got - exp).max() < 1e-12 * np.abs(exp).max()
+
+
+@pytest.fixture(scope="module")
+def rev(tmp_path_factory):
+    out = str(tmp_path_factory.mktemp("coupledrev") / "libcoupledrev.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-I", CSRC, "-o", out,
+                    os.path.join(HERE, "native", "coupled_reverse_host.cpp")], check=True)
+    return ctypes.CDLL(out)
+
+
+@pytest.mark.parametrize("objective", ["melt", "nusselt"])
+def test_reverse_sweep_from_node_functions_equals_autograd(rev, objective):
+    """The reverse sweep of the coupled step assembled from the node functions
+    (tests/native/coupled_reverse_host.cpp: streaming reversed with
+    bounce-back, the flow collision's adjoint, the thermal collision's with the
+    velocity, the wall extrapolation's, the enthalpy fixed point's on the
+    band) over 40 steps of a 24^2 melting cavity equals autograd of the FP64
+    reference for the gradients in ln K, phi and the wall profile."""
+    from oracle.coupled_ref import CoupledRef
+    w = W.melted_cavity(24)
+    params = dict(w.params)
+    params.update(T_s=0.1, T_l=0.4)
+    tw = 1.0 + 0.1 * np.sin(2 * np.pi * np.arange(w.ny) / w.ny)
+    steps = 40
+    ref = CoupledRef(w.nx, w.ny, params)
+    J, d_phi, d_lnK, d_tw = ref.gradients(steps, w.T0, w.fl0, w.phi, w.K, tw, objective)
+    # forward states
+    t = lambda a: torch.tensor(a, dtype=torch.float64)
+    f, g, fl = ref.initial(w.T0, w.fl0)
+    states = []
+    for _ in range(steps):
+        states.append((f.numpy().copy(), g.numpy().copy(), fl.numpy().copy()))
+        f, g, fl = ref.step(f, g, fl, t(w.phi), t(w.K), t(tw))
+    states.append((f.numpy().copy(), g.numpy().copy(), fl.numpy().copy()))
+    n = w.nx * w.ny
+    wall = ref.wall.numpy()
+    lf, lg, lfl = np.zeros(9 * n), np.zeros(5 * n), np.zeros(n)
+    lphi, lK, lTw = np.zeros(n), np.zeros(n), np.zeros(w.ny)
+    H, dT = ref.H, ref.dT
+    nu_src = None
+    if objective == "melt":
+        lfl[:] = np.where(wall.ravel(), 0.0, 1.0 / (~wall).sum())
+    else:
+        # d Nu / d T at x = 1, 2 (all rows of a walled cavity but the first and
+        # last) and d Nu / d T_w, per state, divided by the number of steps
+        rows = np.arange(1, w.ny - 1)
+        k = H / (dT * len(rows) * steps)
+        nu_src = np.zeros((w.ny, w.nx))
+        nu_src[rows, 1] = -2 * k
+        nu_src[rows, 2] = 0.5 * k
+        lg += np.tile(nu_src.ravel(), 5)
+    bc = (ctypes.c_int * 4)(*[{"periodic": 0, "dirichlet": 1, "adiabatic": 2}[b] if isinstance(b, str)
+                              else int(b) for b in params["bc"]])
+    fprm = np.concatenate([[ref.rho0, ref.nu_l, ref.g_beta, ref.T_ref], ref.lam.numpy(), [1e-300]])
+    tprm = np.concatenate([[ref.sigma, ref.csT2, ref.varpi], ref.theta.numpy(),
+                           [ref.w5[0].item(), ref.w5[1].item()]])
+    sc = np.array([ref.f_act, ref.T_s, ref.T_l, ref.lat])
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    phi, K = np.ascontiguousarray(w.phi.ravel()), np.ascontiguousarray(w.K.ravel())
+    for m in range(steps - 1, -1, -1):
+        f0, g0, fl0 = states[m]
+        fl1 = states[m + 1][2]
+        rev.coupled_reverse_step_f64(w.nx, w.ny, 0, 0, bc, _P(fprm), _P(tprm), _P(sc),
+                                     _P(f0.ravel()), _P(g0.ravel()), _P(fl0.ravel()),
+                                     _P(fl1.ravel()), _P(phi), _P(K), vp(lf), vp(lg), vp(lfl),
+                                     vp(lphi), vp(lK), vp(lTw))
+        if nu_src is not None and m > 0:   # the Nusselt number of the state before
+            lg += np.tile(nu_src.ravel(), 5)
+    if nu_src is not None:   # its direct term in T_w, once per state
+        lTw[1:-1] += 1.5 * H / (dT * (w.ny - 2) * steps) * steps
+    got = {"phi": lphi.reshape(w.ny, w.nx), "lnK": (lK * K).reshape(w.ny, w.nx), "tw": lTw}
+    exp = {"phi": d_phi, "lnK": d_lnK, "tw": d_tw}
+    for k in exp:
+        scale = np.abs(exp[k]).max()
+        assert scale > 0, k
+        err = np.abs(got[k] - exp[k]).max() / scale
+        assert err < 1e-9, (k, err, scale)
