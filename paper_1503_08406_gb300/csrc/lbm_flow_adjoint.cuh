@@ -352,4 +352,180 @@ LBM_HD void wall_extrapolation_adjoint(const ThermalNode<R>& p, const R gf[5], R
   *luyf = ly;
 }
 
+// ---- one reversed coupled step at one node (gather form) ---------------------
+
+LBM_HD int hd_fetch_add(int* p, int v) {
+#ifdef __CUDA_ARCH__
+  return atomicAdd(p, v);
+#else
+  const int o = *p;
+  *p += v;
+  return o;
+#endif
+}
+
+// Lattice geometry of the oracle: an axis is periodic or walled on both sides;
+// bc = left, right, bottom, top: 0 periodic, 1 Dirichlet, 2 adiabatic.
+struct CoupledGeo {
+  int nx, ny, per_x, per_y;
+  int bc[4];
+  LBM_HD int nb(int x, int y, int dx, int dy) const {
+    int xx = x + dx, yy = y + dy;
+    if (xx < 0 || xx >= nx) {
+      if (!per_x) return -1;
+      xx = (xx + nx) % nx;
+    }
+    if (yy < 0 || yy >= ny) {
+      if (!per_y) return -1;
+      yy = (yy + ny) % ny;
+    }
+    return yy * nx + xx;
+  }
+  LBM_HD bool vx(int x) const { return !per_x && (x == 0 || x == nx - 1); }
+  LBM_HD bool vy(int y) const { return !per_y && (y == 0 || y == ny - 1); }
+  LBM_HD bool wall(int x, int y) const { return vx(x) || vy(y); }
+  // inward neighbour of a wall node (the diagonal one at corners)
+  LBM_HD int inward(int x, int y) const {
+    const int xx = vx(x) ? (x == 0 ? 1 : nx - 2) : x;
+    const int yy = vy(y) ? (y == 0 ? 1 : ny - 2) : y;
+    return yy * nx + xx;
+  }
+  // 0 left, 1 right, 2 bottom, 3 top (corners go to the vertical wall)
+  LBM_HD int side(int x, int y) const { return vx(x) ? (x == 0 ? 0 : 1) : (y == 0 ? 2 : 3); }
+};
+
+// Everything one reversed step reads and writes (natural layout, planes of n).
+template <typename R>
+struct CoupledStep {
+  CoupledGeo geo;
+  long long n;
+  FlowNode<R> fp;
+  ThermalNode<R> tp;
+  R f_act, T_s, T_l, lat;
+  // the objective's direct terms in the state before the step: all five
+  // populations at x = 1 and x = 2 and the left wall value, rows [ny0, ny1)
+  R nu_g1, nu_g2, nu_tw;
+  int ny0, ny1;
+  const R *f0, *g0, *fl0, *fl1, *phi, *K;   // the step's state: before it, and f_l after
+  const R* lf1;                              // adjoint of f after the step
+  const R* lg1;                              // adjoint of g after it, nu added on the band
+  R *lf0, *lg0;                              // adjoints before the step
+  R* lfl;                                    // adjoint of f_l: after the step in, before it out
+  R *lphi, *lK, *lTw;                        // accumulated
+  int *next_list, *next_count;               // band of the state before the step
+};
+
+template <typename R>
+LBM_HD bool coupled_active(const CoupledStep<R>& A, int s) {
+  const int y = s / A.geo.nx, x = s - y * A.geo.nx;
+  return !A.geo.wall(x, y) && A.fl0[s] >= A.f_act;
+}
+
+// lam_g+ of node (x, y) streamed back from lg1 (0 from outside the lattice)
+template <typename R>
+LBM_HD void coupled_lp(const CoupledStep<R>& A, int x, int y, R lp[5]) {
+  const int ex[5] = {0, 1, 0, -1, 0};
+  const int ey[5] = {0, 0, 1, 0, -1};
+  for (int i = 0; i < 5; ++i) {
+    const int t = A.geo.nb(x, y, ex[i], ey[i]);
+    lp[i] = t >= 0 ? A.lg1[i * A.n + t] : R(0);
+  }
+}
+
+template <typename R>
+LBM_HD void coupled_reverse_node(const CoupledStep<R>& A, int x, int y) {
+  const CoupledGeo& G = A.geo;
+  const long long n = A.n;
+  const int s = y * G.nx + x;
+  const bool wall = G.wall(x, y);
+  const bool act = coupled_active(A, s);
+  R g[5], T = 0;
+  for (int i = 0; i < 5; ++i) T += (g[i] = A.g0[i * n + s]);
+  R f[9], ux = 0, uy = 0;
+  for (int i = 0; i < 9; ++i) f[i] = A.f0[i * n + s];
+  if (act) {
+    FlowFwd<R> w;
+    flow_node_forward(A.fp, f, T, A.fl0[s], A.phi[s], A.K[s], w);
+    ux = w.ux;
+    uy = w.uy;
+  }
+  // thermal: this node's collision (u = 0 on walls and off flow)
+  R lp[5], lgin[5], lux = 0, luy = 0, S = 0;
+  coupled_lp(A, x, y, lp);
+  for (int i = 0; i < 5; ++i) S += (i == 0 ? A.tp.w0 : A.tp.w1) * lp[i];
+  {
+    R lx, ly;
+    thermal_node_adjoint(A.tp, g, wall ? R(0) : ux, wall ? R(0) : uy, lp, lgin, &lx, &ly);
+    if (act) {
+      lux += lx;
+      luy += ly;
+    }
+  }
+  R lg[5];
+  R lfl;
+  const R a = A.phi[s] * A.lat;
+  if (wall) {
+    for (int i = 0; i < 5; ++i) lg[i] = 0;   // the extrapolation rewrites them
+    lfl = A.lfl[s];                          // a wall node keeps f_l(n)
+  } else {
+    const bool r = y >= A.ny0 && y < A.ny1;
+    const R src = r && x == 1 ? A.nu_g1 : r && x == 2 ? A.nu_g2 : R(0);
+    for (int i = 0; i < 5; ++i) lg[i] = lgin[i] + src;
+    lfl = a * S;
+    const R df = A.fl1[s] - A.fl0[s];
+    if (df != 0) A.lphi[s] += -df * S * A.lat;
+    // the extrapolation of every wall node whose inward node this is
+    const int ex9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int ey9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    for (int d = 1; d < 9; ++d) {
+      const int bx = x + ex9[d], by = y + ey9[d];
+      if (bx < 0 || bx >= G.nx || by < 0 || by >= G.ny) continue;
+      if (!G.wall(bx, by) || G.inward(bx, by) != s) continue;
+      R lpb[5], lgb[5], lx, ly, lTwv, lxf, lyf;
+      coupled_lp(A, bx, by, lpb);
+      thermal_node_adjoint(A.tp, g, R(0), R(0), lpb, lgb, &lx, &ly);
+      R lgf[5] = {0, 0, 0, 0, 0};
+      wall_extrapolation_adjoint(A.tp, g, ux, uy, lgb, lgf, &lTwv, &lxf, &lyf);
+      const int sd = G.side(bx, by);
+      bool fixed = G.bc[sd] == 1;   // Dirichlet: the imposed value
+      if (!fixed && G.vx(bx) && G.vy(by) && G.bc[by == 0 ? 2 : 3] == 1) fixed = true;
+      if (G.bc[sd] == 1 && sd == 0) {
+        A.lTw[by] += lTwv;
+        if (by >= A.ny0 && by < A.ny1) A.lTw[by] += A.nu_tw;
+      } else if (!fixed) {
+        for (int i = 0; i < 5; ++i) lgf[i] += lTwv;   // adiabatic: T_w = T_f
+      }
+      for (int i = 0; i < 5; ++i) lg[i] += lgf[i];
+      if (act) {
+        lux += lxf;
+        luy += lyf;
+      }
+    }
+  }
+  // flow: streaming reversed (bounce-back links in place), then the collision
+  const int ex9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  const int ey9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  const int op9[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+  if (act) {
+    R lpost[9], lfin[9], lT, lflv, lphiv, lKv;
+    for (int j = 0; j < 9; ++j) {
+      const int t = G.nb(x, y, ex9[j], ey9[j]);
+      lpost[j] = (t >= 0 && coupled_active(A, t)) ? A.lf1[j * n + t] : A.lf1[op9[j] * n + s];
+    }
+    flow_node_adjoint(A.fp, f, T, A.fl0[s], A.phi[s], A.K[s], lpost, lux, luy, lfin, &lT, &lflv,
+                      &lphiv, &lKv);
+    for (int i = 0; i < 9; ++i) A.lf0[i * n + s] = lfin[i];
+    for (int i = 0; i < 5; ++i) lg[i] += lT;   // T(n) = sum g(n)
+    lfl += lflv;
+    A.lphi[s] += lphiv;
+    A.lK[s] += lKv;
+  } else {
+    for (int i = 0; i < 9; ++i) A.lf0[i * n + s] = A.lf1[i * n + s];
+  }
+  for (int i = 0; i < 5; ++i) A.lg0[i * n + s] = lg[i];
+  A.lfl[s] = lfl;
+  const R fa = A.fl0[s];
+  if (!wall && fa > 0 && fa < 1) A.next_list[hd_fetch_add(A.next_count, 1)] = s;
+}
+
 }  // namespace lbm

@@ -161,12 +161,12 @@ def rev(tmp_path_factory):
 
 @pytest.mark.parametrize("objective", ["melt", "nusselt"])
 def test_reverse_sweep_from_node_functions_equals_autograd(rev, objective):
-    """The reverse sweep of the coupled step assembled from the node functions
-    (tests/native/coupled_reverse_host.cpp: streaming reversed with
-    bounce-back, the flow collision's adjoint, the thermal collision's with the
-    velocity, the wall extrapolation's, the enthalpy fixed point's on the
-    band) over 40 steps of a 24^2 melting cavity equals autograd of the FP64
-    reference for the gradients in ln K, phi and the wall profile."""
+    """The reverse sweep of the coupled step from lbm::coupled_reverse_node, the
+    reverse-sweep kernel's body (run over every node on the host, after a
+    Jacobi solve of the fixed point's adjoint on the band, by
+    tests/native/coupled_reverse_host.cpp), over 40 steps of a 24^2 melting
+    cavity: the gradients in ln K, phi and the wall profile equal autograd of
+    the FP64 reference."""
     from oracle.coupled_ref import CoupledRef
     w = W.melted_cavity(24)
     params = dict(w.params)
@@ -188,18 +188,21 @@ def test_reverse_sweep_from_node_functions_equals_autograd(rev, objective):
     lf, lg, lfl = np.zeros(9 * n), np.zeros(5 * n), np.zeros(n)
     lphi, lK, lTw = np.zeros(n), np.zeros(n), np.zeros(w.ny)
     H, dT = ref.H, ref.dT
-    nu_src = None
+    nuprm = np.zeros(5)
     if objective == "melt":
         lfl[:] = np.where(wall.ravel(), 0.0, 1.0 / (~wall).sum())
     else:
-        # d Nu / d T at x = 1, 2 (all rows of a walled cavity but the first and
-        # last) and d Nu / d T_w, per state, divided by the number of steps
-        rows = np.arange(1, w.ny - 1)
-        k = H / (dT * len(rows) * steps)
-        nu_src = np.zeros((w.ny, w.nx))
-        nu_src[rows, 1] = -2 * k
-        nu_src[rows, 2] = 0.5 * k
-        lg += np.tile(nu_src.ravel(), 5)
+        # Nu = -(-3 T_w + 4 T_1 - T_2)/2 H/dT over the rows 1..ny-2 (walls below
+        # and above), after each step, averaged: its terms per state; those of
+        # the last state seed the sweep, each reversed step adds those of the
+        # state before it (the wall term for the states 0..N-1: the same constant
+        # N times)
+        k = H / (dT * (w.ny - 2) * steps)
+        nuprm[:] = (-2 * k, 0.5 * k, 1.5 * k, 1, w.ny - 1)
+        src = np.zeros((w.ny, w.nx))
+        src[1:-1, 1] = -2 * k
+        src[1:-1, 2] = 0.5 * k
+        lg += np.tile(src.ravel(), 5)
     bc = (ctypes.c_int * 4)(*[{"periodic": 0, "dirichlet": 1, "adiabatic": 2}[b] if isinstance(b, str)
                               else int(b) for b in params["bc"]])
     fprm = np.concatenate([[ref.rho0, ref.nu_l, ref.g_beta, ref.T_ref], ref.lam.numpy(), [1e-300]])
@@ -211,14 +214,10 @@ def test_reverse_sweep_from_node_functions_equals_autograd(rev, objective):
     for m in range(steps - 1, -1, -1):
         f0, g0, fl0 = states[m]
         fl1 = states[m + 1][2]
-        rev.coupled_reverse_step_f64(w.nx, w.ny, 0, 0, bc, _P(fprm), _P(tprm), _P(sc),
+        rev.coupled_reverse_step_f64(w.nx, w.ny, 0, 0, bc, _P(fprm), _P(tprm), _P(sc), _P(nuprm),
                                      _P(f0.ravel()), _P(g0.ravel()), _P(fl0.ravel()),
                                      _P(fl1.ravel()), _P(phi), _P(K), vp(lf), vp(lg), vp(lfl),
                                      vp(lphi), vp(lK), vp(lTw))
-        if nu_src is not None and m > 0:   # the Nusselt number of the state before
-            lg += np.tile(nu_src.ravel(), 5)
-    if nu_src is not None:   # its direct term in T_w, once per state
-        lTw[1:-1] += 1.5 * H / (dT * (w.ny - 2) * steps) * steps
     got = {"phi": lphi.reshape(w.ny, w.nx), "lnK": (lK * K).reshape(w.ny, w.nx), "tw": lTw}
     exp = {"phi": d_phi, "lnK": d_lnK, "tw": d_tw}
     for k in exp:
