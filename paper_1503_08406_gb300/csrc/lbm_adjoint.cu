@@ -25,17 +25,23 @@
 // At the fixed point z = f on those nodes, which removes the direct term of
 // d z / d a.
 #include "lbm_adjoint.cuh"
+#include "lbm_flow_adjoint.cuh"
 
 namespace lbm {
 
 constexpr int AB = 256;   // block size of the adjoint kernels
 
+// neighbour (x + dx, y + dy): wraps on periodic axes, -1 beyond a wall side
 __device__ __forceinline__ int adj_nb(const Dev& d, int x, int y, int dx, int dy) {
-  const int xx = x + dx;
-  if (xx < 0 || xx >= d.nx) return -1;
-  int yy = y + dy;
-  if (yy < 0) yy += d.ny;
-  if (yy >= d.ny) yy -= d.ny;
+  int xx = x + dx, yy = y + dy;
+  if (xx < 0 || xx >= d.nx) {
+    if (!d.per_x) return -1;
+    xx = xx < 0 ? xx + d.nx : xx - d.nx;
+  }
+  if (yy < 0 || yy >= d.ny) {
+    if (!d.per_y) return -1;
+    yy = yy < 0 ? yy + d.ny : yy - d.ny;
+  }
   return yy * d.nx + xx;
 }
 
@@ -63,9 +69,9 @@ __device__ __forceinline__ float wt(const Dev& d, int i) { return i == 0 ? d.wt0
 
 __device__ __forceinline__ bool band_node(const Dev& d, const float* f, int t) {
   if (t < 0) return false;
-  const int x = t % d.nx;
+  const int y = t / d.nx, x = t - y * d.nx;
   const float v = f[t];
-  return x != 0 && x != d.nx - 1 && v > 0.f && v < 1.f;
+  return !is_wall(d, x, y) && v > 0.f && v < 1.f;
 }
 
 // the band of the state with liquid fraction f, appended at list[*count]
@@ -352,6 +358,22 @@ void adj_objective(const Dev& d, const float* fl, double* out, cudaStream_t s) {
   const int nb = d.ny < OBLOCKS ? d.ny : OBLOCKS;
   adj_partial_kernel<<<nb, OB, 0, s>>>(d, fl, out + 1);
   adj_objective_kernel<<<1, 32, 0, s>>>(d, out + 1, nb, out);
+}
+
+// One reversed coupled step (flow on): lbm::coupled_reverse_node per node,
+// rows along blockIdx.y.
+__global__ void __launch_bounds__(128) adj_coupled_kernel(CoupledStep<float> A) {
+  const int x = blockIdx.x * 128 + threadIdx.x;
+  if (x >= A.geo.nx) return;
+  for (int y = blockIdx.y; y < A.geo.ny; y += gridDim.y) coupled_reverse_node(A, x, y);
+}
+
+void adj_coupled_step(const Dev& d, const AdjBuffers& b, const CoupledStep<float>& A, int* list,
+                      int* count, int* old_count, int mu_sweeps, cudaStream_t s) {
+  adj_band_kernel<<<1, BAND_THREADS, BAND_SMEM, s>>>(d, b, A.fl1, list, count, old_count,
+                                                     mu_sweeps);
+  const dim3 grid((d.nx + 127) / 128, d.ny < 65535 ? d.ny : 65535);
+  adj_coupled_kernel<<<grid, 128, 0, s>>>(A);
 }
 
 bool adj_init() {

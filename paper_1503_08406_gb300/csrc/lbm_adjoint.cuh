@@ -1,5 +1,6 @@
 // Host entry points of the adjoint of the conduction step (lbm_adjoint.cu).
 #pragma once
+#include "lbm_flow_adjoint.cuh"
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -54,6 +55,12 @@ void adj_save(const Dev& d, float* base, unsigned* ctr, cudaStream_t s);
 void adj_step(const Dev& d, const AdjBuffers& b, const float* f0, const float* f1, int* list,
               int* count, int* old_list, int* old_count, int mu_sweeps, NuSrc nu,
               cudaStream_t s);
+// One reversed step of the coupled adjoint (flow on): the band kernel on
+// b.lamg / b.lamf (A.lg1 is b.lamg, A.lfl is b.lamf, A.fl1 the band's f_l),
+// then lbm::coupled_reverse_node over every node; the band before the step is
+// listed at A.next_list (its count at old_count, emptied first).
+void adj_coupled_step(const Dev& d, const AdjBuffers& b, const CoupledStep<float>& A, int* list,
+                      int* count, int* old_count, int mu_sweeps, cudaStream_t s);
 // once per process before adj_step: the band kernel's shared-memory opt-in
 bool adj_init();
 

@@ -1200,3 +1200,187 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
   if (!melt) *J /= (double)nsteps;
   return LBM_OK;
 }
+
+int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t mu_sweeps,
+                        float* d_phi, float* d_lnK, float* d_wall_T_left, double* J,
+                        int device_ptrs) {
+  if (!c || nsteps < 1 || mu_sweeps < 0 || !d_phi || !d_lnK || !d_wall_T_left || !J)
+    return LBM_ERR_INVALID_ARG;
+  if (objective != LBM_OBJ_MELT && objective != LBM_OBJ_NUSSELT) return LBM_ERR_INVALID_ARG;
+  const lbm_params& p = c->p;
+  const lbm::Dev& d = c->d;
+  if (!p.flow || c->timing || p.storage != LBM_STORAGE_FP32 || d.alpha_var)
+    return LBM_ERR_INVALID_ARG;
+  if (d.per_x || p.bc[0] != LBM_BC_DIRICHLET || d.nx < 5) return LBM_ERR_INVALID_ARG;
+  const bool melt = objective == LBM_OBJ_MELT;
+  const int sweeps = mu_sweeps > 0 ? mu_sweeps : 64;
+  const size_t n = (size_t)d.n, st = 15 * n;   // a kept state: f (9), g (5), f_l
+  if (!lbm::adj_init()) return LBM_ERR_CUDA;
+  size_t free_b = 0, total_b = 0;
+  LBM_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  if ((double)(nsteps + 1) * st * sizeof(float) > 0.5 * (double)free_b) return LBM_ERR_OOM;
+  DevMem mem;
+  float* S = mem.get((size_t)(nsteps + 1) * st);
+  float* lf[2] = {mem.get(9 * n), mem.get(9 * n)};
+  float* lg[2] = {mem.get(5 * n), mem.get(5 * n)};
+  lbm::AdjBuffers b;
+  b.a = mem.get(n);
+  b.lamf = mem.get(n);
+  b.rhs = mem.get(n);
+  b.mu0 = mem.get(n);
+  b.mu1 = mem.get(n);
+  b.lama = mem.get(n);   // adjoint of phi
+  b.lamtw = mem.get((size_t)d.ny);
+  b.pos = reinterpret_cast<int*>(mem.get(n));
+  float* lK = mem.get(n);
+  int* lists[2] = {reinterpret_cast<int*>(mem.get(n)), reinterpret_cast<int*>(mem.get(n))};
+  int* counts = reinterpret_cast<int*>(mem.get(2));
+  double* nu_acc = reinterpret_cast<double*>(mem.get(2));
+  if (!S || !lf[0] || !lf[1] || !lg[0] || !lg[1] || !b.a || !b.lamf || !b.rhs || !b.mu0 ||
+      !b.mu1 || !b.lama || !b.lamtw || !b.pos || !lK || !lists[0] || !lists[1] || !counts ||
+      !nu_acc)
+    return LBM_ERR_OOM;
+  // rows of the Nusselt number (lbm_reduce's): all but horizontal wall rows
+  const int y0 = d.wall_b ? 1 : 0, y1 = d.wall_t ? d.ny - 1 : d.ny;
+  const double kN = melt ? 0.0 : (double)d.H_over_dT / ((double)(y1 - y0) * (double)nsteps);
+  // forward, every state kept (natural layout, f as deviations)
+  auto keep = [&](int64_t k) -> int {
+    float* dst = S + (size_t)k * st;
+    LBM_TRY(lbm_get_state(c, dst, dst + 9 * n, dst + 14 * n, 1));
+    return LBM_OK;
+  };
+  LBM_CUDA(cudaMemsetAsync(nu_acc, 0, sizeof(double), c->stream));
+  for (int64_t k = 0; k < nsteps; ++k) {
+    LBM_TRY(keep(k));
+    LBM_TRY(step_direct(c));
+    if (!melt) lbm::launch_wall_nusselt(c->d, c->parity, nu_acc, c->stream);
+  }
+  LBM_TRY(keep(nsteps));
+  LBM_CUDA(cudaGetLastError());
+  // objective and seeds (host side: small arrays)
+  std::vector<float> hfl(n), seedf(n, 0.f), seedg(5 * n, 0.f);
+  LBM_CUDA(cudaMemcpyAsync(hfl.data(), S + (size_t)nsteps * st + 14 * n, n * sizeof(float),
+                           cudaMemcpyDeviceToHost, c->stream));
+  double accv = 0;
+  LBM_CUDA(cudaMemcpyAsync(&accv, nu_acc, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(cudaStreamSynchronize(c->stream));
+  auto is_wall = [&](int x, int y) {
+    return (d.wall_l && x == 0) || (d.wall_r && x == d.nx - 1) || (d.wall_b && y == 0) ||
+           (d.wall_t && y == d.ny - 1);
+  };
+  size_t cnt = 0;
+  double sum = 0;
+  for (int y = 0; y < d.ny; ++y)
+    for (int x = 0; x < d.nx; ++x)
+      if (!is_wall(x, y)) {
+        ++cnt;
+        sum += hfl[(size_t)y * d.nx + x];
+      }
+  if (melt) {
+    *J = cnt ? sum / (double)cnt : 0.0;
+    for (int y = 0; y < d.ny; ++y)
+      for (int x = 0; x < d.nx; ++x)
+        if (!is_wall(x, y)) seedf[(size_t)y * d.nx + x] = (float)(1.0 / (double)cnt);
+  } else {
+    *J = accv / (double)nsteps;
+    for (int y = y0; y < y1; ++y)
+      for (int i = 0; i < 5; ++i) {
+        seedg[i * n + (size_t)y * d.nx + 1] = (float)(-2.0 * kN);
+        seedg[i * n + (size_t)y * d.nx + 2] = (float)(0.5 * kN);
+      }
+  }
+  LBM_CUDA(cudaMemcpyAsync(b.lamf, seedf.data(), n * sizeof(float), cudaMemcpyHostToDevice,
+                           c->stream));
+  LBM_CUDA(cudaMemcpyAsync(lg[0], seedg.data(), 5 * n * sizeof(float), cudaMemcpyHostToDevice,
+                           c->stream));
+  LBM_CUDA(cudaMemsetAsync(lf[0], 0, 9 * n * sizeof(float), c->stream));
+  LBM_CUDA(cudaMemsetAsync(b.lama, 0, n * sizeof(float), c->stream));
+  LBM_CUDA(cudaMemsetAsync(lK, 0, n * sizeof(float), c->stream));
+  LBM_CUDA(cudaMemsetAsync(b.lamtw, 0, d.ny * sizeof(float), c->stream));
+  LBM_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(int), c->stream));
+  {
+    std::vector<float> ha(n);
+    std::vector<float> hphi(n);
+    LBM_CUDA(cudaMemcpy(hphi.data(), d.phi, n * sizeof(float), cudaMemcpyDeviceToHost));
+    for (size_t s = 0; s < n; ++s) ha[s] = hphi[s] * d.lat;
+    LBM_CUDA(cudaMemcpyAsync(b.a, ha.data(), n * sizeof(float), cudaMemcpyHostToDevice,
+                             c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  lbm::adj_list(c->d, S + (size_t)nsteps * st + 14 * n, lists[0], counts, c->stream);
+  // the step's parameters
+  lbm::CoupledStep<float> A;
+  A.geo = lbm::CoupledGeo{d.nx, d.ny, d.per_x, d.per_y, {d.bc[0], d.bc[1], d.bc[2], d.bc[3]}};
+  A.n = (long long)n;
+  A.fp.rho0 = d.rho0;
+  A.fp.nu_l = d.nu_l;
+  A.fp.g_beta = d.g_beta;
+  A.fp.T_ref = d.T_ref;
+  const float lam[9] = {1.f, d.s_e, d.s_eps, 1.f, d.s_q, 1.f, d.s_q, d.s_nu, d.s_nu};
+  for (int k = 0; k < 9; ++k) A.fp.lam[k] = lam[k];
+  A.fp.eps = 1e-30f;
+  A.tp.sigma = d.sigma;
+  A.tp.csT2 = d.csT2;
+  A.tp.varpi = d.varpi;
+  const float th[5] = {1.f, d.z_a, d.z_a, d.z_e, d.z_nu};
+  for (int k = 0; k < 5; ++k) A.tp.theta[k] = th[k];
+  A.tp.w0 = d.wt0;
+  A.tp.w1 = d.wt1;
+  A.f_act = d.f_act;
+  A.T_s = d.T_s;
+  A.T_l = d.T_l;
+  A.lat = d.lat;
+  A.nu_g1 = (float)(-2.0 * kN);
+  A.nu_g2 = (float)(0.5 * kN);
+  A.nu_tw = (float)(1.5 * kN);
+  A.ny0 = y0;
+  A.ny1 = y1;
+  const float w9[9] = {4.f / 9, 1.f / 9, 1.f / 9, 1.f / 9, 1.f / 9,
+                       1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36};
+  for (int i = 0; i < 9; ++i) A.foff[i] = w9[i] * d.rho0;
+  A.phi = d.phi;
+  A.K = d.K;
+  A.lfl = b.lamf;
+  A.lphi = b.lama;
+  A.lK = lK;
+  A.lTw = b.lamtw;
+  // reverse sweep
+  int cur = 0;
+  for (int64_t m = nsteps - 1; m >= 0; --m) {
+    const float* s0 = S + (size_t)m * st;
+    const float* s1 = S + (size_t)(m + 1) * st;
+    A.f0 = s0;
+    A.g0 = s0 + 9 * n;
+    A.fl0 = s0 + 14 * n;
+    A.fl1 = s1 + 14 * n;
+    A.lf1 = lf[cur];
+    A.lg1 = lg[cur];
+    A.lf0 = lf[1 - cur];
+    A.lg0 = lg[1 - cur];
+    A.next_list = lists[1 - cur];
+    A.next_count = counts + 1 - cur;
+    b.lamg = lg[cur];
+    lbm::adj_coupled_step(c->d, b, A, lists[cur], counts + cur, counts + 1 - cur, sweeps,
+                          c->stream);
+    LBM_CUDA(cudaGetLastError());
+    cur ^= 1;
+  }
+  // d J / d ln K = K d J / d K
+  std::vector<float> hphi(n), hK(n), hlK(n), hlphi(n), hltw(d.ny);
+  LBM_CUDA(cudaMemcpyAsync(hlphi.data(), b.lama, n * sizeof(float), cudaMemcpyDeviceToHost,
+                           c->stream));
+  LBM_CUDA(cudaMemcpyAsync(hlK.data(), lK, n * sizeof(float), cudaMemcpyDeviceToHost,
+                           c->stream));
+  LBM_CUDA(cudaMemcpyAsync(hK.data(), d.K, n * sizeof(float), cudaMemcpyDeviceToHost,
+                           c->stream));
+  LBM_CUDA(cudaMemcpyAsync(hltw.data(), b.lamtw, d.ny * sizeof(float), cudaMemcpyDeviceToHost,
+                           c->stream));
+  LBM_CUDA(cudaStreamSynchronize(c->stream));
+  for (size_t s = 0; s < n; ++s) hlK[s] *= hK[s];
+  const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+  LBM_CUDA(cudaMemcpy(d_phi, hlphi.data(), n * sizeof(float), kind));
+  LBM_CUDA(cudaMemcpy(d_lnK, hlK.data(), n * sizeof(float), kind));
+  LBM_CUDA(cudaMemcpy(d_wall_T_left, hltw.data(), d.ny * sizeof(float), kind));
+  // the context ends where the forward run left it
+  return LBM_OK;
+}

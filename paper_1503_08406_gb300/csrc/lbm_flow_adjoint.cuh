@@ -407,6 +407,7 @@ struct CoupledStep {
   R nu_g1, nu_g2, nu_tw;
   int ny0, ny1;
   const R *f0, *g0, *fl0, *fl1, *phi, *K;   // the step's state: before it, and f_l after
+  R foff[9];                                 // added to f0 (stored deviations: w_i rho0)
   const R* lf1;                              // adjoint of f after the step
   const R* lg1;                              // adjoint of g after it, nu added on the band
   R *lf0, *lg0;                              // adjoints before the step
@@ -442,7 +443,7 @@ LBM_HD void coupled_reverse_node(const CoupledStep<R>& A, int x, int y) {
   R g[5], T = 0;
   for (int i = 0; i < 5; ++i) T += (g[i] = A.g0[i * n + s]);
   R f[9], ux = 0, uy = 0;
-  for (int i = 0; i < 9; ++i) f[i] = A.f0[i * n + s];
+  for (int i = 0; i < 9; ++i) f[i] = A.f0[i * n + s] + A.foff[i];
   if (act) {
     FlowFwd<R> w;
     flow_node_forward(A.fp, f, T, A.fl0[s], A.phi[s], A.K[s], w);

@@ -135,6 +135,8 @@ def load():
                                          _VP, _VP, _DP, ctypes.c_int]
         lib.lbm_adjoint.argtypes = [_VP, ctypes.c_int, ctypes.c_int64, ctypes.c_int32,
                                     ctypes.c_int32, _VP, _VP, _DP, ctypes.c_int]
+        lib.lbm_adjoint_coupled.argtypes = [_VP, ctypes.c_int, ctypes.c_int64, ctypes.c_int32,
+                                            _VP, _VP, _VP, _DP, ctypes.c_int]
         lib.lbm_batch_create.argtypes = [ctypes.POINTER(_VP), ctypes.c_int, _VP,
                                          ctypes.POINTER(_VP)]
         lib.lbm_batch_step.argtypes = [_VP, ctypes.c_int64]
@@ -294,6 +296,21 @@ class Lattice:
                                     int(checkpoint_every), int(mu_sweeps), dphi.ctypes.data,
                                     dtw.ctypes.data, ctypes.byref(J), 0), "lbm_adjoint")
         return J.value, dphi, dtw
+
+    def adjoint_coupled(self, nsteps: int, objective: str = "melt", mu_sweeps: int = 0):
+        """The flow lattice on: run nsteps steps; return the objective and its
+        gradients with respect to the porosity field ([ny, nx]), ln K
+        ([ny, nx]) and the left wall's temperature profile ([ny])
+        (lbm_adjoint_coupled in include/lbm.h)."""
+        dphi = np.zeros((self.ny, self.nx), dtype=np.float32)
+        dlnK = np.zeros((self.ny, self.nx), dtype=np.float32)
+        dtw = np.zeros(self.ny, dtype=np.float32)
+        J = ctypes.c_double()
+        _check(self.lib.lbm_adjoint_coupled(self._h, self.OBJECTIVES[objective], int(nsteps),
+                                            int(mu_sweeps), dphi.ctypes.data, dlnK.ctypes.data,
+                                            dtw.ctypes.data, ctypes.byref(J), 0),
+               "lbm_adjoint_coupled")
+        return J.value, dphi, dlnK, dtw
 
     def adjoint_melt(self, nsteps: int, checkpoint_every: int = 0, mu_sweeps: int = 0):
         """The melted fraction after nsteps steps and its gradients

@@ -96,6 +96,7 @@ extern "C" int coupled_reverse_step_f64(int nx, int ny, int per_x, int per_y, co
   std::vector<int> list(n);
   int count = 0;
   A.f0 = f0;
+  for (int i = 0; i < 9; ++i) A.foff[i] = 0;
   A.g0 = g0;
   A.fl0 = fl0;
   A.fl1 = fl1;
