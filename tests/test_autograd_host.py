@@ -35,7 +35,7 @@ def test_coupled_objective_plumbing():
     lnK = torch.zeros((3, 4), dtype=torch.float32, requires_grad=True)
     tw = torch.ones(3, dtype=torch.float32, requires_grad=True)
     J = CoupledObjective.apply(phi, lnK, tw, lat, np.zeros((3, 4)), np.zeros((3, 4)), 7, "nusselt")
-    assert abs(J.item() - (6.0 + 0.0 + 3.0)) < 1e-6 if not J.requires_grad else abs(J.detach().item() - 9.0) < 1e-6
+    assert abs(J.detach().item() - 9.0) < 1e-6   # phi 12 x 0.5, ln K 0, wall 3 x 1
     np.testing.assert_allclose(lat.fields[1], 1.0)   # K = exp(lnK)
     (0.5 * J).backward()
     np.testing.assert_allclose(phi.grad.numpy(), 1.0)
