@@ -364,5 +364,7 @@ class CoupledRef:
         lnK = torch.tensor(np.log(np.asarray(K, dtype=np.float64)), requires_grad=True)
         tw = torch.tensor(np.asarray(Tw_left, dtype=np.float64), requires_grad=True)
         _, _, _, J = self.run(steps, T0, fl0, phi_t, torch.exp(lnK), tw, objective, ckpt)
-        d_phi, d_lnK, d_tw = torch.autograd.grad(J, (phi_t, lnK, tw))
+        grads = torch.autograd.grad(J, (phi_t, lnK, tw), allow_unused=True)
+        d_phi, d_lnK, d_tw = (torch.zeros_like(x) if gr is None else gr
+                              for gr, x in zip(grads, (phi_t, lnK, tw)))   # no wall: no T_w
         return float(J.detach()), d_phi.numpy(), d_lnK.numpy(), d_tw.numpy()
