@@ -71,11 +71,13 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--storage", choices=("fp32", "fp16", "bf16"), default="fp32",
                     help="population storage (arithmetic is FP32 in every case)")
-    ap.add_argument("--workload", choices=("cavity", "batched", "adjoint"), default="cavity",
+    ap.add_argument("--workload", choices=("cavity", "batched", "adjoint", "adjoint_coupled"),
+                    default="cavity",
                     help="cavity: the 2048^2 heterogeneous cavity (default); batched: 64 "
                          "uneven cavities advanced together through one CUDA graph; adjoint: "
                          "melted fraction and its gradients on an n x ny conduction slab, "
-                         "timed against the forward run alone")
+                         "timed against the forward run alone; adjoint_coupled: the same "
+                         "with the flow lattice on, an n^2 melting cavity")
     ap.add_argument("--ny", type=int, default=512, help="adjoint workload: slab height")
     ap.add_argument("--objective", choices=("melt", "nusselt"), default="melt",
                     help="adjoint workload: melted fraction at the end, or the left-wall "
@@ -389,6 +391,58 @@ def adjoint(args, torch):
     return 0
 
 
+def adjoint_coupled(args, torch):
+    """An n^2 melting cavity (lbm_workloads.melted_cavity, mushy band [0.1, 0.4]):
+    `steps` steps forward alone, then the same steps with the coupled adjoint
+    (lbm_adjoint_coupled: forward keeping every state, reverse sweep,
+    gradients back on the host); value = adjoint time / forward time."""
+    import lbm_workloads as W
+    from paper_1503_08406_gb300 import Lattice
+    w = W.melted_cavity(args.n)
+    params = dict(w.params)
+    params.update(T_s=0.1, T_l=0.4)
+    stream = torch.cuda.current_stream()
+    lat = Lattice(w.nx, w.ny, stream=stream, **params)
+
+    def reset():
+        lat.set_fields(w.phi, w.K, w.T0, w.fl0)
+        torch.cuda.synchronize()
+
+    reset()
+    lat.step(args.warmup)
+    reset()
+    lat.adjoint_coupled(max(args.warmup, 2), args.objective)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reset()
+    e0.record(stream)
+    lat.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_fwd = e0.elapsed_time(e1)
+    reset()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    with ClockSampler(vis.split(",")[0] if vis else "0") as clk:
+        t0 = time.perf_counter()
+        J, dphi, dlnK, dtw = lat.adjoint_coupled(args.steps, args.objective)
+        ms_adj = (time.perf_counter() - t0) * 1e3
+    line = {
+        "metric": "coupled adjoint time / forward time, %s and its gradients" % args.objective,
+        "value": ms_adj / ms_fwd, "unit": "x", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_adj / args.steps, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name + "_band0.1-0.4", "lattice": [w.nx, w.ny],
+                   "memory": "every state kept (%.2f GB)" % ((args.steps + 1) * w.cells * 60 / 1e9)},
+        "forward": {"ms": ms_fwd, "MLUPS": w.cells * args.steps / (ms_fwd * 1e-3) / 1e6,
+                    "timing": "CUDA events on the lattice's stream (CUDA graphs)"},
+        "adjoint": {"ms": ms_adj, "timing": "host wall clock around lbm_adjoint_coupled",
+                    "J": J, "dJ_dlnK_max": float(abs(dlnK).max()),
+                    "dJ_dphi_max": float(abs(dphi).max())},
+        "status": lat.status(), "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse(argv)
     if args.impl == "reference":
@@ -398,12 +452,13 @@ def main(argv=None):
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device (there is no CPU path)")
     torch.cuda.set_device(local)
-    if args.workload in ("batched", "adjoint"):
+    if args.workload in ("batched", "adjoint", "adjoint_coupled"):
         if world > 1:
             raise SystemExit("the %s workload runs on one GPU" % args.workload)
         import __graft_entry__
         __graft_entry__.build()
-        return batched(args, torch) if args.workload == "batched" else adjoint(args, torch)
+        run = {"batched": batched, "adjoint": adjoint, "adjoint_coupled": adjoint_coupled}
+        return run[args.workload](args, torch)
     dist = init_dist(world, "nccl")
     device = torch.device("cuda", local)
     if local == 0:
