@@ -25,9 +25,11 @@ The flow nodes are chosen by f_l(n) >= f_act, a step function: its derivative
 is 0 wherever it is defined, and finite differences that do not move a node
 across f_act agree with it.  Square roots of speeds carry a 1e-300 floor so
 that a node at rest has a finite derivative; the forward values are those of
-the oracle.  Scope: one sigma, one thermal diffusivity; any mix of periodic
-axes and wall sides the oracle accepts (left and right walls together, bottom
-and top together).
+the oracle.  Scope: one sigma; one thermal diffusivity or, with
+alpha_l != alpha_s (Sec. 4.1), the rate of the flux moments following f_l(n)
+(a wall node's that of its inward node); the flow lattice on or off; any mix
+of periodic axes and wall sides the oracle accepts (left and right walls
+together, bottom and top together).
 """
 from __future__ import annotations
 
@@ -71,8 +73,8 @@ def _inv_orthogonal_rows(M):
 
 
 class CoupledRef:
-    """The oracle's coupled step for a parameter set (the keys of
-    oracle.DEFAULTS, flow = 1)."""
+    """The oracle's step for a parameter set (the keys of oracle.DEFAULTS; with
+    flow = 0 the flow populations stay as they are and u = 0)."""
 
     def __init__(self, nx: int, ny: int, params: dict):
         p = dict(params)
@@ -80,10 +82,11 @@ class CoupledRef:
         bc = [BC[b] if isinstance(b, str) else int(b) for b in p["bc"]]
         if (bc[0] == 0) != (bc[1] == 0) or (bc[2] == 0) != (bc[3] == 0):
             raise ValueError("left and right (bottom and top) are periodic together")
-        if not p.get("flow", 1):
-            raise ValueError("the coupled reference runs the flow lattice")
-        if float(p.get("alpha_ratio", 0.0)) not in (0.0, 1.0) or float(p.get("sigma_solid", 0.0)):
-            raise ValueError("one thermal diffusivity and one sigma")
+        self.flow = int(p.get("flow", 1))
+        if float(p.get("sigma_solid", 0.0)):
+            raise ValueError("one sigma")
+        r = float(p.get("alpha_ratio", 0.0))
+        self.alpha_ratio = r if (r > 0 and r != 1.0) else None
         self.bc = bc
         self.T_bc = [float(t) for t in p.get("T_bc", (1.0, 0.0, 0.0, 0.0))]
         self.per_x, self.per_y = bc[0] == 0, bc[2] == 0
@@ -103,18 +106,23 @@ class CoupledRef:
         # Sec. 4.3 relations for the relaxation times and the buoyancy
         J, Pr, Ra, Ma, lam = g("J", 1.0) or 1.0, g("Pr", 0.0), g("Ra", 0.0), g("Ma", 0.1), \
             g("lambda_", 1.0) or 1.0
-        tau_nu = g("tau_nu", -1.0)
-        if not tau_nu > 0:
-            tau_nu = 0.5 + Ma * J * self.H * math.sqrt(3 * Pr) / math.sqrt(Ra)
-        self.nu_l = CS2 * (tau_nu - 0.5) / J
-        tau_T = g("tau_T", -1.0)
-        if not tau_T > 0:
-            tau_T = 0.5 + lam * CS2 * (tau_nu - 0.5) / (J * self.sigma * csT2 * Pr)
-        g_beta = g("g_beta", -1.0)
-        if not g_beta >= 0:
-            alpha_l = self.nu_l / Pr
-            g_beta = Ra * self.nu_l * alpha_l / (self.dT * self.H ** 3)
+        if self.flow:
+            tau_nu = g("tau_nu", -1.0)
+            if not tau_nu > 0:
+                tau_nu = 0.5 + Ma * J * self.H * math.sqrt(3 * Pr) / math.sqrt(Ra)
+            self.nu_l = CS2 * (tau_nu - 0.5) / J
+            tau_T = g("tau_T", -1.0)
+            if not tau_T > 0:
+                tau_T = 0.5 + lam * CS2 * (tau_nu - 0.5) / (J * self.sigma * csT2 * Pr)
+            g_beta = g("g_beta", -1.0)
+            if not g_beta >= 0:
+                alpha_l = self.nu_l / Pr
+                g_beta = Ra * self.nu_l * alpha_l / (self.dT * self.H ** 3)
+        else:   # conduction: tau_T given, no flow lattice
+            tau_nu, self.nu_l, g_beta = 1.0, 0.0, 0.0
+            tau_T = g("tau_T", -1.0)
         self.g_beta = g_beta
+        self.tau_T = tau_T
         s_e, s_eps, s_q = (g("s_e", 0.0) or 1.1), (g("s_eps", 0.0) or 1.1), (g("s_q", 0.0) or 1.2)
         self.lam = torch.tensor([1, s_e, s_eps, 1, s_q, 1, s_q, 1 / tau_nu, 1 / tau_nu], dtype=D)
         ze, zn = (g("zeta_e", 0.0) or 1.5), (g("zeta_nu", 0.0) or 1.5)
@@ -266,10 +274,15 @@ class CoupledRef:
         zero = torch.zeros_like(Tf)
         gw = self._geq(Tw, zero, zero) + gf - self._geq(Tf, uxf, uyf)
         gpre = torch.where(self.wall[None], gw, g)
-        # collision, Eq. (35), source-free part
+        # collision, Eq. (35), source-free part; with alpha_l != alpha_s the rate
+        # follows f_l(n), a wall node's that of its inward node
         uxc = torch.where(self.wall, zero, ux)
         uyc = torch.where(self.wall, zero, uy)
-        gpost = self.collide_thermal(gpre, uxc, uyc)
+        za = None
+        if self.alpha_ratio is not None:
+            flw = torch.where(self.wall, flat(fl)[self.inward].reshape(self.ny, self.nx), fl)
+            za = self.theta_T(flw)
+        gpost = self.collide_thermal(gpre, uxc, uyc, za)
         gstar = torch.stack([self._shift(gpost[i], EX5[i], EY5[i]) for i in range(5)])
         # the iterative enthalpy method with the streamed latent source
         base = gstar.sum(dim=0)
@@ -289,16 +302,25 @@ class CoupledRef:
                             for i in range(5)])
         return gnew, fk
 
-    def collide_thermal(self, g, ux, uy):
+    def collide_thermal(self, g, ux, uy, za=None):
         """The source-free D2Q5 collision of Eq. (35) with n^eq of Eq. (34) of
-        every node (g: [5, ...], u: [...])."""
+        every node (g: [5, ...], u: [...]); za: the flux moments' rate per node
+        (default 1/tau_T)."""
         nmom = torch.einsum("ki,i...->k...", N5, g)
         T = nmom[0]
         neq = torch.stack([T, ux * T / self.sigma, uy * T / self.sigma, self.varpi * T,
                            torch.zeros_like(T)])
-        th = self.theta.reshape(5, *([1] * (g.dim() - 1)))
+        th = self.theta.reshape(5, *([1] * (g.dim() - 1))).expand_as(nmom)
+        if za is not None:
+            th = torch.stack([th[0], za.expand_as(T), za.expand_as(T), th[3], th[4]])
         npost = nmom - th * (nmom - neq)
         return torch.einsum("ik,k...->i...", self.Ninv, npost)
+
+    def theta_T(self, fl):
+        """The flux moments' rate with alpha_l != alpha_s (Sec. 4.1):
+        1 / (1/2 + (tau_T - 1/2) (f_l + (1 - f_l) alpha_s / alpha_l))."""
+        r = self.alpha_ratio
+        return 1.0 / (0.5 + (self.tau_T - 0.5) * (fl + (1.0 - fl) / r))
 
     def extrapolate_wall(self, gf, Tw, uxf, uyf):
         """Populations a wall node takes before collision from its inward
@@ -311,7 +333,10 @@ class CoupledRef:
     # ---- steps -------------------------------------------------------------
     def step(self, f, g, fl, phi, K, Tw_left):
         T = g.sum(dim=0)
-        f1, ux, uy = self._flow(f, T, fl, phi, K)
+        if self.flow:
+            f1, ux, uy = self._flow(f, T, fl, phi, K)
+        else:
+            f1, ux, uy = f, torch.zeros_like(T), torch.zeros_like(T)
         g1, fl1 = self._thermal(g, fl, phi * self.lat, ux, uy, Tw_left)
         return f1, g1, fl1
 

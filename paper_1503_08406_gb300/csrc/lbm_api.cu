@@ -1335,6 +1335,10 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t mu_sw
   A.nu_tw = (float)(1.5 * kN);
   A.ny0 = y0;
   A.ny1 = y1;
+  A.alpha_var = 0;   // (rejected above)
+  A.tauT_l = 0.f;
+  A.inv_aratio = 1.f;
+  A.flow = 1;
   const float w9[9] = {4.f / 9, 1.f / 9, 1.f / 9, 1.f / 9, 1.f / 9,
                        1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36};
   for (int i = 0; i < 9; ++i) A.foff[i] = w9[i] * d.rho0;

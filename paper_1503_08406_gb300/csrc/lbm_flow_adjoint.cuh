@@ -306,15 +306,17 @@ LBM_HD void thermal_node_collide(const ThermalNode<R>& p, const R g[5], R ux, R 
   d2q5_NT(np, gpost);
 }
 
-// its reverse: lg = adjoint of g+; out: adjoint of g (lgin) and of u
+// its reverse: lg = adjoint of g+; out: adjoint of g (lgin) and of u, and
+// (lz non-null) of the flux moments' rate theta_1 = theta_2
 template <typename R>
 LBM_HD void thermal_node_adjoint(const ThermalNode<R>& p, const R g[5], R ux, R uy, const R lg[5],
-                                 R lgin[5], R* lux, R* luy) {
+                                 R lgin[5], R* lux, R* luy, R* lz = nullptr) {
   R n[5], lnp[5], ln[5];
   d2q5_N(g, n);
   const R T = n[0];
   d2q5_N(lg, lnp);
   for (int k = 0; k < 5; ++k) lnp[k] /= d2q5_D<R>(k);
+  if (lz) *lz = -lnp[1] * (n[1] - ux * T / p.sigma) - lnp[2] * (n[2] - uy * T / p.sigma);
   R lneq[5];
   for (int k = 0; k < 5; ++k) {
     ln[k] = (1 - p.theta[k]) * lnp[k];
@@ -402,6 +404,12 @@ struct CoupledStep {
   FlowNode<R> fp;
   ThermalNode<R> tp;
   R f_act, T_s, T_l, lat;
+  // alpha_l != alpha_s (Sec. 4.1): the flux moments' rate follows f_l(n),
+  // 1 / (1/2 + (tauT_l - 1/2) (f_l + (1 - f_l) inv_aratio)); a wall node's
+  // that of its inward node
+  int alpha_var;
+  R tauT_l, inv_aratio;
+  int flow;                                  // the flow lattice is on
   // the objective's direct terms in the state before the step: all five
   // populations at x = 1 and x = 2 and the left wall value, rows [ny0, ny1)
   R nu_g1, nu_g2, nu_tw;
@@ -416,10 +424,23 @@ struct CoupledStep {
   int *next_list, *next_count;               // band of the state before the step
 };
 
+// the flux moments' rate at liquid fraction fl, and its derivative
+template <typename R>
+LBM_HD R coupled_rate(const CoupledStep<R>& A, R fl, R* dz) {
+  if (!A.alpha_var) {
+    *dz = 0;
+    return A.tp.theta[1];
+  }
+  const R c = A.tauT_l - R(0.5);
+  const R z = R(1) / (R(0.5) + c * (fl + (1 - fl) * A.inv_aratio));
+  *dz = -z * z * c * (1 - A.inv_aratio);
+  return z;
+}
+
 template <typename R>
 LBM_HD bool coupled_active(const CoupledStep<R>& A, int s) {
   const int y = s / A.geo.nx, x = s - y * A.geo.nx;
-  return !A.geo.wall(x, y) && A.fl0[s] >= A.f_act;
+  return A.flow && !A.geo.wall(x, y) && A.fl0[s] >= A.f_act;
 }
 
 // lam_g+ of node (x, y) streamed back from lg1 (0 from outside the lattice)
@@ -450,13 +471,19 @@ LBM_HD void coupled_reverse_node(const CoupledStep<R>& A, int x, int y) {
     ux = w.ux;
     uy = w.uy;
   }
-  // thermal: this node's collision (u = 0 on walls and off flow)
-  R lp[5], lgin[5], lux = 0, luy = 0, S = 0;
+  // thermal: this node's collision (u = 0 on walls and off flow), at the rate
+  // of f_l(n) (a wall node's inward node's)
+  R lp[5], lgin[5], lux = 0, luy = 0, S = 0, lz = 0;
   coupled_lp(A, x, y, lp);
   for (int i = 0; i < 5; ++i) S += (i == 0 ? A.tp.w0 : A.tp.w1) * lp[i];
+  R dz;
+  ThermalNode<R> tpn = A.tp;
+  tpn.theta[1] = tpn.theta[2] =
+      coupled_rate(A, wall ? A.fl0[G.inward(x, y)] : A.fl0[s], &dz);
   {
     R lx, ly;
-    thermal_node_adjoint(A.tp, g, wall ? R(0) : ux, wall ? R(0) : uy, lp, lgin, &lx, &ly);
+    thermal_node_adjoint(tpn, g, wall ? R(0) : ux, wall ? R(0) : uy, lp, lgin, &lx, &ly,
+                         A.alpha_var ? &lz : nullptr);
     if (act) {
       lux += lx;
       luy += ly;
@@ -472,7 +499,7 @@ LBM_HD void coupled_reverse_node(const CoupledStep<R>& A, int x, int y) {
     const bool r = y >= A.ny0 && y < A.ny1;
     const R src = r && x == 1 ? A.nu_g1 : r && x == 2 ? A.nu_g2 : R(0);
     for (int i = 0; i < 5; ++i) lg[i] = lgin[i] + src;
-    lfl = a * S;
+    lfl = a * S + lz * dz;
     const R df = A.fl1[s] - A.fl0[s];
     if (df != 0) A.lphi[s] += -df * S * A.lat;
     // the extrapolation of every wall node whose inward node this is
@@ -482,9 +509,22 @@ LBM_HD void coupled_reverse_node(const CoupledStep<R>& A, int x, int y) {
       const int bx = x + ex9[d], by = y + ey9[d];
       if (bx < 0 || bx >= G.nx || by < 0 || by >= G.ny) continue;
       if (!G.wall(bx, by) || G.inward(bx, by) != s) continue;
-      R lpb[5], lgb[5], lx, ly, lTwv, lxf, lyf;
+      R lpb[5], lgb[5], lx, ly, lTwv, lxf, lyf, lzb = 0, dzb;
       coupled_lp(A, bx, by, lpb);
-      thermal_node_adjoint(A.tp, g, R(0), R(0), lpb, lgb, &lx, &ly);
+      ThermalNode<R> tpb = A.tp;
+      tpb.theta[1] = tpb.theta[2] = coupled_rate(A, A.fl0[s], &dzb);   // the wall's rate: ours
+      // the wall node's populations before collision up to g^eq(T_w, 0), whose
+      // flux moments are 0: enough for the rate's adjoint (u = 0 there)
+      R gb[5];
+      {
+        const int ex5[5] = {0, 1, 0, -1, 0};
+        const int ey5[5] = {0, 0, 1, 0, -1};
+        const R c = A.tp.sigma * A.tp.csT2;
+        for (int i = 0; i < 5; ++i)
+          gb[i] = g[i] - (i == 0 ? A.tp.w0 : A.tp.w1) * T * (1 + (ex5[i] * ux + ey5[i] * uy) / c);
+      }
+      thermal_node_adjoint(tpb, gb, R(0), R(0), lpb, lgb, &lx, &ly, A.alpha_var ? &lzb : nullptr);
+      lfl += lzb * dzb;
       R lgf[5] = {0, 0, 0, 0, 0};
       wall_extrapolation_adjoint(A.tp, g, ux, uy, lgb, lgf, &lTwv, &lxf, &lyf);
       const int sd = G.side(bx, by);

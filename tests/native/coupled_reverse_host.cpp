@@ -12,7 +12,8 @@
 
 // prm layout: flowprm[14] (rho0, nu_l, g_beta, T_ref, lam[9], eps), thprm[10]
 // (sigma, csT2, varpi, theta[5], w0, w1), sc[4] = (f_act, T_s, T_l, lat),
-// nuprm[5] = (nu_g1, nu_g2, nu_tw, ny0, ny1).  State of the step: f0 [9][n],
+// nuprm[8] = (nu_g1, nu_g2, nu_tw, ny0, ny1, tau_T,l (0: one diffusivity),
+// alpha_s / alpha_l, flow lattice on).  State of the step: f0 [9][n],
 // g0 [5][n], fl0, fl1 (f_l before / after).  Adjoints after the step in lf,
 // lg, lfl (overwritten with those before it); lphi, lK and lTw accumulate.
 // Returns the number of Jacobi sweeps.
@@ -48,6 +49,10 @@ extern "C" int coupled_reverse_step_f64(int nx, int ny, int per_x, int per_y, co
   A.nu_tw = nuprm[2];
   A.ny0 = (int)nuprm[3];
   A.ny1 = (int)nuprm[4];
+  A.alpha_var = nuprm[5] > 0;   // alpha_l / alpha_s != 1: nuprm[5] = tau_T,l, nuprm[6] = alpha_s/alpha_l
+  A.tauT_l = nuprm[5];
+  A.inv_aratio = nuprm[6];
+  A.flow = nuprm[7] != 0;
   const double dTt = A.T_l - A.T_s, w0 = A.tp.w0, w1 = A.tp.w1;
   const int ex[5] = {0, 1, 0, -1, 0};
   const int ey[5] = {0, 0, 1, 0, -1};

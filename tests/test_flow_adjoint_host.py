@@ -166,25 +166,36 @@ def _geometry(which):
     if which == "box":
         w = W.periodic_box(16, flow=1, T_s=-0.1, T_l=0.1)
         return w, dict(w.params), np.zeros(w.ny)
+    if which == "twophase":   # Sec. 4.1 slab, alpha_l = 10 alpha_s, flow off
+        w = W.adjoint_slab(40, 4)
+        params = dict(w.params)
+        params["alpha_ratio"] = 10.0
+        params["tau_T"] = 0.5 + 10 * 0.02 / 0.2
+        return w, params, w.wall_T_left
     w = W.melted_cavity(24)
     params = dict(w.params)
     params.update(T_s=0.1, T_l=0.4)
     if which == "channel":
         params["bc"] = ("dirichlet", "adiabatic", "periodic", "periodic")
+    if which == "cavity_alpha":
+        params["alpha_ratio"] = 3.0
     tw = 1.0 + 0.1 * np.sin(2 * np.pi * np.arange(w.ny) / w.ny)
     return w, params, tw
 
 
 @pytest.mark.parametrize("which,objective", [("cavity", "melt"), ("cavity", "nusselt"),
                                              ("channel", "melt"), ("channel", "nusselt"),
-                                             ("box", "melt")])
+                                             ("box", "melt"), ("twophase", "melt"),
+                                             ("twophase", "nusselt"), ("cavity_alpha", "melt")])
 def test_reverse_sweep_from_node_functions_equals_autograd(rev, which, objective):
     """The reverse sweep of the coupled step from lbm::coupled_reverse_node, the
     reverse-sweep kernel's body (run over every node on the host, after a
     Jacobi solve of the fixed point's adjoint on the band, by
     tests/native/coupled_reverse_host.cpp), over 40 steps: the gradients in
     ln K, phi and the wall profile equal autograd of the FP64 reference, on a
-    walled cavity, a channel periodic in y and a doubly periodic box."""
+    walled cavity, a channel periodic in y, a doubly periodic box, the
+    Sec. 4.1 slab with alpha_l = 10 alpha_s (flow off) and the cavity with
+    alpha_l = 3 alpha_s."""
     from oracle.coupled_ref import BC, CoupledRef
     w, params, tw = _geometry(which)
     steps = 40
@@ -203,7 +214,10 @@ def test_reverse_sweep_from_node_functions_equals_autograd(rev, which, objective
     lphi, lK, lTw = np.zeros(n), np.zeros(n), np.zeros(w.ny)
     bcv = [BC[b] if isinstance(b, str) else int(b) for b in params["bc"]]
     per_x, per_y = int(bcv[0] == 0), int(bcv[2] == 0)
-    nuprm = np.zeros(5)
+    nuprm = np.zeros(8)
+    nuprm[7] = ref.flow
+    if ref.alpha_ratio is not None:
+        nuprm[5], nuprm[6] = ref.tau_T, 1.0 / ref.alpha_ratio
     if objective == "melt":
         lfl[:] = np.where(wall.ravel(), 0.0, 1.0 / (~wall).sum())
     else:
@@ -214,7 +228,7 @@ def test_reverse_sweep_from_node_functions_equals_autograd(rev, which, objective
         # constant N times)
         y0, y1 = (0, w.ny) if per_y else (1, w.ny - 1)
         k = ref.H / (ref.dT * (y1 - y0) * steps)
-        nuprm[:] = (-2 * k, 0.5 * k, 1.5 * k, y0, y1)
+        nuprm[:5] = (-2 * k, 0.5 * k, 1.5 * k, y0, y1)
         src = np.zeros((w.ny, w.nx))
         src[y0:y1, 1] = -2 * k
         src[y0:y1, 2] = 0.5 * k
@@ -237,8 +251,8 @@ def test_reverse_sweep_from_node_functions_equals_autograd(rev, which, objective
     exp = {"phi": d_phi, "lnK": d_lnK, "tw": d_tw}
     for k in exp:
         scale = np.abs(exp[k]).max()
-        if which == "box" and k == "tw":
-            assert scale == 0 and np.abs(got[k]).max() == 0
+        if (which == "box" and k == "tw") or (which == "twophase" and k == "lnK"):
+            assert scale == 0 and np.abs(got[k]).max() == 0   # no wall / no flow
             continue
         assert scale > 0, k
         err = np.abs(got[k] - exp[k]).max() / scale
