@@ -487,6 +487,8 @@ def main(argv=None):
         bytes_step = BYTES_FLOW_NODE_16 * n_flow + BYTES_SOLID_NODE_16 * n_solid
 
     # ---- headline: K steps, CUDA events on the context stream --------------
+    # the CUDA graphs lbm_step will replay are captured before the timed region
+    lat.prepare(args.steps)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     smi_index = vis.split(",")[local] if vis and len(vis.split(",")) > local else str(local)
@@ -530,19 +532,25 @@ def main(argv=None):
                    for a in (w.phi, w.K, w.T0, w.fl0)]
         host_out = [torch.empty((w.ny, w.nx), dtype=torch.float32).pin_memory() for _ in range(5)]
         lat2 = Lattice(w.nx, w.ny, **{**w.params, "storage": args.storage})
+
+        def e2e_run():
+            rc_in = lat2.lib.lbm_set_fields(lat2._h, *[t.data_ptr() for t in host_in], None, 0)
+            lat2.step(args.steps)
+            rc_out = lat2.lib.lbm_get_macros(lat2._h, *[t.data_ptr() for t in host_out], 0)
+            assert rc_in == 0 and rc_out == 0, (rc_in, rc_out)
+
+        e2e_run()            # untimed: the context's graphs are captured, copies warmed
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rc_in = lat2.lib.lbm_set_fields(lat2._h, *[t.data_ptr() for t in host_in], None, 0)
-        lat2.step(args.steps)
-        rc_out = lat2.lib.lbm_get_macros(lat2._h, *[t.data_ptr() for t in host_out], 0)
+        e2e_run()
         dt = time.perf_counter() - t0
-        assert rc_in == 0 and rc_out == 0, (rc_in, rc_out)
         h2d = sum(t.numel() * 4 for t in host_in)
         d2h = sum(t.numel() * 4 for t in host_out)
         e2e_val, _ = aggregate(dt * 1e3, cells, args.steps, world, dist, device)
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                "d2h_bytes_per_step": d2h / args.steps,
-               "note": "set_fields from pinned host + K steps + get_macros to pinned host"}
+               "note": "set_fields from pinned host + K steps + get_macros to pinned host, "
+                       "host wall clock, second run on the same context (graphs captured)"}
         lat2.close()
 
     base = None

@@ -93,6 +93,10 @@ typedef struct {
                                      applied per node as 1/2 + (tau_T - 1/2)(f_l + (1 - f_l)/ratio),
                                      i.e. alpha_e = alpha_l f_l + alpha_s (1 - f_l); 0 or 1: one
                                      diffusivity for both phases */
+  int32_t check_every;            /* > 0: lbm_step scans every population and f_l for NaN or
+                                     Inf after every check_every steps (one read of the state,
+                                     queued on the stream); lbm_status then reports
+                                     LBM_ERR_NONFINITE.  0: no sentinel */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -133,13 +137,32 @@ int lbm_set_fields(lbm_ctx* c, const float* phi, const float* K, const float* T0
 
 /* Queue nsteps >= 0 time steps on the context stream. Returns launch and
  * argument errors only; device-side conditions (an inner iteration that hit
- * its cap) are reported by lbm_status. */
+ * its cap, a non-finite value found by the sentinel, a wait that gave up) are
+ * reported by lbm_status.  Steps are replayed from CUDA graphs of up to 64
+ * steps, keyed by the step parity they start at and their length; a graph is
+ * captured the first time it is needed (host work before its launch). */
 int lbm_step(lbm_ctx* c, int64_t nsteps);
 
-/* Synchronise the stream and report deferred device-side conditions:
- * LBM_ERR_NOT_CONVERGED if any inner enthalpy iteration hit max_inner_iters
- * since the last call (the flag is then cleared), else LBM_OK. */
+/* Capture, without running anything, the CUDA graphs that lbm_step(c, nsteps)
+ * called now would use, so that the call itself only launches them.  No-op
+ * while timing is on.  LBM_ERR_CUDA if a capture fails. */
+int lbm_prepare(lbm_ctx* c, int64_t nsteps);
+
+/* Synchronise the stream and report deferred device-side conditions, in this
+ * order: LBM_ERR_NONFINITE if the sentinel (lbm_params.check_every) found NaN
+ * or Inf in the state (kept until lbm_set_fields or lbm_set_state);
+ * LBM_ERR_TIMEOUT if a bounded device-side wait gave up (the flag is then
+ * cleared); LBM_ERR_NOT_CONVERGED if any inner enthalpy iteration hit
+ * max_inner_iters since the last call (the flag is then cleared); else LBM_OK. */
 int lbm_status(lbm_ctx* c);
+
+/* Self-check of the device-side timeout path: queue one CTA that waits, with
+ * the same bounded wait the stream-collide kernel uses for its bulk copies, on
+ * a shared-memory barrier that nothing ever completes, giving up after
+ * limit_ns nanoseconds (1e3 <= limit_ns <= 1e9).  When it gives up it sets the
+ * flag a timed-out copy sets, so the next lbm_status returns LBM_ERR_TIMEOUT.
+ * The context's state is not touched.  LBM_ERR_INVALID_ARG outside the range. */
+int lbm_check_wait(lbm_ctx* c, int64_t limit_ns);
 
 /* Steps taken since the last lbm_set_fields / lbm_set_state. */
 int64_t lbm_steps_done(const lbm_ctx* c);
@@ -286,23 +309,26 @@ int lbm_timing_read(lbm_ctx* c, double ms[4], int64_t* steps_timed, int64_t* til
 
 /* The sums of lbm_reduce, computed from a checkpoint the caller holds, without
  * allocating any memory. The paper has no counterpart: this is an operational
- * entry point for callers that cannot allocate device memory, e.g. code that
- * records work into a CUDA graph (cudaMalloc is not allowed while a stream is
- * being captured), a framework whose allocator owns all device memory, or
- * monitoring code inside a fixed memory budget. Unlike lbm_create, it needs no
+ * entry point for callers that cannot allocate device memory, e.g. a framework
+ * whose caching allocator owns all device memory and forbids side allocations,
+ * or monitoring code that runs inside a fixed memory budget and must not take
+ * device memory from the job it watches. Unlike lbm_create, it needs no
  * context and no workspace.
- * Inputs (device pointers, natural layout, as lbm_get_state writes them):
- * f[9][ny][nx] as deviations f_i - w_i rho0, g[5][ny][nx], fl and phi
- * [ny][nx]; wall_T_left: NULL or ny device floats (the left-wall profile the
- * context was given). p supplies nx, ny, bc, T_bc, sigma, St, dT, H, rho0.
+ * Inputs (device pointers, natural layout, FP32, as lbm_get_state writes them
+ * for every population storage; p->storage is ignored): f[9][ny][nx] as
+ * deviations f_i - w_i rho0, g[5][ny][nx], fl and phi [ny][nx]; wall_T_left:
+ * NULL or ny device floats (the left-wall profile the context was given).
+ * p supplies nx, ny, bc, T_bc, sigma, St, dT, H, rho0.
  * out (host, 4 doubles): total mass, total enthalpy, mean f_l, mean left-wall
  * Nusselt number, as lbm_reduce defines them.
- * Work is queued on `stream` (a cudaStream_t; NULL: legacy default stream) and
- * the call synchronises it. Scratch is a fixed array of LBM_NOALLOC_MAX_ROWS x 6
- * doubles (768 KB) in the library's device memory, which every GPU that loads
- * the library keeps until the process exits; ny > LBM_NOALLOC_MAX_ROWS returns
- * LBM_ERR_INVALID_ARG. The first call on a device looks up the array's device
- * address (with that device current), so make it before any stream capture.
+ * The call is synchronous: it queues its kernels on `stream` (a cudaStream_t;
+ * NULL: legacy default stream), copies the sums to host memory and synchronises
+ * that stream before it returns. Scratch is a fixed array of
+ * LBM_NOALLOC_MAX_ROWS x 6 doubles (768 KB) in the library's device memory,
+ * which every GPU that loads the library keeps until the process exits;
+ * ny > LBM_NOALLOC_MAX_ROWS returns LBM_ERR_INVALID_ARG. The first call on a
+ * device looks up the array's device address (with that device current), so
+ * make that first call before any stream capture.
  * All calls share the array: calls whose kernels may overlap on the GPU (on
  * different streams without ordering) race and can return wrong sums.
  * Returns LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_CUDA, LBM_ERR_NO_DEVICE or

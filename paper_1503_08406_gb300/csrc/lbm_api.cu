@@ -30,14 +30,15 @@ struct lbm_ctx {
   int nred;
   bool timing;
   std::vector<cudaEvent_t> ev;   // per step: start, after fused, after enthalpy
-  // CUDA graphs of GRAPH_STEPS and 2 steps starting at parity 0, captured on a
-  // private stream and replayed on the context stream
+  // CUDA graphs of 2..GRAPH_MAX steps from either step parity, captured on a
+  // private stream when first needed and replayed on the context stream
   cudaStream_t cap, cap2;         // capture streams (the second one runs the far-tile fused pass)
   cudaEvent_t ev_fork, ev_join;
-  cudaGraphExec_t g_long, g_pair;
+  cudaGraphExec_t gx[2][65];       // [start parity][steps], GRAPH_MAX = 64
+  int gnl[2][65];                  // kernels in each graph
   bool graphs_off;
   int64_t launches;                // kernels launched by lbm_step
-  int nl_long, nl_pair;            // kernels in each graph
+  int64_t since_check;             // steps since the last NaN/Inf sentinel
   lbm::TmaMaps maps;               // tensor maps of the TMA-staged fused kernel
   bool use_tma;
   bool tma_ok;                     // the lattice qualifies for the TMA-staged kernel
@@ -45,7 +46,10 @@ struct lbm_ctx {
   const lbm::TmaMaps* tma() const { return use_tma ? &maps : nullptr; }
 };
 
-static const int GRAPH_STEPS = 32;
+// longest graph lbm_step replays; a call of n steps launches n / GRAPH_MAX of
+// them and one graph of the remainder, so only one graph boundary (where the
+// far-tile overlap restarts) falls in every GRAPH_MAX steps
+static const int GRAPH_MAX = 64;
 
 namespace {
 
@@ -347,8 +351,9 @@ int lbm_create(const lbm_params* pin, void* stream, void* workspace, size_t work
 void lbm_destroy(lbm_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
-  if (c->g_long) cudaGraphExecDestroy(c->g_long);
-  if (c->g_pair) cudaGraphExecDestroy(c->g_pair);
+  for (int q = 0; q < 2; ++q)
+    for (int k = 0; k <= GRAPH_MAX; ++k)
+      if (c->gx[q][k]) cudaGraphExecDestroy(c->gx[q][k]);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->cap2) cudaStreamDestroy(c->cap2);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -372,6 +377,8 @@ static int reset_lists(lbm_ctx* c) {
   const Dev& d = c->d;
   LBM_CUDA(cudaMemsetAsync(d.flags, 0, 2 * sizeof(int) * d.ntiles, c->stream));
   LBM_CUDA(cudaMemsetAsync(d.lcount, 0, 2 * sizeof(int), c->stream));
+  LBM_CUDA(cudaMemsetAsync(d.stats + 5, 0, sizeof(int), c->stream));
+  c->since_check = 0;
   return LBM_OK;
 }
 
@@ -386,28 +393,31 @@ int lbm_set_fields(lbm_ctx* c, const float* phi, const float* K, const float* T0
   if (!c || !phi || !K || !T0 || !fl0) return LBM_ERR_INVALID_ARG;
   const size_t n = (size_t)c->d.n;
   Dev& d = c->d;
+  // Inputs are validated on the device before anything of the context changes:
+  // host arrays are first staged in the scratch buffer (one pinned-to-device
+  // copy each), device arrays are read where they are.
+  const float* src[4] = {phi, K, T0, fl0};
   if (!device_ptrs) {
-    for (size_t s = 0; s < n; ++s) {
-      const float p = phi[s], k = K[s], t = T0[s], l = fl0[s];
-      if (!(p > 0.f && p <= 1.f) || (d.flow && !(p < 1.f)) || !(k > 0.f) || !isfinite(t) ||
-          !(l >= 0.f && l <= 1.f))
-        return LBM_ERR_INVALID_ARG;
+    for (int k = 0; k < 4; ++k) {
+      LBM_CUDA(cudaMemcpyAsync(c->tmp + k * n, src[k], n * sizeof(float), cudaMemcpyHostToDevice,
+                               c->stream));
+      src[k] = c->tmp + k * n;
     }
     if (wall_T_left)
       for (int y = 0; y < c->p.ny; ++y)
         if (!isfinite(wall_T_left[y])) return LBM_ERR_INVALID_ARG;
-  } else {
-    LBM_CUDA(cudaMemsetAsync(c->bad, 0, sizeof(int), c->stream));
-    lbm::launch_validate(d, phi, K, T0, fl0, c->bad, c->stream);
-    int bad = 0;
-    LBM_CUDA(cudaMemcpyAsync(&bad, c->bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    LBM_CUDA(cudaStreamSynchronize(c->stream));
-    if (bad) return LBM_ERR_INVALID_ARG;
   }
-  LBM_TRY(copy_in(c, (float*)d.phi, phi, n, device_ptrs));
-  LBM_TRY(copy_in(c, (float*)d.K, K, n, device_ptrs));
-  LBM_TRY(copy_in(c, d.fl, fl0, n, device_ptrs));
-  LBM_TRY(copy_in(c, c->tmp, T0, n, device_ptrs));
+  LBM_CUDA(cudaMemsetAsync(c->bad, 0, sizeof(int), c->stream));
+  lbm::launch_validate(d, src[0], src[1], src[2], src[3], c->bad, c->stream);
+  int bad = 0;
+  LBM_CUDA(cudaMemcpyAsync(&bad, c->bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(cudaStreamSynchronize(c->stream));
+  if (bad) return LBM_ERR_INVALID_ARG;
+  LBM_CUDA(cudaMemcpyAsync((float*)d.phi, src[0], n * sizeof(float), cudaMemcpyDeviceToDevice,
+                           c->stream));
+  LBM_CUDA(cudaMemcpyAsync((float*)d.K, src[1], n * sizeof(float), cudaMemcpyDeviceToDevice,
+                           c->stream));
+  LBM_CUDA(cudaMemcpyAsync(d.fl, src[3], n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
   if (wall_T_left) {
     LBM_TRY(copy_in(c, (float*)d.wallTl, wall_T_left, (size_t)c->p.ny, device_ptrs));
   } else {
@@ -416,7 +426,7 @@ int lbm_set_fields(lbm_ctx* c, const float* phi, const float* K, const float* T0
                              cudaMemcpyHostToDevice, c->stream));
     LBM_CUDA(cudaStreamSynchronize(c->stream));
   }
-  lbm::launch_init(d, c->tmp, c->stream);
+  lbm::launch_init(d, src[2], c->stream);
   LBM_CUDA(cudaGetLastError());
   LBM_TRY(reset_lists(c));
   c->steps = 0;
@@ -448,18 +458,18 @@ static bool capture_streams(lbm_ctx* c) {
   return true;
 }
 
-// Record `steps` (even) steps starting at parity 0 on c->cap, which is being
+// Record `steps` steps starting at parity `start` on c->cap, which is being
 // captured (alone, or as one branch of a batch capture); returns the number of
 // kernels.  The fused pass of step k+1 is split: its tiles more than one tile
 // away from step k's listed tiles run on a second stream concurrently with step
 // k's enthalpy solve and commit (which touch only nodes within eight nodes of a
 // listed tile); the tiles near the front run after the commit.  Everything
 // forked onto the second stream joins back before the last kernel.
-static int capture_body(lbm_ctx* c, int steps, float* keep_base = nullptr,
+static int capture_body(lbm_ctx* c, int steps, int start = 0, float* keep_base = nullptr,
                         unsigned* keep_ctr = nullptr, double* nu_acc = nullptr) {
   int nl = 0;
   for (int k = 0; k < steps; ++k) {
-    const int par = k & 1;
+    const int par = (start + k) & 1;
     if (k == 0) {
       lbm::launch_fused(c->d, c->tma(), par, 0, c->cap);
     } else {
@@ -499,16 +509,16 @@ static cudaGraphExec_t instantiate(cudaGraph_t g) {
   return ex;
 }
 
-// A graph of `steps` (even) steps starting at parity 0, replayed on the
+// A graph of `steps` steps starting at parity `start`, replayed on the
 // context stream.
-static cudaGraphExec_t capture(lbm_ctx* c, int steps, int* launches) {
+static cudaGraphExec_t capture(lbm_ctx* c, int steps, int start, int* launches) {
   if (!capture_streams(c)) return nullptr;
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
-  const int nl = capture_body(c, steps);
+  const int nl = capture_body(c, steps, start);
   if (cudaStreamEndCapture(c->cap, &g) != cudaSuccess || !g) {
     cudaGetLastError();
     return nullptr;
@@ -519,9 +529,29 @@ static cudaGraphExec_t capture(lbm_ctx* c, int steps, int* launches) {
 
 // Forget the captured graphs (after a change of kernel configuration).
 static void drop_graphs(lbm_ctx* c) {
-  if (c->g_long) cudaGraphExecDestroy(c->g_long);
-  if (c->g_pair) cudaGraphExecDestroy(c->g_pair);
-  c->g_long = c->g_pair = nullptr;
+  for (int q = 0; q < 2; ++q)
+    for (int k = 0; k <= GRAPH_MAX; ++k) {
+      if (c->gx[q][k]) cudaGraphExecDestroy(c->gx[q][k]);
+      c->gx[q][k] = nullptr;
+    }
+}
+
+// The graph of `len` (2..GRAPH_MAX) steps from parity `par`, captured on first
+// use; nullptr if capture fails (the caller then steps kernel by kernel).
+static cudaGraphExec_t graph_for(lbm_ctx* c, int par, int len) {
+  if (!c->gx[par][len]) c->gx[par][len] = capture(c, len, par, &c->gnl[par][len]);
+  return c->gx[par][len];
+}
+
+// Length of the next chunk lbm_step runs from `left` steps: at most GRAPH_MAX,
+// and ending where the next NaN/Inf sentinel is due.
+static int chunk_len(const lbm_ctx* c, int64_t left, int64_t since_check) {
+  int64_t len = left < GRAPH_MAX ? left : GRAPH_MAX;
+  if (c->p.check_every > 0) {
+    const int64_t due = c->p.check_every - since_check;
+    if (due < len) len = due;
+  }
+  return (int)(len < 1 ? 1 : len);
 }
 
 static const int EV_PER_STEP = 5;
@@ -554,28 +584,47 @@ int lbm_step(lbm_ctx* c, int64_t nsteps) {
   if (!c || nsteps < 0) return LBM_ERR_INVALID_ARG;
   // timed runs launch kernel by kernel so events can bracket each kernel
   const bool graphs = !c->timing && !c->graphs_off;
-  while (nsteps > 0 && (c->parity != 0 || !graphs || nsteps < 2)) {
-    LBM_TRY(step_direct(c));
-    --nsteps;
-  }
-  if (nsteps >= GRAPH_STEPS && !c->g_long) c->g_long = capture(c, GRAPH_STEPS, &c->nl_long);
-  if (nsteps >= 2 && !c->g_pair) c->g_pair = capture(c, 2, &c->nl_pair);
-  while (nsteps >= GRAPH_STEPS && c->g_long) {
-    LBM_CUDA(cudaGraphLaunch(c->g_long, c->stream));
-    nsteps -= GRAPH_STEPS;
-    c->steps += GRAPH_STEPS;
-    c->launches += c->nl_long;
-  }
-  while (nsteps >= 2 && c->g_pair) {
-    LBM_CUDA(cudaGraphLaunch(c->g_pair, c->stream));
-    nsteps -= 2;
-    c->steps += 2;
-    c->launches += c->nl_pair;
-  }
   while (nsteps > 0) {
-    LBM_TRY(step_direct(c));
-    --nsteps;
+    const int len = chunk_len(c, nsteps, c->since_check);
+    cudaGraphExec_t g = (graphs && len >= 2) ? graph_for(c, c->parity, len) : nullptr;
+    if (g) {
+      LBM_CUDA(cudaGraphLaunch(g, c->stream));
+      c->launches += c->gnl[c->parity][len];
+      c->steps += len;
+      c->parity ^= len & 1;
+    } else {
+      for (int k = 0; k < len; ++k) LBM_TRY(step_direct(c));
+    }
+    nsteps -= len;
+    c->since_check += len;
+    if (c->p.check_every > 0 && c->since_check >= c->p.check_every) {
+      lbm::launch_nonfinite(c->d, c->nred, c->stream);
+      c->launches += 1;
+      c->since_check = 0;
+    }
   }
+  return cuda_err(cudaGetLastError());
+}
+
+int lbm_prepare(lbm_ctx* c, int64_t nsteps) {
+  if (!c || nsteps < 0) return LBM_ERR_INVALID_ARG;
+  if (c->timing || c->graphs_off) return LBM_OK;
+  int par = c->parity;
+  int64_t since = c->since_check;
+  while (nsteps > 0) {
+    const int len = chunk_len(c, nsteps, since);
+    if (len >= 2 && !graph_for(c, par, len)) return LBM_ERR_CUDA;
+    par ^= len & 1;
+    nsteps -= len;
+    since += len;
+    if (c->p.check_every > 0 && since >= c->p.check_every) since = 0;
+  }
+  return LBM_OK;
+}
+
+int lbm_check_wait(lbm_ctx* c, int64_t limit_ns) {
+  if (!c || limit_ns < 1000 || limit_ns > 1000000000LL) return LBM_ERR_INVALID_ARG;
+  lbm::launch_wait_probe(c->d, (long long)limit_ns, c->stream);
   return cuda_err(cudaGetLastError());
 }
 
@@ -712,7 +761,7 @@ static int batch_capture(lbm_batch* b) {
   for (size_t i = 0; i < b->ctx.size(); ++i) {
     lbm_ctx* c = b->ctx[i];
     cudaStreamWaitEvent(c->cap, b->ev_done, 0);
-    b->nl[i] = capture_body(c, LBM_BATCH_STEPS);
+    b->nl[i] = capture_body(c, LBM_BATCH_STEPS, 0);
     cudaEventRecord(b->ev_out[i], c->cap);
   }
   for (size_t i = 0; i < b->ctx.size(); ++i) cudaStreamWaitEvent(b->cap, b->ev_out[i], 0);
@@ -763,7 +812,12 @@ int lbm_status(lbm_ctx* c) {
   int st[8];
   LBM_CUDA(cudaMemcpyAsync(st, c->d.stats, sizeof st, cudaMemcpyDeviceToHost, c->stream));
   LBM_CUDA(cudaStreamSynchronize(c->stream));
-  if (st[4]) return LBM_ERR_TIMEOUT;
+  if (st[5]) return LBM_ERR_NONFINITE;   // kept until new fields or a new state are loaded
+  if (st[4]) {
+    LBM_CUDA(cudaMemsetAsync(c->d.stats + 4, 0, sizeof(int), c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    return LBM_ERR_TIMEOUT;
+  }
   if (st[0]) {
     LBM_CUDA(cudaMemsetAsync(c->d.stats, 0, sizeof(int), c->stream));
     LBM_CUDA(cudaStreamSynchronize(c->stream));
@@ -933,7 +987,7 @@ static cudaGraphExec_t capture_keep(lbm_ctx* c, int steps, float* base, unsigned
     cudaGetLastError();
     return nullptr;
   }
-  capture_body(c, steps, base, ctr, nu_acc);
+  capture_body(c, steps, 0, base, ctr, nu_acc);
   if (cudaStreamEndCapture(c->cap, &g) != cudaSuccess || !g) {
     cudaGetLastError();
     return nullptr;
@@ -945,7 +999,7 @@ static cudaGraphExec_t capture_keep(lbm_ctx* c, int steps, float* base, unsigned
 // around them), each followed by the hooks of capture_keep; graphs kept in
 // `cache` for later calls with the same hooks.
 struct HookGraphs {
-  cudaGraphExec_t g[2] = {nullptr, nullptr};   // GRAPH_STEPS and 2 steps
+  cudaGraphExec_t g[2] = {nullptr, nullptr};   // GRAPH_MAX and 2 steps
   ~HookGraphs() {
     for (cudaGraphExec_t x : g)
       if (x) cudaGraphExecDestroy(x);
@@ -962,7 +1016,7 @@ static int step_hooked(lbm_ctx* c, int64_t steps, float* base, unsigned* ctr, do
     return LBM_OK;
   };
   while (steps > 0 && (c->parity != 0 || c->graphs_off || steps < 2)) LBM_TRY(direct());
-  const int lens[2] = {GRAPH_STEPS, 2};
+  const int lens[2] = {GRAPH_MAX, 2};
   for (int k = 0; k < 2; ++k) {
     if (steps < lens[k]) continue;
     if (!cache.g[k]) cache.g[k] = capture_keep(c, lens[k], base, ctr, nu_acc);

@@ -236,6 +236,20 @@ __global__ void validate_kernel(Dev d, const float* phi, const float* K, const f
   if (!ok) atomicExch(bad, 1);
 }
 
+// Sentinel: every population and f_l of every node, flag stats[5] on the first
+// value that is not finite (NaN or Inf).
+__global__ void nonfinite_kernel(Dev d) {
+  bool bad = false;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < d.n;
+       s += (long long)gridDim.x * blockDim.x) {
+    bool ok = isfinite(d.fl[s]);
+    for (int i = 0; i < 9; ++i) ok = ok && isfinite(ld_pop(d, d.f, i * d.n + s));
+    for (int i = 0; i < 5; ++i) ok = ok && isfinite(ld_pop(d, d.g, i * d.n + s));
+    bad = bad || !ok;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(&d.stats[5], 1);
+}
+
 static unsigned grid1(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
 void launch_init(const Dev& d, const float* T0, cudaStream_t s) {
@@ -262,6 +276,9 @@ void launch_get_state(const Dev& d, int layout, float* f, float* g, cudaStream_t
 }
 void launch_set_state(const Dev& d, const float* f, const float* g, cudaStream_t s) {
   set_state_kernel<<<grid1(d.n, 256), 256, 0, s>>>(d, f, g);
+}
+void launch_nonfinite(const Dev& d, int nblocks, cudaStream_t s) {
+  nonfinite_kernel<<<nblocks, 256, 0, s>>>(d);
 }
 void launch_validate(const Dev& d, const float* phi, const float* K, const float* T0,
                      const float* fl0, int* bad, cudaStream_t s) {

@@ -503,8 +503,10 @@ __device__ __forceinline__ long long global_ns() {
   return t;
 }
 
-// wait for phase `parity` of an mbarrier, giving up after TMA_WAIT_NS; false on timeout
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+// wait for phase `parity` of an mbarrier, giving up after limit_ns (and after
+// 2^24 polls whatever the clock says); false on timeout
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity,
+                                          long long limit_ns = TMA_WAIT_NS) {
   long long t0 = 0;
   for (int it = 0;; ++it) {
     unsigned done;
@@ -516,7 +518,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
         : "memory");
     if (done) return true;
     if (it == 0) t0 = global_ns();
-    else if (global_ns() - t0 > TMA_WAIT_NS || it > (1 << 24)) return false;
+    else if (global_ns() - t0 > limit_ns || it > (1 << 24)) return false;
   }
 }
 

@@ -92,7 +92,8 @@ struct Dev {
                              // some f_l changed, bit 2 some node's flow activity changed
   float2* scr;               // per node of solved tiles: (f_l(n), f_l(n+1))
   int* stats;                // [0] inner cap hit, [1] tiles solved, [2] max sweeps,
-                             // [3] last tile that hit the cap, [4] a bulk copy timed out
+                             // [3] last tile that hit the cap, [4] a bounded wait gave up,
+                             // [5] the sentinel found a non-finite value
 };
 
 // Tensor maps of the TMA-staged fused kernel (passed as a __grid_constant__
@@ -316,6 +317,11 @@ void launch_reduce(const Dev& d, int parity, double* partials, double* out, int 
 int reduce_blocks(const Dev& d);
 void launch_get_state(const Dev& d, int parity, float* f, float* g, cudaStream_t s);
 void launch_set_state(const Dev& d, const float* f, const float* g, cudaStream_t s);
+// NaN/Inf sentinel over the whole state (sets stats[5])
+void launch_nonfinite(const Dev& d, int nblocks, cudaStream_t s);
+// one CTA waiting, with a limit of limit_ns, on an mbarrier nothing completes
+// (sets stats[4] when the wait gives up, as a timed-out bulk copy does)
+void launch_wait_probe(const Dev& d, long long limit_ns, cudaStream_t s);
 void launch_validate(const Dev& d, const float* phi, const float* K, const float* T0,
                      const float* fl0, int* bad, cudaStream_t s);
 

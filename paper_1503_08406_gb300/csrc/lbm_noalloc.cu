@@ -2,21 +2,24 @@
 // that cannot allocate device memory.
 //
 // Who needs it: code that holds a checkpoint of the lattice (the natural-layout
-// arrays lbm_get_state writes) in device memory it already owns, and wants the
-// conservation sums without creating a context, which allocates a workspace.
-// Typical cases are a caller recording work into a CUDA graph (cudaMalloc is
-// not allowed while a stream is being captured), a framework whose allocator
-// owns all device memory and forbids side allocations, and monitoring code that
-// must not perturb a tight memory budget.
+// FP32 arrays lbm_get_state writes, whatever the context's population storage)
+// in device memory it already owns, and wants the conservation sums without
+// creating a context, which allocates a workspace.  Typical cases are a
+// framework whose caching allocator owns all device memory and forbids side
+// allocations, and monitoring code that runs inside a fixed memory budget and
+// must not take device memory from the job it watches.
+//
+// The call is synchronous: it queues two kernels on the caller's stream, copies
+// the four sums to host memory and synchronises that stream before returning.
 //
 // Scratch lives in a file-scope __device__ array (one FP64 partial per lattice
 // row and quantity), so the call allocates nothing.  Every GPU that loads the
 // library holds it until the process exits.  Its device address is looked up
 // with cudaGetSymbolAddress the first time the function runs on a device, with
-// that device current; that first call therefore must not happen while a stream
-// is being captured.  All calls share the array: every element a call reads it
-// writes first in the same call, but two calls whose kernels overlap on the GPU
-// (different streams, no ordering) race on it and may return wrong sums.
+// that device current; make that first call before any stream capture.  All
+// calls share the array: every element a call reads it writes first in the same
+// call, but two calls whose kernels overlap on the GPU (different streams, no
+// ordering) race on it and may return wrong sums.
 #include <math.h>
 #include <mutex>
 #include <string.h>

@@ -25,6 +25,7 @@ LBM_OK = 0
 ERRORS = {
     -1: "LBM_ERR_INVALID_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_NONFINITE",
     -4: "LBM_ERR_NOT_CONVERGED", -5: "LBM_ERR_OOM", -6: "LBM_ERR_NO_DEVICE",
+    -7: "LBM_ERR_TIMEOUT",
 }
 BC = {"periodic": 0, "dirichlet": 1, "adiabatic": 2}
 
@@ -55,6 +56,7 @@ class lbm_params(ctypes.Structure):
         ("kernel_variant", ctypes.c_int32),
         ("storage", ctypes.c_int32),
         ("alpha_ratio", ctypes.c_double),
+        ("check_every", ctypes.c_int32),
     ]
 
 
@@ -64,6 +66,7 @@ PARAM_DEFAULTS = dict(
     T_ref=0.0, T_s=0.0, T_l=0.0, varpi=-2.0, rho0=1.0, tau_nu=-1.0, tau_T=-1.0, g_beta=-1.0,
     s_e=0.0, s_eps=0.0, s_q=0.0, zeta_e=0.0, zeta_nu=0.0, f_act=1e-3,
     max_inner_iters=1000, inner_tol=1e-6, screen_tol=0.0, kernel_variant=0, storage=0, alpha_ratio=0.0,
+    check_every=0,
 )
 
 
@@ -122,6 +125,8 @@ def load():
         lib.lbm_derived.argtypes = [_VP, _DP]
         lib.lbm_set_fields.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int]
         lib.lbm_step.argtypes = [_VP, ctypes.c_int64]
+        lib.lbm_prepare.argtypes = [_VP, ctypes.c_int64]
+        lib.lbm_check_wait.argtypes = [_VP, ctypes.c_int64]
         lib.lbm_status.argtypes = [_VP]
         lib.lbm_steps_done.argtypes = [_VP]
         lib.lbm_steps_done.restype = ctypes.c_int64
@@ -263,8 +268,17 @@ class Lattice:
     def step(self, nsteps: int = 1):
         lbm_step(self._h, nsteps)
 
+    def prepare(self, nsteps: int):
+        """Capture the CUDA graphs step(nsteps) would use now, without stepping."""
+        _check(self.lib.lbm_prepare(self._h, int(nsteps)), "lbm_prepare")
+
     def status(self) -> int:
         return lbm_status(self._h)
+
+    def check_wait(self, limit_ns: int):
+        """Queue the bounded-wait self-check (lbm_check_wait): a wait that must
+        give up after limit_ns, after which status() reports LBM_ERR_TIMEOUT."""
+        _check(self.lib.lbm_check_wait(self._h, int(limit_ns)), "lbm_check_wait")
 
     def steps_done(self) -> int:
         return int(self.lib.lbm_steps_done(self._h))

@@ -62,7 +62,7 @@ CASES = {
     "melted_cavity_100": (lambda: W.melted_cavity(100), 57, 1),
     # no flow lattice, Dirichlet and adiabatic walls, a moving solidification front
     "corner_100": (lambda: W.corner_solidification(100), 41, 1),
-    # graph path: 2 x 32-step graphs with far/near split passes, then single steps
+    # graph path: a 64-step graph with far/near split passes, then a 6-step graph
     "bench_cavity_256": (lambda: W.bench_cavity(256, melted=0.5), 70, 1),
     # one step per call: only the direct path, both parities
     "melted_cavity_64_direct": (lambda: W.melted_cavity(64), 9, 9),
