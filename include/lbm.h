@@ -229,24 +229,29 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
                 int device_ptrs);
 
 /* Adjoint of the coupled step (flow lattice on).  Runs nsteps steps forward
- * from the context's current state, keeping every state (f, g and f_l: 60
- * bytes per node and step; LBM_ERR_OOM when that exceeds half the free device
- * memory), and returns the objective J (LBM_OBJ_MELT or LBM_OBJ_NUSSELT, as
- * for lbm_adjoint) with its gradients with respect to the porosity field
- * (d_phi, nx*ny), the logarithm of the permeability field (d_lnK, nx*ny) and
- * the left wall's temperature profile (d_wall_T_left, ny): the discrete
- * adjoint of the flow collision with the Darcy-Forchheimer force and
- * buoyancy (Eq. (4)-(6), (16)-(28)), of streaming with bounce-back (the flow
- * mask f_l(n) >= f_act held fixed), of the thermal step with the velocity
- * (Eq. (34)-(36), the wall extrapolation of Sec. 4) and of the enthalpy fixed
- * point (Eq. (38)-(42)).  Covers: FP32 storage, one thermal diffusivity, a
+ * from the context's current state and returns the objective J (LBM_OBJ_MELT
+ * or LBM_OBJ_NUSSELT, as for lbm_adjoint) with its gradients with respect to
+ * the porosity field (d_phi, nx*ny), the logarithm of the permeability field
+ * (d_lnK, nx*ny) and the left wall's temperature profile (d_wall_T_left, ny):
+ * the discrete adjoint of the flow collision with the Darcy-Forchheimer force
+ * and buoyancy (Eq. (4)-(6), (16)-(28)), of streaming with bounce-back (the
+ * flow mask f_l(n) >= f_act held fixed), of the thermal step with the
+ * velocity (Eq. (34)-(36), the wall extrapolation of Sec. 4) and of the
+ * enthalpy fixed point (Eq. (38)-(42)).  The reverse sweep needs the state of
+ * every step (f, g and f_l: 60 bytes per node).  checkpoint_every = 0: every
+ * state kept when that takes at most half the free device memory, else as
+ * for sqrt(nsteps); checkpoint_every = K > 0: the whole state kept every K
+ * steps, and each segment recomputed from its checkpoint and reversed from
+ * one CUDA graph replay (the forward run replays graphs too).  All choices
+ * give the same result bit for bit.  LBM_ERR_OOM when the kept states would
+ * exceed the free memory.  Covers: FP32 storage, one thermal diffusivity, a
  * Dirichlet left wall (walls left and right, nx >= 5); LBM_ERR_INVALID_ARG
  * otherwise.  The context ends where the forward run left it.  Allocates its
  * buffers with cudaMalloc and synchronises.  device_ptrs: the three gradient
  * arrays are device (1) or host (0) pointers. */
-int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t mu_sweeps,
-                        float* d_phi, float* d_lnK, float* d_wall_T_left, double* J,
-                        int device_ptrs);
+int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_every,
+                        int32_t mu_sweeps, float* d_phi, float* d_lnK, float* d_wall_T_left,
+                        double* J, int device_ptrs);
 
 /* Batches.  A batch advances several contexts together: each
  * lbm_batch_step replays one CUDA graph holding LBM_BATCH_STEPS steps of every

@@ -1,7 +1,27 @@
 """torch.autograd.Functions for objectives of a run, their gradients from the
 CUDA adjoints (lbm_adjoint for the conduction step, lbm_adjoint_coupled with
-the flow lattice on)."""
+the flow lattice on).
+
+Inputs that are CUDA tensors go to the library as device pointers, and the
+gradients come back as CUDA tensors written by the library: nothing of the
+run passes through host memory.  Host tensors take the host-pointer path.
+"""
 import torch
+
+
+def _on_device(*ts):
+    return all(isinstance(t, torch.Tensor) and t.is_cuda for t in ts)
+
+
+def _field(t):
+    """A field for Lattice.set_fields: the tensor itself when it lives on the
+    GPU (the binding passes its device pointer), else a host array."""
+    t = t.detach()
+    return t if t.is_cuda else t.cpu().numpy()
+
+
+def _as(t, like):
+    return torch.as_tensor(t, device=like.device)
 
 
 class MeltedFraction(torch.autograd.Function):
@@ -14,11 +34,10 @@ class MeltedFraction(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, phi, wall_T_left, lattice, K, T0, fl0, nsteps, checkpoint_every=0):
-        lattice.set_fields(phi.detach().cpu().numpy(), K, T0, fl0,
-                           wall_T_left.detach().cpu().numpy())
-        J, dphi, dtw = lattice.adjoint_melt(int(nsteps), int(checkpoint_every))
-        ctx.save_for_backward(torch.as_tensor(dphi, device=phi.device),
-                              torch.as_tensor(dtw, device=wall_T_left.device))
+        dev = _on_device(phi, wall_T_left)
+        lattice.set_fields(_field(phi), K, T0, fl0, _field(wall_T_left))
+        J, dphi, dtw = lattice.adjoint(int(nsteps), "melt", int(checkpoint_every), device=dev)
+        ctx.save_for_backward(_as(dphi, phi), _as(dtw, wall_T_left))
         return torch.tensor(J, dtype=torch.float64, device=phi.device)
 
     @staticmethod
@@ -39,11 +58,10 @@ class HotWallNusselt(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, phi, wall_T_left, lattice, K, T0, fl0, nsteps, checkpoint_every=0):
-        lattice.set_fields(phi.detach().cpu().numpy(), K, T0, fl0,
-                           wall_T_left.detach().cpu().numpy())
-        J, dphi, dtw = lattice.adjoint(int(nsteps), "nusselt", int(checkpoint_every))
-        ctx.save_for_backward(torch.as_tensor(dphi, device=phi.device),
-                              torch.as_tensor(dtw, device=wall_T_left.device))
+        dev = _on_device(phi, wall_T_left)
+        lattice.set_fields(_field(phi), K, T0, fl0, _field(wall_T_left))
+        J, dphi, dtw = lattice.adjoint(int(nsteps), "nusselt", int(checkpoint_every), device=dev)
+        ctx.save_for_backward(_as(dphi, phi), _as(dtw, wall_T_left))
         return torch.tensor(J, dtype=torch.float64, device=phi.device)
 
     @staticmethod
@@ -65,18 +83,18 @@ class CoupledObjective(torch.autograd.Function):
     """
 
     @staticmethod
-    def forward(ctx, phi, lnK, wall_T_left, lattice, T0, fl0, nsteps, objective="melt"):
-        K = torch.exp(lnK.detach()).cpu().numpy()
-        lattice.set_fields(phi.detach().cpu().numpy(), K, T0, fl0,
-                           wall_T_left.detach().cpu().numpy())
-        J, dphi, dlnK, dtw = lattice.adjoint_coupled(int(nsteps), objective)
-        ctx.save_for_backward(torch.as_tensor(dphi, device=phi.device),
-                              torch.as_tensor(dlnK, device=lnK.device),
-                              torch.as_tensor(dtw, device=wall_T_left.device))
+    def forward(ctx, phi, lnK, wall_T_left, lattice, T0, fl0, nsteps, objective="melt",
+                checkpoint_every=0):
+        dev = _on_device(phi, lnK, wall_T_left)
+        K = torch.exp(lnK.detach())   # the permeability the lattice takes
+        lattice.set_fields(_field(phi), _field(K), T0, fl0, _field(wall_T_left))
+        J, dphi, dlnK, dtw = lattice.adjoint_coupled(int(nsteps), objective,
+                                                     int(checkpoint_every), device=dev)
+        ctx.save_for_backward(_as(dphi, phi), _as(dlnK, lnK), _as(dtw, wall_T_left))
         return torch.tensor(J, dtype=torch.float64, device=phi.device)
 
     @staticmethod
     def backward(ctx, grad_J):
         dphi, dlnK, dtw = ctx.saved_tensors
         g = grad_J.to(dphi.dtype)
-        return g * dphi, g * dlnK, g * dtw, None, None, None, None, None
+        return g * dphi, g * dlnK, g * dtw, None, None, None, None, None, None

@@ -350,6 +350,19 @@ void adj_seed(const Dev& d, float* lamf, float* lamg, float* a, bool melt, NuSrc
   adj_a_kernel<<<blocks(d.n), AB, 0, s>>>(d, a);
 }
 
+__global__ void adj_mul_kernel(long long n, float* v, const float* w) {
+  const long long s = blockIdx.x * (long long)AB + threadIdx.x;
+  if (s < n) v[s] *= w[s];
+}
+
+void adj_mul(long long n, float* v, const float* w, cudaStream_t s) {
+  adj_mul_kernel<<<(unsigned)((n + AB - 1) / AB), AB, 0, s>>>(n, v, w);
+}
+
+void adj_a(const Dev& d, float* a, cudaStream_t s) {
+  adj_a_kernel<<<blocks(d.n), AB, 0, s>>>(d, a);
+}
+
 void adj_scale(long long n, float* v, float k, cudaStream_t s) {
   adj_scale_kernel<<<(unsigned)((n + AB - 1) / AB), AB, 0, s>>>(n, v, k);
 }

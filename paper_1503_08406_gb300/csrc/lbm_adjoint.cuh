@@ -39,6 +39,10 @@ void adj_seed(const Dev& d, float* lamf, float* lamg, float* a, bool melt, NuSrc
               cudaStream_t s);
 // v[0..n) *= k
 void adj_scale(long long n, float* v, float k, cudaStream_t s);
+// v[0..n) *= w[0..n)
+void adj_mul(long long n, float* v, const float* w, cudaStream_t s);
+// a = phi dT / (sigma St)
+void adj_a(const Dev& d, float* a, cudaStream_t s);
 // J into out[0]; out holds 129 doubles (the rest: partial sums)
 void adj_objective(const Dev& d, const float* fl, double* out, cudaStream_t s);
 // the band (non-wall nodes with 0 < f < 1), appended at list[*count]

@@ -465,8 +465,38 @@ static bool capture_streams(lbm_ctx* c) {
 // k's enthalpy solve and commit (which touch only nodes within eight nodes of a
 // listed tile); the tiles near the front run after the commit.  Everything
 // forked onto the second stream joins back before the last kernel.
-static int capture_body(lbm_ctx* c, int steps, int start = 0, float* keep_base = nullptr,
-                        unsigned* keep_ctr = nullptr, double* nu_acc = nullptr) {
+// Work an adjoint's forward run adds after every step (all optional): f_l
+// into fl_base + fl_ctr[0] n, the whole state into st_base + st_ctr[0] 15 n
+// (each counter then advances, so a graph serves every replay), and the
+// left-wall Nusselt number added to nu_acc[0].
+struct Hooks {
+  float* fl_base = nullptr;
+  unsigned* fl_ctr = nullptr;
+  float* st_base = nullptr;
+  unsigned* st_ctr = nullptr;
+  double* nu_acc = nullptr;
+  bool any() const { return fl_base || st_base || nu_acc; }
+};
+
+static int launch_hooks(lbm_ctx* c, const Hooks* h, int layout, cudaStream_t s) {
+  if (!h) return 0;
+  int nl = 0;
+  if (h->fl_base) {
+    lbm::adj_save(c->d, h->fl_base, h->fl_ctr, s);   // f_l after the step
+    ++nl;
+  }
+  if (h->st_base) {
+    lbm::launch_keep_state(c->d, layout, h->st_base, h->st_ctr, s);   // the state after it
+    ++nl;
+  }
+  if (h->nu_acc) {
+    lbm::launch_wall_nusselt(c->d, layout, h->nu_acc, s);   // Nu after the step
+    ++nl;
+  }
+  return nl;
+}
+
+static int capture_body(lbm_ctx* c, int steps, int start = 0, const Hooks* hooks = nullptr) {
   int nl = 0;
   for (int k = 0; k < steps; ++k) {
     const int par = (start + k) & 1;
@@ -487,14 +517,7 @@ static int capture_body(lbm_ctx* c, int steps, int start = 0, float* keep_base =
     lbm::launch_enthalpy_solve(c->d, par, c->cap);
     lbm::launch_enthalpy_commit(c->d, par, c->cap);
     nl += 2;
-    if (keep_base) {
-      lbm::adj_save(c->d, keep_base, keep_ctr, c->cap);   // f_l after the step
-      nl += 1;
-    }
-    if (nu_acc) {
-      lbm::launch_wall_nusselt(c->d, 1 - par, nu_acc, c->cap);   // Nu after the step
-      nl += 1;
-    }
+    nl += launch_hooks(c, hooks, 1 - par, c->cap);
   }
   return nl;
 }
@@ -976,18 +999,16 @@ struct DevMem {
 
 }  // namespace
 
-// A graph of `steps` (even) steps from parity 0 like capture(), each step
-// followed by lbm::adj_save of f_l (base non-null) and the Nusselt sum (nu_acc
-// non-null).
-static cudaGraphExec_t capture_keep(lbm_ctx* c, int steps, float* base, unsigned* ctr,
-                                    double* nu_acc) {
+// A graph of `steps` steps from parity 0 like capture(), each step followed
+// by the hooks.
+static cudaGraphExec_t capture_keep(lbm_ctx* c, int steps, const Hooks& h) {
   if (!capture_streams(c)) return nullptr;
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
-  capture_body(c, steps, 0, base, ctr, nu_acc);
+  capture_body(c, steps, 0, &h);
   if (cudaStreamEndCapture(c->cap, &g) != cudaSuccess || !g) {
     cudaGetLastError();
     return nullptr;
@@ -996,8 +1017,8 @@ static cudaGraphExec_t capture_keep(lbm_ctx* c, int steps, float* base, unsigned
 }
 
 // Steps `steps` steps like lbm_step (graphs from parity 0, single steps
-// around them), each followed by the hooks of capture_keep; graphs kept in
-// `cache` for later calls with the same hooks.
+// around them), each followed by the hooks; graphs kept in `cache` for later
+// calls with the same hooks.
 struct HookGraphs {
   cudaGraphExec_t g[2] = {nullptr, nullptr};   // GRAPH_MAX and 2 steps
   ~HookGraphs() {
@@ -1006,12 +1027,10 @@ struct HookGraphs {
   }
 };
 
-static int step_hooked(lbm_ctx* c, int64_t steps, float* base, unsigned* ctr, double* nu_acc,
-                       HookGraphs& cache) {
+static int step_hooked(lbm_ctx* c, int64_t steps, const Hooks& h, HookGraphs& cache) {
   auto direct = [&]() -> int {
     LBM_TRY(step_direct(c));
-    if (base) lbm::adj_save(c->d, base, ctr, c->stream);
-    if (nu_acc) lbm::launch_wall_nusselt(c->d, c->parity, nu_acc, c->stream);
+    launch_hooks(c, &h, c->parity, c->stream);
     --steps;
     return LBM_OK;
   };
@@ -1019,7 +1038,7 @@ static int step_hooked(lbm_ctx* c, int64_t steps, float* base, unsigned* ctr, do
   const int lens[2] = {GRAPH_MAX, 2};
   for (int k = 0; k < 2; ++k) {
     if (steps < lens[k]) continue;
-    if (!cache.g[k]) cache.g[k] = capture_keep(c, lens[k], base, ctr, nu_acc);
+    if (!cache.g[k]) cache.g[k] = capture_keep(c, lens[k], h);
     if (!cache.g[k]) break;
     while (steps >= lens[k]) {
       LBM_CUDA(cudaGraphLaunch(cache.g[k], c->stream));
@@ -1138,16 +1157,22 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
     // forward, f_l after every step into flS (its start at index 0)
     LBM_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), c->stream));
     lbm::adj_save(c->d, flS, ctr, c->stream);
-    LBM_TRY(step_hooked(c, nsteps, flS, ctr, acc, fwd_graphs));
+    Hooks h;
+    h.fl_base = flS;
+    h.fl_ctr = ctr;
+    h.nu_acc = acc;
+    LBM_TRY(step_hooked(c, nsteps, h, fwd_graphs));
   } else {
     // forward, keeping the whole state every K steps
     LBM_TRY(save(cps));
+    Hooks h;
+    h.nu_acc = acc;
     for (int64_t j = 1; j < ncp; ++j) {
-      LBM_TRY(step_hooked(c, K, nullptr, nullptr, acc, fwd_graphs));
+      LBM_TRY(step_hooked(c, K, h, fwd_graphs));
       LBM_TRY(save(cps + (size_t)j * st));
     }
     const int64_t done = (ncp - 1) * K;
-    if (nsteps > done) LBM_TRY(step_hooked(c, nsteps - done, nullptr, nullptr, acc, fwd_graphs));
+    if (nsteps > done) LBM_TRY(step_hooked(c, nsteps - done, h, fwd_graphs));
     LBM_TRY(save(fin));
   }
   const float* fl_end = keep_all ? flS + (size_t)nsteps * n : fin + 5 * n;
@@ -1255,10 +1280,11 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
   return LBM_OK;
 }
 
-int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t mu_sweeps,
-                        float* d_phi, float* d_lnK, float* d_wall_T_left, double* J,
-                        int device_ptrs) {
-  if (!c || nsteps < 1 || mu_sweeps < 0 || !d_phi || !d_lnK || !d_wall_T_left || !J)
+int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_every,
+                        int32_t mu_sweeps, float* d_phi, float* d_lnK, float* d_wall_T_left,
+                        double* J, int device_ptrs) {
+  if (!c || nsteps < 1 || checkpoint_every < 0 || mu_sweeps < 0 || !d_phi || !d_lnK ||
+      !d_wall_T_left || !J)
     return LBM_ERR_INVALID_ARG;
   if (objective != LBM_OBJ_MELT && objective != LBM_OBJ_NUSSELT) return LBM_ERR_INVALID_ARG;
   const lbm_params& p = c->p;
@@ -1270,11 +1296,25 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t mu_sw
   const int sweeps = mu_sweeps > 0 ? mu_sweeps : 64;
   const size_t n = (size_t)d.n, st = 15 * n;   // a kept state: f (9), g (5), f_l
   if (!lbm::adj_init()) return LBM_ERR_CUDA;
+  // Every state kept when that takes at most half the free memory (and no
+  // spacing is asked for); otherwise the whole state every K steps (K =
+  // sqrt(nsteps) by default), each segment recomputed from its checkpoint
+  // and reversed from one CUDA graph replay.
   size_t free_b = 0, total_b = 0;
   LBM_CUDA(cudaMemGetInfo(&free_b, &total_b));
-  if ((double)(nsteps + 1) * st * sizeof(float) > 0.5 * (double)free_b) return LBM_ERR_OOM;
+  const bool keep_all = checkpoint_every == 0 &&
+                        (double)(nsteps + 1) * st * sizeof(float) <= 0.5 * (double)free_b;
+  const int64_t K = keep_all ? nsteps
+                    : checkpoint_every > 0 ? checkpoint_every
+                                           : (int64_t)ceil(sqrt((double)nsteps));
+  const int64_t ncp = keep_all ? 1 : nsteps / K + 1;
+  if (!keep_all && (double)(ncp + K + 2) * st * sizeof(float) > 0.8 * (double)free_b)
+    return LBM_ERR_OOM;
   DevMem mem;
-  float* S = mem.get((size_t)(nsteps + 1) * st);
+  // states of one segment (index m: after its m-th step; all steps when keep_all)
+  float* S = mem.get((size_t)(K + 1) * st);
+  float* cps = keep_all ? nullptr : mem.get((size_t)ncp * st);
+  float* fin = keep_all ? nullptr : mem.get(st);
   float* lf[2] = {mem.get(9 * n), mem.get(9 * n)};
   float* lg[2] = {mem.get(5 * n), mem.get(5 * n)};
   lbm::AdjBuffers b;
@@ -1290,30 +1330,46 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t mu_sw
   int* lists[2] = {reinterpret_cast<int*>(mem.get(n)), reinterpret_cast<int*>(mem.get(n))};
   int* counts = reinterpret_cast<int*>(mem.get(2));
   double* nu_acc = reinterpret_cast<double*>(mem.get(2));
-  if (!S || !lf[0] || !lf[1] || !lg[0] || !lg[1] || !b.a || !b.lamf || !b.rhs || !b.mu0 ||
-      !b.mu1 || !b.lama || !b.lamtw || !b.pos || !lK || !lists[0] || !lists[1] || !counts ||
-      !nu_acc)
+  unsigned* ctr = reinterpret_cast<unsigned*>(mem.get(2));
+  if (!S || (!keep_all && (!cps || !fin)) || !lf[0] || !lf[1] || !lg[0] || !lg[1] || !b.a ||
+      !b.lamf || !b.rhs || !b.mu0 || !b.mu1 || !b.lama || !b.lamtw || !b.pos || !lK ||
+      !lists[0] || !lists[1] || !counts || !nu_acc || !ctr)
     return LBM_ERR_OOM;
   // rows of the Nusselt number (lbm_reduce's): all but horizontal wall rows
   const int y0 = d.wall_b ? 1 : 0, y1 = d.wall_t ? d.ny - 1 : d.ny;
   const double kN = melt ? 0.0 : (double)d.H_over_dT / ((double)(y1 - y0) * (double)nsteps);
-  // forward, every state kept (natural layout, f as deviations)
-  auto keep = [&](int64_t k) -> int {
-    float* dst = S + (size_t)k * st;
-    LBM_TRY(lbm_get_state(c, dst, dst + 9 * n, dst + 14 * n, 1));
-    return LBM_OK;
-  };
+  const int64_t steps0 = c->steps;
+  HookGraphs fwd_graphs;
+  Hooks h;
+  h.nu_acc = melt ? nullptr : nu_acc;
   LBM_CUDA(cudaMemsetAsync(nu_acc, 0, sizeof(double), c->stream));
-  for (int64_t k = 0; k < nsteps; ++k) {
-    LBM_TRY(keep(k));
-    LBM_TRY(step_direct(c));
-    if (!melt) lbm::launch_wall_nusselt(c->d, c->parity, nu_acc, c->stream);
+  auto save = [&](float* dst) -> int {   // the whole state, natural layout
+    lbm::launch_keep_state(c->d, c->parity, dst, nullptr, c->stream);
+    return cuda_err(cudaGetLastError());
+  };
+  if (keep_all) {
+    // forward, every state kept (a device counter picks the slot)
+    LBM_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), c->stream));
+    lbm::launch_keep_state(c->d, c->parity, S, ctr, c->stream);
+    h.st_base = S;
+    h.st_ctr = ctr;
+    LBM_TRY(step_hooked(c, nsteps, h, fwd_graphs));
+  } else {
+    // forward, the whole state every K steps
+    LBM_TRY(save(cps));
+    for (int64_t j = 1; j < ncp; ++j) {
+      LBM_TRY(step_hooked(c, K, h, fwd_graphs));
+      LBM_TRY(save(cps + (size_t)j * st));
+    }
+    const int64_t done = (ncp - 1) * K;
+    if (nsteps > done) LBM_TRY(step_hooked(c, nsteps - done, h, fwd_graphs));
+    LBM_TRY(save(fin));
   }
-  LBM_TRY(keep(nsteps));
   LBM_CUDA(cudaGetLastError());
+  const float* last = keep_all ? S + (size_t)nsteps * st : fin;
   // objective and seeds (host side: small arrays)
   std::vector<float> hfl(n), seedf(n, 0.f), seedg(5 * n, 0.f);
-  LBM_CUDA(cudaMemcpyAsync(hfl.data(), S + (size_t)nsteps * st + 14 * n, n * sizeof(float),
+  LBM_CUDA(cudaMemcpyAsync(hfl.data(), last + 14 * n, n * sizeof(float),
                            cudaMemcpyDeviceToHost, c->stream));
   double accv = 0;
   LBM_CUDA(cudaMemcpyAsync(&accv, nu_acc, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -1352,16 +1408,8 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t mu_sw
   LBM_CUDA(cudaMemsetAsync(lK, 0, n * sizeof(float), c->stream));
   LBM_CUDA(cudaMemsetAsync(b.lamtw, 0, d.ny * sizeof(float), c->stream));
   LBM_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(int), c->stream));
-  {
-    std::vector<float> ha(n);
-    std::vector<float> hphi(n);
-    LBM_CUDA(cudaMemcpy(hphi.data(), d.phi, n * sizeof(float), cudaMemcpyDeviceToHost));
-    for (size_t s = 0; s < n; ++s) ha[s] = hphi[s] * d.lat;
-    LBM_CUDA(cudaMemcpyAsync(b.a, ha.data(), n * sizeof(float), cudaMemcpyHostToDevice,
-                             c->stream));
-    LBM_CUDA(cudaStreamSynchronize(c->stream));
-  }
-  lbm::adj_list(c->d, S + (size_t)nsteps * st + 14 * n, lists[0], counts, c->stream);
+  lbm::adj_a(c->d, b.a, c->stream);
+  lbm::adj_list(c->d, last + 14 * n, lists[0], counts, c->stream);
   // the step's parameters
   lbm::CoupledStep<float> A;
   A.geo = lbm::CoupledGeo{d.nx, d.ny, d.per_x, d.per_y, {d.bc[0], d.bc[1], d.bc[2], d.bc[3]}};
@@ -1402,43 +1450,104 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t mu_sw
   A.lphi = b.lama;
   A.lK = lK;
   A.lTw = b.lamtw;
-  // reverse sweep
+  // reverse sweep: step m of a stretch whose states sit at F (index m - lo)
   int cur = 0;
-  for (int64_t m = nsteps - 1; m >= 0; --m) {
-    const float* s0 = S + (size_t)m * st;
-    const float* s1 = S + (size_t)(m + 1) * st;
-    A.f0 = s0;
-    A.g0 = s0 + 9 * n;
-    A.fl0 = s0 + 14 * n;
-    A.fl1 = s1 + 14 * n;
-    A.lf1 = lf[cur];
-    A.lg1 = lg[cur];
-    A.lf0 = lf[1 - cur];
-    A.lg0 = lg[1 - cur];
-    A.next_list = lists[1 - cur];
-    A.next_count = counts + 1 - cur;
-    b.lamg = lg[cur];
-    lbm::adj_coupled_step(c->d, b, A, lists[cur], counts + cur, counts + 1 - cur, sweeps,
-                          c->stream);
-    LBM_CUDA(cudaGetLastError());
-    cur ^= 1;
+  auto reverse = [&](cudaStream_t sm, const float* F, int64_t lo, int64_t hi) {
+    for (int64_t m = hi - 1; m >= lo; --m) {
+      const float* s0 = F + (size_t)(m - lo) * st;
+      const float* s1 = s0 + st;
+      A.f0 = s0;
+      A.g0 = s0 + 9 * n;
+      A.fl0 = s0 + 14 * n;
+      A.fl1 = s1 + 14 * n;
+      A.lf1 = lf[cur];
+      A.lg1 = lg[cur];
+      A.lf0 = lf[1 - cur];
+      A.lg0 = lg[1 - cur];
+      A.next_list = lists[1 - cur];
+      A.next_count = counts + 1 - cur;
+      b.lamg = lg[cur];
+      lbm::adj_coupled_step(c->d, b, A, lists[cur], counts + cur, counts + 1 - cur, sweeps, sm);
+      cur ^= 1;
+    }
+  };
+  if (keep_all) {
+    reverse(c->stream, S, 0, nsteps);
+  } else {
+    // One segment, its checkpoint first copied to S (index 0): the state set
+    // from it (parity 0, empty work lists), len steps forward kernel by kernel
+    // with the state after each kept at S + m st, then the len reversed steps.
+    // The launches are the same for every whole segment that starts with the
+    // same adjoint buffer, so each (len, buffer) pair is captured once.
+    auto record_segment = [&](cudaStream_t sm, int64_t len) {
+      lbm::launch_set_state(c->d, S, S + 9 * n, sm);
+      cudaMemcpyAsync(c->d.fl, S + 14 * n, n * sizeof(float), cudaMemcpyDeviceToDevice, sm);
+      cudaMemsetAsync(c->d.flags, 0, 2 * sizeof(int) * c->d.ntiles, sm);
+      cudaMemsetAsync(c->d.lcount, 0, 2 * sizeof(int), sm);
+      int par = 0;
+      for (int64_t m = 1; m <= len; ++m) {
+        lbm::launch_fused(c->d, c->tma(), par, 0, sm);
+        lbm::launch_enthalpy_solve(c->d, par, sm);
+        lbm::launch_enthalpy_commit(c->d, par, sm);
+        par ^= 1;
+        lbm::launch_keep_state(c->d, par, S + (size_t)m * st, nullptr, sm);
+      }
+      reverse(sm, S, 0, len);
+    };
+    struct SegGraph {
+      int64_t len;
+      int cur;
+      cudaGraphExec_t ex;
+    };
+    struct SegGraphs {
+      std::vector<SegGraph> v;
+      ~SegGraphs() {
+        for (SegGraph& g : v) cudaGraphExecDestroy(g.ex);
+      }
+    } seg_graphs;
+    const bool can_capture = !c->graphs_off && capture_streams(c);
+    for (int64_t j = ncp - 1; j >= 0; --j) {
+      const int64_t first = j * K;
+      const int64_t len = (j == ncp - 1) ? nsteps - first : K;
+      if (len <= 0) continue;
+      LBM_CUDA(cudaMemcpyAsync(S, cps + (size_t)j * st, st * sizeof(float),
+                               cudaMemcpyDeviceToDevice, c->stream));
+      const int cur0 = cur;
+      cudaGraphExec_t ex = nullptr;
+      for (const SegGraph& g : seg_graphs.v)
+        if (g.len == len && g.cur == cur0) ex = g.ex;
+      if (!ex && can_capture) {
+        cudaGraph_t gr = nullptr;
+        if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+          record_segment(c->cap, len);
+          if (cudaStreamEndCapture(c->cap, &gr) == cudaSuccess && gr) {
+            ex = instantiate(gr);
+            if (ex) seg_graphs.v.push_back({len, cur0, ex});
+          }
+        }
+        cudaGetLastError();
+        cur = cur0;
+      }
+      if (ex) {
+        // the graph was ordered after the copy above by the stream
+        LBM_CUDA(cudaGraphLaunch(ex, c->stream));
+        if (len & 1) cur ^= 1;
+      } else {
+        record_segment(c->stream, len);
+      }
+      LBM_CUDA(cudaGetLastError());
+    }
+    // back to where the forward run ended
+    LBM_TRY(lbm_set_state(c, fin, fin + 9 * n, fin + 14 * n, 1));
+    c->steps = steps0 + nsteps;
   }
-  // d J / d ln K = K d J / d K
-  std::vector<float> hphi(n), hK(n), hlK(n), hlphi(n), hltw(d.ny);
-  LBM_CUDA(cudaMemcpyAsync(hlphi.data(), b.lama, n * sizeof(float), cudaMemcpyDeviceToHost,
-                           c->stream));
-  LBM_CUDA(cudaMemcpyAsync(hlK.data(), lK, n * sizeof(float), cudaMemcpyDeviceToHost,
-                           c->stream));
-  LBM_CUDA(cudaMemcpyAsync(hK.data(), d.K, n * sizeof(float), cudaMemcpyDeviceToHost,
-                           c->stream));
-  LBM_CUDA(cudaMemcpyAsync(hltw.data(), b.lamtw, d.ny * sizeof(float), cudaMemcpyDeviceToHost,
-                           c->stream));
+  // d J / d ln K = K d J / d K, then straight into the caller's arrays
+  lbm::adj_mul((long long)n, lK, d.K, c->stream);
+  const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  LBM_CUDA(cudaMemcpyAsync(d_phi, b.lama, n * sizeof(float), kind, c->stream));
+  LBM_CUDA(cudaMemcpyAsync(d_lnK, lK, n * sizeof(float), kind, c->stream));
+  LBM_CUDA(cudaMemcpyAsync(d_wall_T_left, b.lamtw, d.ny * sizeof(float), kind, c->stream));
   LBM_CUDA(cudaStreamSynchronize(c->stream));
-  for (size_t s = 0; s < n; ++s) hlK[s] *= hK[s];
-  const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
-  LBM_CUDA(cudaMemcpy(d_phi, hlphi.data(), n * sizeof(float), kind));
-  LBM_CUDA(cudaMemcpy(d_lnK, hlK.data(), n * sizeof(float), kind));
-  LBM_CUDA(cudaMemcpy(d_wall_T_left, hltw.data(), d.ny * sizeof(float), kind));
   // the context ends where the forward run left it
   return LBM_OK;
 }

@@ -236,6 +236,40 @@ __global__ void validate_kernel(Dev d, const float* phi, const float* K, const f
   if (!ok) atomicExch(bad, 1);
 }
 
+// The whole state in natural layout (f as deviations, 9 planes; g, 5 planes;
+// f_l) into dst, 15 n floats; with ctr non-null into base + ctr[0] 15 n, after
+// which ctr[0] advances (ctr[1]: 0, scratch), so one captured launch serves
+// every replay of a graph.
+__global__ void keep_state_kernel(Dev d, int layout, float* base, unsigned* ctr) {
+  const long long n = d.n;
+  float* dst = base + (ctr ? (long long)ctr[0] * 15 * n : 0LL);
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n;
+       s += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(s / d.nx), x = (int)(s - (long long)y * d.nx);
+    float fv[9], gv[5];
+    if (is_wall(d, x, y)) {
+      for (int i = 0; i < 9; ++i) fv[i] = ld_f(d, i, s);
+      for (int i = 0; i < 5; ++i) gv[i] = ld_g(d, i, s);
+    } else {
+      gather_f(d, x, y, layout, fv);
+      gather_g(d, x, y, layout, gv);
+    }
+    for (int i = 0; i < 9; ++i) dst[i * n + s] = fv[i];
+    for (int i = 0; i < 5; ++i) dst[(9 + i) * n + s] = gv[i];
+    dst[14 * n + s] = d.fl[s];
+  }
+  if (ctr) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (atomicAdd(ctr + 1, 1u) == gridDim.x - 1) {
+        ctr[1] = 0;
+        ctr[0] = ctr[0] + 1;
+      }
+    }
+  }
+}
+
 // Sentinel: every population and f_l of every node, flag stats[5] on the first
 // value that is not finite (NaN or Inf).
 __global__ void nonfinite_kernel(Dev d) {
@@ -276,6 +310,11 @@ void launch_get_state(const Dev& d, int layout, float* f, float* g, cudaStream_t
 }
 void launch_set_state(const Dev& d, const float* f, const float* g, cudaStream_t s) {
   set_state_kernel<<<grid1(d.n, 256), 256, 0, s>>>(d, f, g);
+}
+void launch_keep_state(const Dev& d, int layout, float* base, unsigned* ctr, cudaStream_t s) {
+  long long nb = (d.n + 255) / 256;
+  if (nb > 8 * 152) nb = 8 * 152;
+  keep_state_kernel<<<(unsigned)nb, 256, 0, s>>>(d, layout, base, ctr);
 }
 void launch_nonfinite(const Dev& d, int nblocks, cudaStream_t s) {
   nonfinite_kernel<<<nblocks, 256, 0, s>>>(d);

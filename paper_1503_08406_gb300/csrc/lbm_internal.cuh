@@ -317,6 +317,9 @@ void launch_reduce(const Dev& d, int parity, double* partials, double* out, int 
 int reduce_blocks(const Dev& d);
 void launch_get_state(const Dev& d, int parity, float* f, float* g, cudaStream_t s);
 void launch_set_state(const Dev& d, const float* f, const float* g, cudaStream_t s);
+// the whole state (f, g, f_l: 15 n floats, natural layout) into base, or into
+// base + ctr[0] 15 n and then ctr[0]++ when ctr is non-null (ctr[1] must be 0)
+void launch_keep_state(const Dev& d, int layout, float* base, unsigned* ctr, cudaStream_t s);
 // NaN/Inf sentinel over the whole state (sets stats[5])
 void launch_nonfinite(const Dev& d, int nblocks, cudaStream_t s);
 // one CTA waiting, with a limit of limit_ns, on an mbarrier nothing completes

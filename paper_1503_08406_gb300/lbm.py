@@ -141,7 +141,7 @@ def load():
         lib.lbm_adjoint.argtypes = [_VP, ctypes.c_int, ctypes.c_int64, ctypes.c_int32,
                                     ctypes.c_int32, _VP, _VP, _DP, ctypes.c_int]
         lib.lbm_adjoint_coupled.argtypes = [_VP, ctypes.c_int, ctypes.c_int64, ctypes.c_int32,
-                                            _VP, _VP, _VP, _DP, ctypes.c_int]
+                                            ctypes.c_int32, _VP, _VP, _VP, _DP, ctypes.c_int]
         lib.lbm_batch_create.argtypes = [ctypes.POINTER(_VP), ctypes.c_int, _VP,
                                          ctypes.POINTER(_VP)]
         lib.lbm_batch_step.argtypes = [_VP, ctypes.c_int64]
@@ -296,33 +296,46 @@ class Lattice:
 
     OBJECTIVES = {"melt": 0, "nusselt": 1}
 
+    def _grad_buffers(self, shapes, device: bool):
+        """Gradient outputs: torch CUDA tensors (device=True, written in place
+        by the library) or numpy arrays; returns (arrays, pointers)."""
+        if device:
+            torch = _torch()
+            outs = [torch.zeros(sh, dtype=torch.float32, device="cuda") for sh in shapes]
+            _torch().cuda.current_stream().synchronize()
+            return outs, [t.data_ptr() for t in outs]
+        outs = [np.zeros(sh, dtype=np.float32) for sh in shapes]
+        return outs, [a.ctypes.data for a in outs]
+
     def adjoint(self, nsteps: int, objective: str = "melt", checkpoint_every: int = 0,
-                mu_sweeps: int = 0):
+                mu_sweeps: int = 0, device: bool = False):
         """Run nsteps steps; return the objective and its gradient with respect
         to the porosity field ([ny, nx]) and the left wall's temperature
         profile ([ny]) (lbm_adjoint in include/lbm.h).  objective "melt": the
         melted fraction after the steps; "nusselt": the left-wall Nusselt
-        number after each step, averaged over the steps."""
-        dphi = np.zeros((self.ny, self.nx), dtype=np.float32)
-        dtw = np.zeros(self.ny, dtype=np.float32)
+        number after each step, averaged over the steps.  device=True returns
+        the gradients as CUDA tensors (no host copy)."""
+        (dphi, dtw), ptrs = self._grad_buffers([(self.ny, self.nx), (self.ny,)], device)
         J = ctypes.c_double()
         _check(self.lib.lbm_adjoint(self._h, self.OBJECTIVES[objective], int(nsteps),
-                                    int(checkpoint_every), int(mu_sweeps), dphi.ctypes.data,
-                                    dtw.ctypes.data, ctypes.byref(J), 0), "lbm_adjoint")
+                                    int(checkpoint_every), int(mu_sweeps), *ptrs,
+                                    ctypes.byref(J), int(device)), "lbm_adjoint")
         return J.value, dphi, dtw
 
-    def adjoint_coupled(self, nsteps: int, objective: str = "melt", mu_sweeps: int = 0):
+    def adjoint_coupled(self, nsteps: int, objective: str = "melt", checkpoint_every: int = 0,
+                        mu_sweeps: int = 0, device: bool = False):
         """The flow lattice on: run nsteps steps; return the objective and its
         gradients with respect to the porosity field ([ny, nx]), ln K
         ([ny, nx]) and the left wall's temperature profile ([ny])
-        (lbm_adjoint_coupled in include/lbm.h)."""
-        dphi = np.zeros((self.ny, self.nx), dtype=np.float32)
-        dlnK = np.zeros((self.ny, self.nx), dtype=np.float32)
-        dtw = np.zeros(self.ny, dtype=np.float32)
+        (lbm_adjoint_coupled in include/lbm.h).  checkpoint_every: 0 keeps
+        every state when it fits, K > 0 keeps one every K steps and recomputes
+        the rest.  device=True returns CUDA tensors."""
+        (dphi, dlnK, dtw), ptrs = self._grad_buffers(
+            [(self.ny, self.nx), (self.ny, self.nx), (self.ny,)], device)
         J = ctypes.c_double()
         _check(self.lib.lbm_adjoint_coupled(self._h, self.OBJECTIVES[objective], int(nsteps),
-                                            int(mu_sweeps), dphi.ctypes.data, dlnK.ctypes.data,
-                                            dtw.ctypes.data, ctypes.byref(J), 0),
+                                            int(checkpoint_every), int(mu_sweeps), *ptrs,
+                                            ctypes.byref(J), int(device)),
                "lbm_adjoint_coupled")
         return J.value, dphi, dlnK, dtw
 

@@ -15,12 +15,15 @@ class _FakeLattice:
     def set_fields(self, phi, K, T0, fl0, wall_T_left=None):
         self.fields = (phi, K, T0, fl0, wall_T_left)
 
-    def adjoint_coupled(self, nsteps, objective="melt"):
+    def adjoint_coupled(self, nsteps, objective="melt", checkpoint_every=0, mu_sweeps=0,
+                        device=False):
+        assert not device   # host tensors in, host arrays out
         phi, K, _, _, tw = self.fields
         return (float(phi.sum() + np.log(K).sum() + tw.sum()), 2 * np.ones_like(phi),
                 3 * np.ones_like(K), 4 * np.ones_like(tw))
 
-    def adjoint(self, nsteps, objective="melt", checkpoint_every=0, mu_sweeps=0):
+    def adjoint(self, nsteps, objective="melt", checkpoint_every=0, mu_sweeps=0, device=False):
+        assert not device
         phi, _, _, _, tw = self.fields
         return float(phi.sum() + tw.sum()), 5 * np.ones_like(phi), 6 * np.ones_like(tw)
 

@@ -1,10 +1,16 @@
-"""The CUDA adjoint of the coupled step (flow on) against the FP64 reference.
+"""The CUDA adjoint of the coupled step (flow on) against the FP64 reference
+and against finite differences of the FP64 oracle.
 
 lbm_adjoint_coupled differentiates the melted fraction, or the hot-wall
 Nusselt number averaged over the steps, with respect to porosity, ln K and
 the left wall profile; oracle/coupled_ref.py differentiates the same map by
-autograd and is pinned to finite differences of the C oracle.  FP32 on the
-GPU: bars of 2e-3 of the largest entry.
+autograd and is pinned to finite differences of the C oracle.  The GPU runs
+in FP32: its gradients are held to 1e-3 of the largest entry of the FP64
+reference's (normwise, the benchmark spec bar), and, at sampled cells, to central
+differences of the oracle's objective with h = 1e-4.
+
+Memory schedules: keeping every state, and keeping one every K steps with
+each segment recomputed from a CUDA graph, give the same bits.
 """
 import numpy as np
 import pytest
@@ -14,16 +20,33 @@ import lbm_workloads as W
 pytestmark = pytest.mark.gpu
 
 STEPS = 40
+TOL = 1e-3
+
+
+def _f32(w):
+    for k in ("phi", "K", "T0", "fl0"):
+        setattr(w, k, getattr(w, k).astype(np.float32).astype(np.float64))
+    if w.wall_T_left is not None:
+        w.wall_T_left = w.wall_T_left.astype(np.float32).astype(np.float64)
+    return w
 
 
 def _case():
     w = W.melted_cavity(24)
     params = dict(w.params)
     params.update(T_s=0.1, T_l=0.4)
-    tw = (1.0 + 0.1 * np.sin(2 * np.pi * np.arange(w.ny) / w.ny)).astype(np.float32)
-    for k in ("phi", "K", "T0", "fl0"):
-        setattr(w, k, getattr(w, k).astype(np.float32).astype(np.float64))
-    return w, params, tw.astype(np.float64)
+    w.wall_T_left = 1.0 + 0.1 * np.sin(2 * np.pi * np.arange(w.ny) / w.ny)
+    w.params = params
+    return _f32(w)
+
+
+def _copy64():
+    """The 64^2 copy of the 512^2 inverse-problem cavity (fields block-averaged
+    from the large draw), started a quarter melted so that 100 steps move
+    the front and the flow."""
+    w = W.adjoint_cavity(64, melted=0.25)
+    w.wall_T_left = 1.0 + 0.1 * np.sin(2 * np.pi * np.arange(w.ny) / w.ny)
+    return _f32(w)
 
 
 @pytest.fixture(scope="module")
@@ -36,21 +59,149 @@ def lbm():
     return P
 
 
+def _gpu(lbm, w, steps, objective, **kw):
+    lat = lbm.Lattice(w.nx, w.ny, **w.params)
+    lat.set_fields(w.phi, w.K, w.T0, w.fl0, w.wall_T_left)
+    out = lat.adjoint_coupled(steps, objective, **kw)
+    assert lat.status() == 0 and lat.steps_done() == steps
+    return out
+
+
+def _check_normwise(got, ref):
+    J, dphi, dlnK, dtw = got
+    J_ref, dphi_ref, dlnK_ref, dtw_ref = ref
+    assert abs(J - J_ref) < 1e-4 * abs(J_ref), (J, J_ref)
+    for name, g, e in (("phi", dphi, dphi_ref), ("lnK", dlnK, dlnK_ref), ("Tw", dtw, dtw_ref)):
+        scale = np.abs(e).max()
+        assert scale > 0
+        err = np.abs(np.asarray(g, dtype=np.float64) - e).max() / scale
+        assert err < TOL, (name, err)
+
+
 @pytest.mark.parametrize("objective", ["melt", "nusselt"])
 def test_coupled_adjoint_matches_fp64_reference(lbm, oracle_mod, objective):
     from oracle.coupled_ref import CoupledRef
-    w, params, tw = _case()
-    J_ref, dphi_ref, dlnK_ref, dtw_ref = CoupledRef(w.nx, w.ny, params).gradients(
-        STEPS, w.T0, w.fl0, w.phi, w.K, tw, objective)
-    lat = lbm.Lattice(w.nx, w.ny, **params)
-    lat.set_fields(w.phi, w.K, w.T0, w.fl0, tw)
-    J, dphi, dlnK, dtw = lat.adjoint_coupled(STEPS, objective)
-    assert lat.status() == 0 and lat.steps_done() == STEPS
-    assert abs(J - J_ref) < 1e-4 * abs(J_ref), (J, J_ref)
-    for got, exp in ((dphi, dphi_ref), (dlnK, dlnK_ref), (dtw, dtw_ref)):
-        scale = np.abs(exp).max()
-        assert scale > 0
-        assert np.abs(got - exp).max() < 2e-3 * scale, (np.abs(got - exp).max(), scale)
+    w = _case()
+    ref = CoupledRef(w.nx, w.ny, w.params).gradients(STEPS, w.T0, w.fl0, w.phi, w.K,
+                                                     w.wall_T_left, objective)
+    _check_normwise(_gpu(lbm, w, STEPS, objective), ref)
+
+
+@pytest.mark.parametrize("objective", ["melt", "nusselt"])
+def test_coupled_adjoint_64_copy_matches_fp64_reference(lbm, oracle_mod, objective):
+    from oracle.coupled_ref import CoupledRef
+    w = _copy64()
+    steps = 100
+    ref = CoupledRef(w.nx, w.ny, w.params).gradients(steps, w.T0, w.fl0, w.phi, w.K,
+                                                     w.wall_T_left, objective)
+    _check_normwise(_gpu(lbm, w, steps, objective, checkpoint_every=10), ref)
+
+
+def test_checkpointed_schedule_gives_the_same_bits(lbm):
+    w = _f32(W.melted_cavity(48))
+    w.params = {**w.params, "T_s": 0.1, "T_l": 0.4}
+    for objective in ("melt", "nusselt"):
+        full = _gpu(lbm, w, 61, objective, checkpoint_every=0)
+        for K in (7, 8, 61):
+            seg = _gpu(lbm, w, 61, objective, checkpoint_every=K)
+            assert full[0] == seg[0], (objective, K)
+            for a, b in zip(full[1:], seg[1:]):
+                assert np.array_equal(a, b), (objective, K)
+
+
+def test_device_gradients_equal_host_gradients(lbm):
+    import torch
+    w = _case()
+    host = _gpu(lbm, w, 20, "melt")
+    dev = _gpu(lbm, w, 20, "melt", device=True)
+    assert host[0] == dev[0]
+    for a, b in zip(host[1:], dev[1:]):
+        assert isinstance(b, torch.Tensor) and b.is_cuda
+        assert np.array_equal(a, b.cpu().numpy())
+
+
+def test_coupled_objective_autograd_on_device(lbm):
+    """CoupledObjective with CUDA tensors: gradients land on the device and
+    equal the adjoint's."""
+    import torch
+    from paper_1503_08406_gb300.autograd import CoupledObjective
+    w = _case()
+    lat = lbm.Lattice(w.nx, w.ny, **w.params)
+    phi = torch.tensor(w.phi, dtype=torch.float32, device="cuda", requires_grad=True)
+    lnK = torch.tensor(np.log(w.K), dtype=torch.float32, device="cuda", requires_grad=True)
+    tw = torch.tensor(w.wall_T_left, dtype=torch.float32, device="cuda", requires_grad=True)
+    J = CoupledObjective.apply(phi, lnK, tw, lat, w.T0, w.fl0, 20, "nusselt")
+    J.backward()
+    assert phi.grad.is_cuda and lnK.grad.is_cuda and tw.grad.is_cuda
+    lat2 = lbm.Lattice(w.nx, w.ny, **w.params)
+    lat2.set_fields(phi.detach(), torch.exp(lnK.detach()), w.T0, w.fl0, tw.detach())
+    J2, dphi, dlnK, dtw = lat2.adjoint_coupled(20, "nusselt")
+    assert abs(J.item() - J2) <= 1e-12 * abs(J2)
+    np.testing.assert_array_equal(phi.grad.cpu().numpy(), dphi)
+    np.testing.assert_array_equal(lnK.grad.cpu().numpy(), dlnK)
+    np.testing.assert_array_equal(tw.grad.cpu().numpy(), dtw)
+
+
+def _oracle_objective(oracle_mod, w, steps, objective, phi=None, K=None, tw=None):
+    o = oracle_mod.Oracle(w.nx, w.ny, **{**w.params, "inner_tol": 1e-13})
+    o.set_fields(w.phi if phi is None else phi, w.K if K is None else K, w.T0, w.fl0,
+                 w.wall_T_left if tw is None else tw)
+    if objective == "melt":
+        o.step(steps)
+        return o.reduce()["melt_frac"]
+    acc = 0.0
+    for _ in range(steps):
+        o.step(1)
+        acc += o.reduce()["nu_hot"]
+    return acc / steps
+
+
+@pytest.mark.parametrize("objective", ["melt", "nusselt"])
+def test_coupled_adjoint_matches_oracle_finite_differences(lbm, oracle_mod, objective):
+    """Central differences of the FP64 oracle's objective, h = 1e-4 (in phi,
+    ln K and the wall profile), on seeded cells: 16 cells whose f_l after the
+    run lies in (0.05, 0.95) (the front, away from the clamps), and wall rows."""
+    w = _copy64()
+    steps = 100
+    J, dphi, dlnK, dtw = _gpu(lbm, w, steps, objective)
+    o = oracle_mod.Oracle(w.nx, w.ny, **w.params)
+    o.set_fields(w.phi, w.K, w.T0, w.fl0, w.wall_T_left)
+    o.step(steps)
+    fl_end = o.macros()["fl"]
+    rng = np.random.default_rng(12)
+    cand = np.argwhere((fl_end > 0.05) & (fl_end < 0.95))
+    cells = cand[rng.choice(len(cand), size=min(16, len(cand)), replace=False)]
+    h = 1e-4
+    rows = rng.choice(np.arange(1, w.ny - 1), size=4, replace=False)
+    scale = {"phi": np.abs(dphi).max(), "lnK": np.abs(dlnK).max(), "Tw": np.abs(dtw).max()}
+    worst = {}
+    for (y, x) in cells:
+        for name, grad in (("phi", dphi), ("lnK", dlnK)):
+            vals = []
+            for sgn in (1, -1):
+                if name == "phi":
+                    p = w.phi.copy()
+                    p[y, x] += sgn * h
+                    vals.append(_oracle_objective(oracle_mod, w, steps, objective, phi=p))
+                else:
+                    K = w.K.copy()
+                    K[y, x] *= np.exp(sgn * h)
+                    vals.append(_oracle_objective(oracle_mod, w, steps, objective, K=K))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            err = abs(grad[y, x] - fd) / max(abs(fd), 1e-2 * scale[name])
+            worst[name] = max(worst.get(name, 0.0), err)
+    for y in rows:
+        vals = []
+        for sgn in (1, -1):
+            tw = w.wall_T_left.copy()
+            tw[y] += sgn * h
+            vals.append(_oracle_objective(oracle_mod, w, steps, objective, tw=tw))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        err = abs(dtw[y] - fd) / max(abs(fd), 1e-2 * scale["Tw"])
+        worst["Tw"] = max(worst.get("Tw", 0.0), err)
+    print("worst relative gap to the oracle's central differences:", worst)
+    for name, err in worst.items():
+        assert err < TOL, (name, err, worst)
 
 
 def test_coupled_adjoint_rejects_conduction(lbm):
