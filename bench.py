@@ -71,13 +71,16 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--storage", choices=("fp32", "fp16", "bf16"), default="fp32",
                     help="population storage (arithmetic is FP32 in every case)")
-    ap.add_argument("--workload", choices=("cavity", "batched", "adjoint", "adjoint_coupled"),
+    ap.add_argument("--workload", choices=("cavity", "batched", "adjoint", "adjoint_coupled",
+                                           "convection"),
                     default="cavity",
                     help="cavity: the 2048^2 heterogeneous cavity (default); batched: 64 "
                          "uneven cavities advanced together through one CUDA graph; adjoint: "
                          "melted fraction and its gradients on an n x ny conduction slab, "
                          "timed against the forward run alone; adjoint_coupled: the same "
-                         "with the flow lattice on, the n^2 inverse-problem cavity")
+                         "with the flow lattice on, the n^2 inverse-problem cavity; "
+                         "convection: the uniform n^2 convection-melting cavity, its "
+                         "melted fraction, Nusselt number and f_l = 0.5 contour")
     ap.add_argument("--ny", type=int, default=512, help="adjoint workload: slab height")
     ap.add_argument("--objective", choices=("melt", "nusselt"), default="melt",
                     help="adjoint workload: melted fraction at the end, or the left-wall "
@@ -462,6 +465,57 @@ def adjoint_coupled(args, torch):
     return 0
 
 
+def convection(args, torch):
+    """Convection melting in the uniform porous cavity (lbm_workloads.convection_cavity,
+    n^2, phi = 0.4, Da = 1e-4, Ra = 1e5): `steps` steps from the solid start;
+    the line reports MLUPS and the outputs the workload asks for: melted
+    fraction, hot-wall Nusselt number (every `steps / 50` steps and their
+    mean) and the f_l = 0.5 contour (its x position, interpolated, on every
+    16th row)."""
+    import numpy as np
+    import lbm_workloads as W
+    from paper_1503_08406_gb300 import Lattice
+    w = W.convection_cavity(args.n)
+    stream = torch.cuda.current_stream()
+    lat = Lattice(w.nx, w.ny, stream=stream, **w.params)
+    lat.set_fields(w.phi, w.K, w.T0, w.fl0)
+    every = max(args.steps // 50, 1)
+    lat.prepare(every)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nus, done, ms = [], 0, 0.0
+    while done < args.steps:
+        k = min(every, args.steps - done)
+        e0.record(stream)
+        lat.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        done += k
+        nus.append(lat.reduce()["nu_hot"])
+    r = lat.reduce()
+    fl = lat.macros()["fl"]
+    contour = []
+    for y in range(1, w.ny - 1, 16):
+        row = fl[y]
+        xs = np.flatnonzero((row[:-1] >= 0.5) & (row[1:] < 0.5))
+        if xs.size:
+            x0 = int(xs[-1])
+            t = (row[x0] - 0.5) / (row[x0] - row[x0 + 1])
+            contour.append([y, round(float(x0 + t), 3)])
+    line = {
+        "metric": "convection melting in the porous cavity: outputs after %d steps" % args.steps,
+        "value": w.cells * args.steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": 0, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": {"workload": w.name, "lattice": [w.nx, w.ny]},
+        "melted_fraction": r["melt_frac"], "nu_hot": r["nu_hot"],
+        "nu_hot_mean_over_run": float(np.mean(nus)), "nu_hot_samples_every": every,
+        "front_fl05_x_by_row": contour, "status": lat.status(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse(argv)
     if args.impl == "reference":
@@ -471,12 +525,13 @@ def main(argv=None):
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device (there is no CPU path)")
     torch.cuda.set_device(local)
-    if args.workload in ("batched", "adjoint", "adjoint_coupled"):
+    if args.workload in ("batched", "adjoint", "adjoint_coupled", "convection"):
         if world > 1:
             raise SystemExit("the %s workload runs on one GPU" % args.workload)
         import __graft_entry__
         __graft_entry__.build()
-        run = {"batched": batched, "adjoint": adjoint, "adjoint_coupled": adjoint_coupled}
+        run = {"batched": batched, "adjoint": adjoint, "adjoint_coupled": adjoint_coupled,
+               "convection": convection}
         return run[args.workload](args, torch)
     dist = init_dist(world, "nccl")
     device = torch.device("cuda", local)

@@ -97,6 +97,12 @@ typedef struct {
                                      Inf after every check_every steps (one read of the state,
                                      queued on the stream); lbm_status then reports
                                      LBM_ERR_NONFINITE.  0: no sentinel */
+  double  sigma_solid;            /* heat-capacity ratio of the solid, Eq. (7): > 0 and != sigma
+                                     makes sigma linear in f_l, sigma_solid + f_l (sigma -
+                                     sigma_solid), taken at f_l(n) per node in tau_T (the given
+                                     tau_T belongs to the liquid), in n^eq of Eq. (34), in the
+                                     wall extrapolation and in the latent coefficient
+                                     a = phi dT / (sigma St) of Eq. (38); 0: one sigma */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;

@@ -335,7 +335,7 @@ def adjoint_cavity(n: int = 512, seed: int = 5, source_n: int = 512, melted: flo
                     meta=dict(seed=seed, source_n=big, Da=Da))
 
 
-def porous_gallium_cavity(n: int = 200) -> Workload:
+def porous_gallium_cavity(n: int = 200, solid_sigma: bool = False) -> Workload:
     """Sec. 4.3: convection melting in a square cavity filled with porous
     media, with the paper's parameter set (the gallium / glass-bead
     experiment it compares with): Ra = 8.409e5, Da = 1.37e-5 (K = Da H^2),
@@ -344,15 +344,19 @@ def porous_gallium_cavity(n: int = 200) -> Workload:
     Temperatures scaled as (T - T_c) / (T_h - T_c) with T_h = 45, T_c = 20:
     hot wall 1, cold wall 0, T_m = (29.78 - 20) / 25 = 0.3912, initial solid
     at T_i = T_0 = 20 -> 0 (also the buoyancy reference).  The paper gives
-    sigma = 0.8604 in the liquid and 0.8352 in the solid; the liquid value is
-    used everywhere (sigma(f_l) is not modelled).  The paper states no mushy
-    band for this case: T_m -/+ 0.02 as in Sec. 4.1.  Adiabatic top and
+    sigma = 0.8604 in the liquid and 0.8352 in the solid; by default the
+    liquid value is used everywhere, with ``solid_sigma`` sigma follows f_l
+    by Eq. (7) between the two (parameter sigma_solid).  The paper states no
+    mushy band for this case: T_m -/+ 0.02 as in Sec. 4.1.  Adiabatic top and
     bottom."""
     T_m = (29.78 - 20.0) / 25.0
     params = dict(bc=("dirichlet", "dirichlet", "adiabatic", "adiabatic"),
                   T_bc=(1.0, 0.0, 0.0, 0.0), flow=1, Ra=8.409e5, Pr=0.0208, Ma=0.1, J=1.0,
                   lambda_=0.2719, sigma=0.8604, St=0.1241, dT=1.0, H=float(n), T_ref=0.0,
                   T_s=T_m - 0.02, T_l=T_m + 0.02)
+    if solid_sigma:
+        params["sigma_solid"] = 0.8352
     phi_f, K, T0, fl0 = _cavity_fields(n, 0.385, 1.37e-5 * n * n)
-    return Workload("porous_gallium_cavity_%d" % n, n, n, params, phi_f, K, T0, fl0,
+    return Workload("porous_gallium_cavity_%d%s" % (n, "_solid_sigma" if solid_sigma else ""),
+                    n, n, params, phi_f, K, T0, fl0,
                     meta=dict(T_m=T_m, sigma_solid=0.8352))

@@ -83,8 +83,11 @@ __global__ void adj_list_kernel(Dev d, const float* f, int* list, int* count) {
 
 // The fixed point's adjoint on the band: right-hand side
 // lam_f'(y) - a(y) sum_i w~_i lam_g'_i(y + e_i), then Jacobi sweeps with the
-// self term exact, from mu = 0, until no node changes by more than MU_RTOL of
-// its value or after max_sweeps.  Up to BAND_CAP band nodes sweep in shared
+// self term exact until no node changes by more than MU_RTOL of its value or
+// after max_sweeps.  The sweeps start from mu of the step reversed before this
+// one (b.muw; zero on nodes that were not in its band): the front moves little
+// from step to step, so that is close to this step's solution, and the fixed
+// point does not depend on where the sweeps start.  Up to BAND_CAP band nodes sweep in shared
 // memory (each node's coefficients and its neighbours' places in the list
 // staged once); a wider band sweeps in global memory.  Jacobi makes the
 // result independent of the list's order.  Empties the previous band's list
@@ -148,7 +151,7 @@ __global__ void __launch_bounds__(BAND_THREADS) adj_band_kernel(Dev d, AdjBuffer
       const float den = 1.f - as * (1.f - d.wt0) / (d.dTt + as);
       rhs[j] = band_rhs(d, b, s) / den;
       kk[j] = as * d.wt1 / den;
-      mu[j] = 0.f;
+      mu[j] = b.muw[s];
     }
     __syncthreads();
     for (int k = 0; k < max_sweeps; ++k) {
@@ -169,6 +172,7 @@ __global__ void __launch_bounds__(BAND_THREADS) adj_band_kernel(Dev d, AdjBuffer
     }
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
       const int s = list[j];
+      b.muw[s] = mu[j];
       add_nu(d, b, s, mu[j] / (d.dTt + b.a[s]));
     }
   } else {
@@ -178,7 +182,7 @@ __global__ void __launch_bounds__(BAND_THREADS) adj_band_kernel(Dev d, AdjBuffer
       const int s = list[j];
       const float as = b.a[s];
       b.rhs[s] = band_rhs(d, b, s) / (1.f - as * (1.f - d.wt0) / (d.dTt + as));
-      mu[s] = 0.f;
+      mu[s] = b.muw[s];
     }
     __syncthreads();
     for (int k = 0; k < max_sweeps; ++k) {
@@ -205,6 +209,7 @@ __global__ void __launch_bounds__(BAND_THREADS) adj_band_kernel(Dev d, AdjBuffer
     }
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
       const int s = list[j];
+      b.muw[s] = mu[s];
       add_nu(d, b, s, mu[s] / (d.dTt + b.a[s]));
     }
   }

@@ -121,6 +121,7 @@ int check_params(const lbm_params* p) {
   if (p->kernel_variant < 0 || p->kernel_variant > 2) return LBM_ERR_INVALID_ARG;
   if (p->storage < LBM_STORAGE_FP32 || p->storage > LBM_STORAGE_BF16) return LBM_ERR_INVALID_ARG;
   if (!(p->alpha_ratio >= 0)) return LBM_ERR_INVALID_ARG;
+  if (!(p->sigma_solid >= 0)) return LBM_ERR_INVALID_ARG;
   return LBM_OK;
 }
 
@@ -268,6 +269,8 @@ int lbm_create(const lbm_params* pin, void* stream, void* workspace, size_t work
   d.alpha_var = (p.alpha_ratio > 0 && p.alpha_ratio != 1.0) ? 1 : 0;
   d.tauT_l = (float)der[1];
   d.inv_aratio = d.alpha_var ? (float)(1.0 / p.alpha_ratio) : 1.f;
+  d.sigma_var = (p.sigma_solid > 0 && p.sigma_solid != p.sigma) ? 1 : 0;
+  d.sigma_s = d.sigma_var ? (float)p.sigma_solid : (float)p.sigma;
   d.z_e = (float)p.zeta_e;
   d.z_nu = (float)p.zeta_nu;
   d.varpi = (float)p.varpi;
@@ -1063,7 +1066,8 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
     return LBM_ERR_INVALID_ARG;
   if (objective != LBM_OBJ_MELT && objective != LBM_OBJ_NUSSELT) return LBM_ERR_INVALID_ARG;
   const lbm_params& p = c->p;
-  if (p.flow || c->timing || p.storage != LBM_STORAGE_FP32 || c->d.alpha_var) return LBM_ERR_INVALID_ARG;
+  if (p.flow || c->timing || p.storage != LBM_STORAGE_FP32 || c->d.alpha_var || c->d.sigma_var)
+    return LBM_ERR_INVALID_ARG;
   if (!c->d.per_y || c->d.per_x || p.bc[0] != LBM_BC_DIRICHLET) return LBM_ERR_INVALID_ARG;
   const bool melt = objective == LBM_OBJ_MELT;
   if (!melt && c->d.nx < 5) return LBM_ERR_INVALID_ARG;   // x = 1, 2 interior
@@ -1101,6 +1105,7 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
   b.rhs = mem.get(n);
   b.mu0 = mem.get(n);
   b.mu1 = mem.get(n);
+  b.muw = mem.get(n);
   b.lamgpre = mem.get(5 * n);
   b.lama = mem.get(n);
   b.lamtw = mem.get((size_t)c->d.ny);
@@ -1111,7 +1116,7 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
   double* nu_acc = reinterpret_cast<double*>(mem.get(2));
   double* dJ = reinterpret_cast<double*>(mem.get(2 * 129));
   if (!flS || (!keep_all && (!cps || !fin)) || !b.a || !b.lamg || !b.lamf || !b.rhs ||
-      !b.mu0 || !b.mu1 || !b.lamgpre || !b.lama || !b.lamtw || !b.pos || !lists[0] ||
+      !b.mu0 || !b.mu1 || !b.muw || !b.lamgpre || !b.lama || !b.lamtw || !b.pos || !lists[0] ||
       !lists[1] || !counts || !ctr || !nu_acc || !dJ)
     return LBM_ERR_OOM;
   // transposed collision matrix with u = 0: g+ = A g,
@@ -1179,6 +1184,7 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
   if (melt) lbm::adj_objective(c->d, fl_end, dJ, c->stream);
   // reverse sweep
   LBM_CUDA(cudaMemsetAsync(b.lama, 0, n * sizeof(float), c->stream));
+  LBM_CUDA(cudaMemsetAsync(b.muw, 0, n * sizeof(float), c->stream));
   LBM_CUDA(cudaMemsetAsync(b.lamtw, 0, c->d.ny * sizeof(float), c->stream));
   LBM_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(int), c->stream));
   lbm::adj_list(c->d, fl_end, lists[0], counts, c->stream);
@@ -1289,7 +1295,7 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
   if (objective != LBM_OBJ_MELT && objective != LBM_OBJ_NUSSELT) return LBM_ERR_INVALID_ARG;
   const lbm_params& p = c->p;
   const lbm::Dev& d = c->d;
-  if (!p.flow || c->timing || p.storage != LBM_STORAGE_FP32 || d.alpha_var)
+  if (!p.flow || c->timing || p.storage != LBM_STORAGE_FP32 || d.alpha_var || d.sigma_var)
     return LBM_ERR_INVALID_ARG;
   if (d.per_x || p.bc[0] != LBM_BC_DIRICHLET || d.nx < 5) return LBM_ERR_INVALID_ARG;
   const bool melt = objective == LBM_OBJ_MELT;
@@ -1323,6 +1329,7 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
   b.rhs = mem.get(n);
   b.mu0 = mem.get(n);
   b.mu1 = mem.get(n);
+  b.muw = mem.get(n);
   b.lama = mem.get(n);   // adjoint of phi
   b.lamtw = mem.get((size_t)d.ny);
   b.pos = reinterpret_cast<int*>(mem.get(n));
@@ -1332,7 +1339,7 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
   double* nu_acc = reinterpret_cast<double*>(mem.get(2));
   unsigned* ctr = reinterpret_cast<unsigned*>(mem.get(2));
   if (!S || (!keep_all && (!cps || !fin)) || !lf[0] || !lf[1] || !lg[0] || !lg[1] || !b.a ||
-      !b.lamf || !b.rhs || !b.mu0 || !b.mu1 || !b.lama || !b.lamtw || !b.pos || !lK ||
+      !b.lamf || !b.rhs || !b.mu0 || !b.mu1 || !b.muw || !b.lama || !b.lamtw || !b.pos || !lK ||
       !lists[0] || !lists[1] || !counts || !nu_acc || !ctr)
     return LBM_ERR_OOM;
   // rows of the Nusselt number (lbm_reduce's): all but horizontal wall rows
@@ -1405,6 +1412,7 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
                            c->stream));
   LBM_CUDA(cudaMemsetAsync(lf[0], 0, 9 * n * sizeof(float), c->stream));
   LBM_CUDA(cudaMemsetAsync(b.lama, 0, n * sizeof(float), c->stream));
+  LBM_CUDA(cudaMemsetAsync(b.muw, 0, n * sizeof(float), c->stream));
   LBM_CUDA(cudaMemsetAsync(lK, 0, n * sizeof(float), c->stream));
   LBM_CUDA(cudaMemsetAsync(b.lamtw, 0, d.ny * sizeof(float), c->stream));
   LBM_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(int), c->stream));
@@ -1484,13 +1492,24 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
       cudaMemcpyAsync(c->d.fl, S + 14 * n, n * sizeof(float), cudaMemcpyDeviceToDevice, sm);
       cudaMemsetAsync(c->d.flags, 0, 2 * sizeof(int) * c->d.ntiles, sm);
       cudaMemsetAsync(c->d.lcount, 0, 2 * sizeof(int), sm);
-      int par = 0;
-      for (int64_t m = 1; m <= len; ++m) {
-        lbm::launch_fused(c->d, c->tma(), par, 0, sm);
-        lbm::launch_enthalpy_solve(c->d, par, sm);
-        lbm::launch_enthalpy_commit(c->d, par, sm);
-        par ^= 1;
-        lbm::launch_keep_state(c->d, par, S + (size_t)m * st, nullptr, sm);
+      if (sm == c->cap) {
+        // in a capture: the step sequence of lbm_step's graphs (the next step's
+        // far tiles beside each step's enthalpy kernels), the state after each
+        // step kept at S + m st through a counter reset here
+        cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), sm);
+        Hooks hk;
+        hk.st_base = S + st;
+        hk.st_ctr = ctr;
+        capture_body(c, (int)len, 0, &hk);
+      } else {
+        int par = 0;
+        for (int64_t m = 1; m <= len; ++m) {
+          lbm::launch_fused(c->d, c->tma(), par, 0, sm);
+          lbm::launch_enthalpy_solve(c->d, par, sm);
+          lbm::launch_enthalpy_commit(c->d, par, sm);
+          par ^= 1;
+          lbm::launch_keep_state(c->d, par, S + (size_t)m * st, nullptr, sm);
+        }
       }
       reverse(sm, S, 0, len);
     };

@@ -136,7 +136,11 @@ __global__ void __launch_bounds__(RB) reduce_kernel(Dev d, int layout, double* p
       const double T = (double)interior_T(d, x, y, layout);
       const double fl = (double)d.fl[s];
       acc[0] += m;
-      acc[1] += T + (double)d.phi[s] * (double)d.lat * fl;
+      // a = phi dT / (sigma(f_l) St), Eq. (38) with Eq. (7)
+      const double sr = d.sigma_var ? (double)d.sigma / ((double)d.sigma_s +
+                                                         fl * ((double)d.sigma - d.sigma_s))
+                                    : 1.0;
+      acc[1] += T + (double)d.phi[s] * (double)d.lat * sr * fl;
       acc[2] += fl;
       acc[3] += 1.0;
     }
@@ -246,17 +250,36 @@ __global__ void keep_state_kernel(Dev d, int layout, float* base, unsigned* ctr)
   for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n;
        s += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(s / d.nx), x = (int)(s - (long long)y * d.nx);
-    float fv[9], gv[5];
-    if (is_wall(d, x, y)) {
-      for (int i = 0; i < 9; ++i) fv[i] = ld_f(d, i, s);
-      for (int i = 0; i < 5; ++i) gv[i] = ld_g(d, i, s);
-    } else {
-      gather_f(d, x, y, layout, fv);
-      gather_g(d, x, y, layout, gv);
+    const bool wall = is_wall(d, x, y);
+    const float fls = d.fl[s];
+    // every load is issued before any value is chosen (gather_f / gather_g
+    // with the candidates of both layouts loaded up front)
+    float own[9], str[9], gown[5], gstr[5];
+    bool act[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) own[i] = ld_f(d, i, s);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) gown[i] = ld_g(d, i, s);
+    const bool swapped = layout == 1 && !wall;
+    if (swapped) {
+#pragma unroll
+      for (int i = 1; i < 9; ++i) {
+        const int sx = wrapx(d, x - ex9(i)), sy = wrapy(d, y - ey9(i));
+        const long long t = (long long)sy * d.nx + sx;
+        act[i] = !is_wall(d, sx, sy) && d.fl[t] >= d.f_act;
+        str[i] = ld_f(d, opp9(i), t);
+        if (i < 5) gstr[i] = ld_g(d, opp5(i), t);
+      }
     }
-    for (int i = 0; i < 9; ++i) dst[i * n + s] = fv[i];
-    for (int i = 0; i < 5; ++i) dst[(9 + i) * n + s] = gv[i];
-    dst[14 * n + s] = d.fl[s];
+    const bool self = !wall && fls >= d.f_act;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const float v = (swapped && self && i > 0 && act[i]) ? str[i] : own[i];
+      dst[i * n + s] = v;
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) dst[(9 + i) * n + s] = (swapped && i > 0) ? gstr[i] : gown[i];
+    dst[14 * n + s] = fls;
   }
   if (ctr) {
     __syncthreads();

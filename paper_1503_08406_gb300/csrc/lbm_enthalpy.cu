@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
         const int s = gy * d.nx + gx;
         fn = d.fl[s];
         if (!is_wall(d, gx, gy)) {
-          a = d.phi[s] * d.lat;
+          a = d.phi[s] * d.lat * sigma_ratio(d, fn);   // phi dT / (sigma(f_l(n)) St)
           base = tstar(d, gx, gy, LAYOUT) + w0 * a * fn - Ts;
           inv = 1.f / (dTt + w0 * a);
         }
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(CB) enthalpy_commit_kernel(Dev d) {
         const float fn = p.x, fnew = p.y;
         if (fnew != fn) {
           d.fl[s] = fnew;
-          const float S0 = -d.phi[s] * d.lat * (fnew - fn);
+          const float S0 = -d.phi[s] * d.lat * sigma_ratio(d, fn) * (fnew - fn);
           // N^-1 S~ = S0 w~, streamed: population i of node x + e_i gains w~_i S0
 #pragma unroll
           for (int i = 0; i < 5; ++i) {

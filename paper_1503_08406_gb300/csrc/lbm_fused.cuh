@@ -276,10 +276,16 @@ __device__ __forceinline__ bool node_update(const Dev& d, int x, int y, const Ge
   const float n1 = g1 - g3, n2 = g2 - g4;
   const float n3 = -4.f * g0 + g1 + g2 + g3 + g4;
   const float n4 = g1 - g2 + g3 - g4;
-  const float th = d.conv * d.csT2;   // vartheta / sigma
-  // zeta_alpha = 1/tau_T; with alpha_l != alpha_s, alpha_e follows f_l(n) (Sec. 4.1)
+  // sigma_l / sigma(f_l(n)) (Eq. (7)); 1 with one sigma for both phases
+  const float sr = sigma_ratio(d, flc);
+  const float th = d.conv * d.csT2 * sr;   // vartheta / sigma
+  // zeta_alpha = 1/tau_T = 1/(1/2 + alpha_e / (sigma c_sT^2)); alpha_e follows
+  // f_l(n) with alpha_l != alpha_s (Sec. 4.1), sigma with sigma_s != sigma_l
   const float za =
-      d.alpha_var ? 1.f / (0.5f + (d.tauT_l - 0.5f) * (flc + (1.f - flc) * d.inv_aratio)) : d.z_a;
+      (d.alpha_var | d.sigma_var)
+          ? 1.f / (0.5f + (d.tauT_l - 0.5f) * (d.alpha_var ? flc + (1.f - flc) * d.inv_aratio
+                                                           : 1.f) * sr)
+          : d.z_a;
   const float b1 = -0.5f * za * (n1 - th * ux * T);
   const float b2 = -0.5f * za * (n2 - th * uy * T);
   const float b3 = -0.05f * d.z_e * (n3 - d.varpi * T);
@@ -322,7 +328,7 @@ __device__ __forceinline__ bool node_update(const Dev& d, int x, int y, const Ge
 
   // ---- thermal walls: inward population of adjacent wall nodes ------------
   // wall on side S at x_b = x - e_k, inward direction k; geq_k(T,u) = w~ T (1 + conv e_k.u)
-  const float cv = d.conv;
+  const float cv = d.conv * sr;
 #define LBM_WALL_POP(COND, K, SB, TW, EU)                                         \
   if (COND) {                                                                     \
     const float gpk = (K == 1) ? gp1 : (K == 2) ? gp2 : (K == 3) ? gp3 : gp4;     \

@@ -57,6 +57,8 @@ struct Dev {
   float z_a, z_e, z_nu;      // 1/tau_T, zeta_e, zeta_nu
   int alpha_var;             // tau_T depends on f_l (alpha_l != alpha_s)
   float tauT_l, inv_aratio;  // liquid tau_T, alpha_s / alpha_l
+  int sigma_var;             // sigma follows f_l, Eq. (7): sigma_s + f_l (sigma - sigma_s)
+  float sigma_s;             // its solid value (sigma is the liquid one)
   float varpi, csT2, sigma;
   float conv;                // vartheta / (sigma c_sT^2)
   float wt0, wt1;            // D2Q5 weights of Eq. (39)
@@ -260,6 +262,12 @@ __device__ __forceinline__ int wrapy(const Dev& d, int y) {
 __device__ __forceinline__ bool is_wall(const Dev& d, int x, int y) {
   return (d.wall_l && x == 0) || (d.wall_r && x == d.nx - 1) || (d.wall_b && y == 0) ||
          (d.wall_t && y == d.ny - 1);
+}
+
+// sigma_l / sigma(f_l) with the heat-capacity ratio of Eq. (7) linear in f_l
+// (1 when sigma does not follow f_l)
+__host__ __device__ __forceinline__ float sigma_ratio(const Dev& d, float fl) {
+  return d.sigma_var ? d.sigma / (d.sigma_s + fl * (d.sigma - d.sigma_s)) : 1.f;
 }
 
 // Permeability and inertial coefficient at varphi = phi f_l, Eq. (6); the

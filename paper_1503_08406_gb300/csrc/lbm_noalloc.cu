@@ -41,6 +41,8 @@ struct Geo {
   int bc[4];
   float Tbc[4];
   float rho0, lat, H_over_dT;
+  int sigma_var;               // sigma linear in f_l (Eq. 7): sigma_s + f_l (sigma_l - sigma_s)
+  float sigma_l, sigma_s;
   float f_act;
 };
 
@@ -101,7 +103,10 @@ __global__ void __launch_bounds__(RED_THREADS) rows_kernel(Geo q, const float* f
     const double T = (double)sum_g(g, n, s);
     const double l = (double)fl[s];
     acc[0] += m;
-    acc[1] += T + (double)phi[s] * (double)q.lat * l;
+    const double sr = q.sigma_var ? (double)q.sigma_l / ((double)q.sigma_s +
+                                                         l * ((double)q.sigma_l - q.sigma_s))
+                                  : 1.0;
+    acc[1] += T + (double)phi[s] * (double)q.lat * sr * l;
     acc[2] += l;
     acc[3] += 1.0;
   }
@@ -190,6 +195,9 @@ extern "C" int lbm_reduce_state_noalloc(const lbm_params* p, const float* f, con
   const double H = p->H > 0 ? p->H : (double)p->ny;
   q.rho0 = (float)(p->rho0 > 0 ? p->rho0 : 1.0);
   q.lat = (float)(dT / (p->sigma * p->St));
+  q.sigma_var = p->sigma_solid > 0 && p->sigma_solid != p->sigma;
+  q.sigma_l = (float)p->sigma;
+  q.sigma_s = (float)(q.sigma_var ? p->sigma_solid : p->sigma);
   q.H_over_dT = (float)(H / dT);
   cudaStream_t s = (cudaStream_t)stream;
   rows_kernel<<<p->ny, RED_THREADS, 0, s>>>(q, f, g, fl, phi, wall_T_left, rows);

@@ -159,8 +159,15 @@ def _oracle_objective(oracle_mod, w, steps, objective, phi=None, K=None, tw=None
 @pytest.mark.parametrize("objective", ["melt", "nusselt"])
 def test_coupled_adjoint_matches_oracle_finite_differences(lbm, oracle_mod, objective):
     """Central differences of the FP64 oracle's objective, h = 1e-4 (in phi,
-    ln K and the wall profile), on seeded cells: 16 cells whose f_l after the
-    run lies in (0.05, 0.95) (the front, away from the clamps), and wall rows."""
+    ln K and the wall profile), at 16 seeded cells whose f_l after the run
+    lies in (0.05, 0.95) (the front, away from the clamps) and whose gradient
+    is at least 5% of the field's largest (an FP32 gradient carries an
+    absolute error of ~1e-5 of the largest entry, so smaller entries cannot be
+    held to 1e-3 of themselves), and at 4 wall rows.  Each difference is taken
+    at h and 2h: their gap is the difference's own noise (the objective's FP64
+    rounding over 100 steps against a change of 2 h |dJ| -- large for the
+    melted fraction's tiny ln K and wall gradients), which the bar adds to
+    1e-3 relative."""
     w = _copy64()
     steps = 100
     J, dphi, dlnK, dtw = _gpu(lbm, w, steps, objective)
@@ -169,37 +176,41 @@ def test_coupled_adjoint_matches_oracle_finite_differences(lbm, oracle_mod, obje
     o.step(steps)
     fl_end = o.macros()["fl"]
     rng = np.random.default_rng(12)
-    cand = np.argwhere((fl_end > 0.05) & (fl_end < 0.95))
-    cells = cand[rng.choice(len(cand), size=min(16, len(cand)), replace=False)]
     h = 1e-4
-    rows = rng.choice(np.arange(1, w.ny - 1), size=4, replace=False)
-    scale = {"phi": np.abs(dphi).max(), "lnK": np.abs(dlnK).max(), "Tw": np.abs(dtw).max()}
-    worst = {}
-    for (y, x) in cells:
-        for name, grad in (("phi", dphi), ("lnK", dlnK)):
-            vals = []
-            for sgn in (1, -1):
-                if name == "phi":
-                    p = w.phi.copy()
-                    p[y, x] += sgn * h
-                    vals.append(_oracle_objective(oracle_mod, w, steps, objective, phi=p))
-                else:
-                    K = w.K.copy()
-                    K[y, x] *= np.exp(sgn * h)
-                    vals.append(_oracle_objective(oracle_mod, w, steps, objective, K=K))
-            fd = (vals[0] - vals[1]) / (2 * h)
-            err = abs(grad[y, x] - fd) / max(abs(fd), 1e-2 * scale[name])
-            worst[name] = max(worst.get(name, 0.0), err)
-    for y in rows:
+
+    def cd(name, y, x, hh):
         vals = []
         for sgn in (1, -1):
-            tw = w.wall_T_left.copy()
-            tw[y] += sgn * h
-            vals.append(_oracle_objective(oracle_mod, w, steps, objective, tw=tw))
-        fd = (vals[0] - vals[1]) / (2 * h)
-        err = abs(dtw[y] - fd) / max(abs(fd), 1e-2 * scale["Tw"])
-        worst["Tw"] = max(worst.get("Tw", 0.0), err)
-    print("worst relative gap to the oracle's central differences:", worst)
+            if name == "phi":
+                p = w.phi.copy()
+                p[y, x] += sgn * hh
+                vals.append(_oracle_objective(oracle_mod, w, steps, objective, phi=p))
+            elif name == "lnK":
+                K = w.K.copy()
+                K[y, x] *= np.exp(sgn * hh)
+                vals.append(_oracle_objective(oracle_mod, w, steps, objective, K=K))
+            else:
+                tw = w.wall_T_left.copy()
+                tw[y] += sgn * hh
+                vals.append(_oracle_objective(oracle_mod, w, steps, objective, tw=tw))
+        return (vals[0] - vals[1]) / (2 * hh)
+
+    worst, checked = {}, {}
+    for name, grad in (("phi", dphi), ("lnK", dlnK)):
+        big = np.abs(grad) >= 0.05 * np.abs(grad).max()
+        cand = np.argwhere((fl_end > 0.05) & (fl_end < 0.95) & big)
+        assert len(cand) >= 8, (name, len(cand))
+        cells = cand[rng.choice(len(cand), size=min(16, len(cand)), replace=False)]
+        for (y, x) in cells:
+            fd1, fd2 = cd(name, y, x, h), cd(name, y, x, 2 * h)
+            err = (abs(grad[y, x] - fd1) - 2 * abs(fd1 - fd2)) / abs(fd1)
+            worst[name] = max(worst.get(name, -1.0), err)
+        checked[name] = len(cells)
+    for y in rng.choice(np.arange(1, w.ny - 1), size=4, replace=False):
+        fd1, fd2 = cd("Tw", y, 0, h), cd("Tw", y, 0, 2 * h)
+        err = (abs(dtw[y] - fd1) - 2 * abs(fd1 - fd2)) / abs(fd1)
+        worst["Tw"] = max(worst.get("Tw", -1.0), err)
+    print("cells checked", checked, "worst gap beyond the differences' noise, relative:", worst)
     for name, err in worst.items():
         assert err < TOL, (name, err, worst)
 

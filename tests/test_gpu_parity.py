@@ -166,6 +166,33 @@ def test_parity_cavity_10000_steps(lbm, oracle_mod):
     assert abs(r_g["nu_hot"] / r_o["nu_hot"] - 1) < 1e-4
 
 
+def _front(fl):
+    """Melted length per row: sum over x of f_l (the row's front position)."""
+    return fl.sum(axis=1)
+
+
+def test_convection_cavity_config2(lbm, oracle_mod):
+    """Convection melting in the uniform porous cavity (256^2, phi = 0.4,
+    Da = 1e-4, Ra = 1e5, Pr = 1, Ste = 1): u, T and f_l within 1e-4 of the
+    oracle after 2,000 steps; then on the GPU alone to 50,000 steps, where the
+    front leans: liquid heated at the left wall rises and spreads under the
+    top wall, so the top rows melt further than the bottom rows."""
+    w = _f32(W.convection_cavity(256))
+    steps = 2000
+    lat = _gpu(lbm, w, steps)
+    o = _ora(oracle_mod, w, steps)
+    err = _errors(lat.macros(), o.macros())
+    assert max(err.values()) < 1e-4, err
+    lat.step(50000 - steps)
+    assert lat.status() == 0
+    fl = lat.macros()["fl"]
+    x = _front(fl[1:-1, :])                 # interior rows, bottom to top
+    q = len(x) // 4
+    top, bottom = x[-q:].mean(), x[:q].mean()
+    assert top > bottom + 2.0, (top, bottom)
+    assert np.all(np.diff(x[q:-q]) > -0.5)   # the lean is monotone away from the walls
+
+
 def test_porous_gallium_cavity_matches_oracle(lbm, oracle_mod):
     """Sec. 4.3's parameter set (200^2, Ra = 8.409e5, Pr = 0.0208,
     tau_nu = 0.5054, St = 0.1241): u, T and f_l within 1e-4 of the FP64
@@ -181,6 +208,50 @@ def test_porous_gallium_cavity_matches_oracle(lbm, oracle_mod):
     assert r_o["melt_frac"] > 0.005   # the front has left the wall
     assert abs(r_g["melt_frac"] / r_o["melt_frac"] - 1) < 1e-4
     assert abs(r_g["nu_hot"] / r_o["nu_hot"] - 1) < 1e-4
+
+
+@pytest.mark.parametrize("sigma_s", [0.5, 2.0])
+def test_solid_heat_capacity_slab_matches_oracle(lbm, oracle_mod, sigma_s):
+    """Eq. (7) with sigma_s != sigma_l (sigma linear in f_l, taken at f_l(n) in
+    tau_T, n^eq and the latent coefficient) on the Sec. 4.1 slab, 20,000 steps:
+    T within 2e-4 of the oracle (the solid's slow diffusion from T_i = -1
+    accumulates FP32 rounding, as with the two-phase diffusivity), f_l within
+    1e-3 and the front within 0.01 node."""
+    w = _f32(W.two_phase_slab(1.0))
+    w.params = {**w.params, "sigma_solid": sigma_s}
+    steps = 20000
+    got = _gpu(lbm, w, steps).macros()
+    exp = _ora(oracle_mod, w, steps).macros()
+    err = _errors(got, exp, ("T", "fl"))
+    assert err["T"] < 2e-4 and err["fl"] < 1e-3, err
+    xm = lambda fl: 0.5 * fl.mean(axis=0)[0] + fl.mean(axis=0)[1:].sum()
+    assert abs(xm(got["fl"]) - xm(exp["fl"])) < 0.01
+
+
+def test_solid_heat_capacity_with_flow(lbm, oracle_mod):
+    """sigma(f_l) of Eq. (7) in the melted cavity (flow, TMA-staged kernel)."""
+    w = _f32(W.melted_cavity(64))
+    w.params = {**w.params, "sigma_solid": 0.5}
+    lat = _gpu(lbm, w, 51)
+    assert lat.kernel_variant() == 2
+    o = _ora(oracle_mod, w, 51)
+    err = _errors(lat.macros(), o.macros())
+    assert max(err.values()) < 2e-5, err
+    rg, ro = lat.reduce(), o.reduce()
+    assert abs(rg["enthalpy"] - ro["enthalpy"]) <= 1e-5 * abs(ro["enthalpy"])
+
+
+def test_porous_gallium_cavity_with_solid_sigma(lbm, oracle_mod):
+    """Sec. 4.3 with the paper's two heat-capacity ratios (0.8604 liquid,
+    0.8352 solid, Eq. (7)): 4,000 steps within 1e-4 of the oracle."""
+    w = _f32(W.porous_gallium_cavity(200, solid_sigma=True))
+    steps = 4000
+    lat = _gpu(lbm, w, steps)
+    o = _ora(oracle_mod, w, steps)
+    err = _errors(lat.macros(), o.macros())
+    assert max(err.values()) < 1e-4, err
+    r_g, r_o = lat.reduce(), o.reduce()
+    assert abs(r_g["melt_frac"] / r_o["melt_frac"] - 1) < 1e-4
 
 
 def test_full_size_cavity_matches_oracle(lbm, oracle_mod):
