@@ -439,6 +439,7 @@ def adjoint_coupled(args, torch):
         t0 = time.perf_counter()
         J, dphi, dlnK, dtw = lat.adjoint_coupled(args.steps, args.objective, args.checkpoint)
         ms_adj = (time.perf_counter() - t0) * 1e3
+    ph_fwd, ph_rev = lat.adjoint_timing()
     if keep_all:
         memory = "every state kept (%.2f GB)" % ((args.steps + 1) * st_bytes / 1e9)
     else:
@@ -456,6 +457,8 @@ def adjoint_coupled(args, torch):
         "forward": {"ms": ms_fwd, "MLUPS": n * args.steps / (ms_fwd * 1e-3) / 1e6,
                     "timing": "CUDA events on the lattice's stream (CUDA graphs)"},
         "adjoint": {"ms": ms_adj, "timing": "host wall clock around lbm_adjoint_coupled",
+                    "device_ms_forward_run": ph_fwd, "device_ms_reverse_sweep": ph_rev,
+                    "reverse_over_forward": ph_rev / ms_fwd,
                     "J": J, "dJ_dlnK_max": float(abs(dlnK).max()),
                     "dJ_dphi_max": float(abs(dphi).max()),
                     "dJ_dTw_max": float(abs(dtw).max())},

@@ -221,6 +221,12 @@ int lbm_autotune(lbm_ctx* c, int trial_steps, int32_t* variant, int32_t* tiles_p
 int lbm_adjoint_melt(lbm_ctx* c, int64_t nsteps, int32_t checkpoint_every, int32_t mu_sweeps,
                      float* d_phi, float* d_wall_T_left, double* J, int device_ptrs);
 
+/* Device time (CUDA events on the context stream, ms) of the last adjoint call
+ * on this context (lbm_adjoint, lbm_adjoint_melt or lbm_adjoint_coupled):
+ * ms[0] its forward run with the saves it makes, ms[1] its reverse sweep
+ * (recomputation of checkpointed segments included); zeros before the first. */
+int lbm_adjoint_timing(const lbm_ctx* c, double ms[2]);
+
 /* Objectives of lbm_adjoint. */
 enum { LBM_OBJ_MELT = 0, LBM_OBJ_NUSSELT = 1 };
 

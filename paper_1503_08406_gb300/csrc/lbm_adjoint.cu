@@ -83,11 +83,8 @@ __global__ void adj_list_kernel(Dev d, const float* f, int* list, int* count) {
 
 // The fixed point's adjoint on the band: right-hand side
 // lam_f'(y) - a(y) sum_i w~_i lam_g'_i(y + e_i), then Jacobi sweeps with the
-// self term exact until no node changes by more than MU_RTOL of its value or
-// after max_sweeps.  The sweeps start from mu of the step reversed before this
-// one (b.muw; zero on nodes that were not in its band): the front moves little
-// from step to step, so that is close to this step's solution, and the fixed
-// point does not depend on where the sweeps start.  Up to BAND_CAP band nodes sweep in shared
+// self term exact, from mu = 0, until no node changes by more than MU_RTOL of
+// its value or after max_sweeps.  Up to BAND_CAP band nodes sweep in shared
 // memory (each node's coefficients and its neighbours' places in the list
 // staged once); a wider band sweeps in global memory.  Jacobi makes the
 // result independent of the list's order.  Empties the previous band's list
@@ -151,7 +148,7 @@ __global__ void __launch_bounds__(BAND_THREADS) adj_band_kernel(Dev d, AdjBuffer
       const float den = 1.f - as * (1.f - d.wt0) / (d.dTt + as);
       rhs[j] = band_rhs(d, b, s) / den;
       kk[j] = as * d.wt1 / den;
-      mu[j] = b.muw[s];
+      mu[j] = 0.f;
     }
     __syncthreads();
     for (int k = 0; k < max_sweeps; ++k) {
@@ -172,7 +169,6 @@ __global__ void __launch_bounds__(BAND_THREADS) adj_band_kernel(Dev d, AdjBuffer
     }
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
       const int s = list[j];
-      b.muw[s] = mu[j];
       add_nu(d, b, s, mu[j] / (d.dTt + b.a[s]));
     }
   } else {
@@ -182,7 +178,7 @@ __global__ void __launch_bounds__(BAND_THREADS) adj_band_kernel(Dev d, AdjBuffer
       const int s = list[j];
       const float as = b.a[s];
       b.rhs[s] = band_rhs(d, b, s) / (1.f - as * (1.f - d.wt0) / (d.dTt + as));
-      mu[s] = b.muw[s];
+      mu[s] = 0.f;
     }
     __syncthreads();
     for (int k = 0; k < max_sweeps; ++k) {
@@ -209,7 +205,6 @@ __global__ void __launch_bounds__(BAND_THREADS) adj_band_kernel(Dev d, AdjBuffer
     }
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
       const int s = list[j];
-      b.muw[s] = mu[s];
       add_nu(d, b, s, mu[s] / (d.dTt + b.a[s]));
     }
   }
@@ -380,7 +375,7 @@ void adj_objective(const Dev& d, const float* fl, double* out, cudaStream_t s) {
 
 // One reversed coupled step (flow on): lbm::coupled_reverse_node per node,
 // rows along blockIdx.y.
-__global__ void __launch_bounds__(128) adj_coupled_kernel(CoupledStep<float> A) {
+__global__ void __launch_bounds__(128, 6) adj_coupled_kernel(CoupledStep<float> A) {
   const int x = blockIdx.x * 128 + threadIdx.x;
   if (x >= A.geo.nx) return;
   for (int y = blockIdx.y; y < A.geo.ny; y += gridDim.y) coupled_reverse_node(A, x, y);

@@ -13,8 +13,6 @@ struct AdjBuffers {
   float* rhs;        // band nodes (wide bands): right-hand side of mu's equation
   float* mu0;        // mu in global memory (wide bands), ping-pong
   float* mu1;
-  float* muw;        // mu of the last reversed step per node (zero at the start of the sweep):
-                     // the next step's band solve starts from it
   float* lamgpre;    // 5 n: adjoint of the populations before the step
   float* lama;       // accumulated adjoint of a
   float* lamtw;      // ny: accumulated adjoint of the left wall profile

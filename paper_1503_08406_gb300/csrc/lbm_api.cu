@@ -39,6 +39,7 @@ struct lbm_ctx {
   bool graphs_off;
   int64_t launches;                // kernels launched by lbm_step
   int64_t since_check;             // steps since the last NaN/Inf sentinel
+  double adj_ms[2];                // last adjoint call: forward run, reverse sweep (device ms)
   lbm::TmaMaps maps;               // tensor maps of the TMA-staged fused kernel
   bool use_tma;
   bool tma_ok;                     // the lattice qualifies for the TMA-staged kernel
@@ -944,6 +945,13 @@ int lbm_set_state(lbm_ctx* c, const float* f, const float* g, const float* fl, i
   return LBM_OK;
 }
 
+int lbm_adjoint_timing(const lbm_ctx* c, double ms[2]) {
+  if (!c || !ms) return LBM_ERR_INVALID_ARG;
+  ms[0] = c->adj_ms[0];
+  ms[1] = c->adj_ms[1];
+  return LBM_OK;
+}
+
 int lbm_timing(lbm_ctx* c, int enable) {
   if (!c) return LBM_ERR_INVALID_ARG;
   LBM_CUDA(cudaStreamSynchronize(c->stream));
@@ -982,6 +990,35 @@ int lbm_timing_read(lbm_ctx* c, double ms[4], int64_t* steps_timed, int64_t* til
 // ---- adjoint of the conduction step ------------------------------------------------
 
 namespace {
+
+// CUDA events bracketing the phases of one adjoint call on the context
+// stream; their times land in c->adj_ms when it returns
+struct PhaseEvents {
+  lbm_ctx* c;
+  cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+  explicit PhaseEvents(lbm_ctx* ctx) : c(ctx) {
+    for (cudaEvent_t& x : e)
+      if (cudaEventCreate(&x) != cudaSuccess) {
+        cudaGetLastError();
+        x = nullptr;
+      }
+  }
+  void mark(int k) {
+    if (e[k]) cudaEventRecord(e[k], c->stream);
+  }
+  ~PhaseEvents() {
+    float a = 0.f, b = 0.f;
+    if (e[0] && e[1] && e[2] && cudaEventSynchronize(e[2]) == cudaSuccess &&
+        cudaEventElapsedTime(&a, e[0], e[1]) == cudaSuccess &&
+        cudaEventElapsedTime(&b, e[1], e[2]) == cudaSuccess) {
+      c->adj_ms[0] = a;
+      c->adj_ms[1] = b;
+    }
+    cudaGetLastError();
+    for (cudaEvent_t x : e)
+      if (x) cudaEventDestroy(x);
+  }
+};
 
 // device buffers of one adjoint run, freed on scope exit
 struct DevMem {
@@ -1105,7 +1142,6 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
   b.rhs = mem.get(n);
   b.mu0 = mem.get(n);
   b.mu1 = mem.get(n);
-  b.muw = mem.get(n);
   b.lamgpre = mem.get(5 * n);
   b.lama = mem.get(n);
   b.lamtw = mem.get((size_t)c->d.ny);
@@ -1116,7 +1152,7 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
   double* nu_acc = reinterpret_cast<double*>(mem.get(2));
   double* dJ = reinterpret_cast<double*>(mem.get(2 * 129));
   if (!flS || (!keep_all && (!cps || !fin)) || !b.a || !b.lamg || !b.lamf || !b.rhs ||
-      !b.mu0 || !b.mu1 || !b.muw || !b.lamgpre || !b.lama || !b.lamtw || !b.pos || !lists[0] ||
+      !b.mu0 || !b.mu1 || !b.lamgpre || !b.lama || !b.lamtw || !b.pos || !lists[0] ||
       !lists[1] || !counts || !ctr || !nu_acc || !dJ)
     return LBM_ERR_OOM;
   // transposed collision matrix with u = 0: g+ = A g,
@@ -1156,6 +1192,8 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
   HookGraphs fwd_graphs;
   const int64_t steps0 = c->steps;
   lbm::adj_seed(c->d, b.lamf, b.lamg, b.a, melt, nu, c->stream);   // a is needed from here on
+  PhaseEvents ph(c);
+  ph.mark(0);
   LBM_CUDA(cudaMemsetAsync(nu_acc, 0, sizeof(double), c->stream));
   double* const acc = melt ? nullptr : nu_acc;
   if (keep_all) {
@@ -1182,9 +1220,9 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
   }
   const float* fl_end = keep_all ? flS + (size_t)nsteps * n : fin + 5 * n;
   if (melt) lbm::adj_objective(c->d, fl_end, dJ, c->stream);
+  ph.mark(1);
   // reverse sweep
   LBM_CUDA(cudaMemsetAsync(b.lama, 0, n * sizeof(float), c->stream));
-  LBM_CUDA(cudaMemsetAsync(b.muw, 0, n * sizeof(float), c->stream));
   LBM_CUDA(cudaMemsetAsync(b.lamtw, 0, c->d.ny * sizeof(float), c->stream));
   LBM_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(int), c->stream));
   lbm::adj_list(c->d, fl_end, lists[0], counts, c->stream);
@@ -1271,6 +1309,7 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
     c->steps = steps0 + nsteps;
   }
   LBM_CUDA(cudaGetLastError());
+  ph.mark(2);
   // d J / d phi = (dT / (sigma St)) d J / d a, straight into the caller's arrays
   lbm::adj_scale((long long)n, b.lama, c->d.lat, c->stream);
   const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -1329,7 +1368,6 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
   b.rhs = mem.get(n);
   b.mu0 = mem.get(n);
   b.mu1 = mem.get(n);
-  b.muw = mem.get(n);
   b.lama = mem.get(n);   // adjoint of phi
   b.lamtw = mem.get((size_t)d.ny);
   b.pos = reinterpret_cast<int*>(mem.get(n));
@@ -1339,7 +1377,7 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
   double* nu_acc = reinterpret_cast<double*>(mem.get(2));
   unsigned* ctr = reinterpret_cast<unsigned*>(mem.get(2));
   if (!S || (!keep_all && (!cps || !fin)) || !lf[0] || !lf[1] || !lg[0] || !lg[1] || !b.a ||
-      !b.lamf || !b.rhs || !b.mu0 || !b.mu1 || !b.muw || !b.lama || !b.lamtw || !b.pos || !lK ||
+      !b.lamf || !b.rhs || !b.mu0 || !b.mu1 || !b.lama || !b.lamtw || !b.pos || !lK ||
       !lists[0] || !lists[1] || !counts || !nu_acc || !ctr)
     return LBM_ERR_OOM;
   // rows of the Nusselt number (lbm_reduce's): all but horizontal wall rows
@@ -1349,6 +1387,8 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
   HookGraphs fwd_graphs;
   Hooks h;
   h.nu_acc = melt ? nullptr : nu_acc;
+  PhaseEvents ph(c);
+  ph.mark(0);
   LBM_CUDA(cudaMemsetAsync(nu_acc, 0, sizeof(double), c->stream));
   auto save = [&](float* dst) -> int {   // the whole state, natural layout
     lbm::launch_keep_state(c->d, c->parity, dst, nullptr, c->stream);
@@ -1373,6 +1413,7 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
     LBM_TRY(save(fin));
   }
   LBM_CUDA(cudaGetLastError());
+  ph.mark(1);
   const float* last = keep_all ? S + (size_t)nsteps * st : fin;
   // objective and seeds (host side: small arrays)
   std::vector<float> hfl(n), seedf(n, 0.f), seedg(5 * n, 0.f);
@@ -1412,7 +1453,6 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
                            c->stream));
   LBM_CUDA(cudaMemsetAsync(lf[0], 0, 9 * n * sizeof(float), c->stream));
   LBM_CUDA(cudaMemsetAsync(b.lama, 0, n * sizeof(float), c->stream));
-  LBM_CUDA(cudaMemsetAsync(b.muw, 0, n * sizeof(float), c->stream));
   LBM_CUDA(cudaMemsetAsync(lK, 0, n * sizeof(float), c->stream));
   LBM_CUDA(cudaMemsetAsync(b.lamtw, 0, d.ny * sizeof(float), c->stream));
   LBM_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(int), c->stream));
@@ -1560,6 +1600,7 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
     LBM_TRY(lbm_set_state(c, fin, fin + 9 * n, fin + 14 * n, 1));
     c->steps = steps0 + nsteps;
   }
+  ph.mark(2);
   // d J / d ln K = K d J / d K, then straight into the caller's arrays
   lbm::adj_mul((long long)n, lK, d.K, c->stream);
   const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;

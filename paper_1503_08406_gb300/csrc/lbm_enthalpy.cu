@@ -35,6 +35,8 @@
 // every changed node to the five populations it reaches, and, before an odd
 // step, swap the two slots of every flow link whose "both ends carry flow"
 // state changed, so the AA layout matches the new flow mask.
+#include <type_traits>
+
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -52,25 +54,40 @@ __device__ __forceinline__ bool solved(const Dev& d, int tile, int stamp) {
   return (d.proc[tile] >> 3) == stamp;
 }
 
-// T* at node (x, y) from the populations after the step: natural layout
-// (layout 0) or swapped (layout 1, population i of x sits in x - e_i).
-__device__ __forceinline__ float tstar(const Dev& d, int x, int y, int layout) {
+// T* at node (x, y) from the populations after the step, stored as S:
+// natural layout (layout 0) or swapped (layout 1, population i of x sits in
+// x - e_i).  Neighbours one step away (xm, xp, ym, yp) wrap once at most.
+template <typename S>
+__device__ __forceinline__ float tstar_t(const Dev& d, int s, int xm, int xp, int ym, int yp,
+                                         int x, int y, int layout) {
   const int n = (int)d.n;
-  const int s = y * d.nx + x;
+  const S* G = static_cast<const S*>(d.g);
   // the stored g deviations add up to T* - T_m (the weights sum to 1)
-  const float ref = d.storage ? d.g_ref : 0.f;
-  const void* G = d.g;
+  const float ref = std::is_same<S, float>::value ? 0.f : d.g_ref;
   if (layout == 0)
-    return ld_pop(d, G, s) + ld_pop(d, G, n + s) + ld_pop(d, G, 2 * n + s) +
-           ld_pop(d, G, 3 * n + s) + ld_pop(d, G, 4 * n + s) + ref;
-  const int xm = (x == 0) ? d.nx - 1 : x - 1, xp = (x == d.nx - 1) ? 0 : x + 1;
-  const int ym = (y == 0) ? d.ny - 1 : y - 1, yp = (y == d.ny - 1) ? 0 : y + 1;
-  return ld_pop(d, G, s) + ld_pop(d, G, 3 * n + y * d.nx + xm) +
-         ld_pop(d, G, 4 * n + ym * d.nx + x) + ld_pop(d, G, 1 * n + y * d.nx + xp) +
-         ld_pop(d, G, 2 * n + yp * d.nx + x) + ref;
+    return Pop<S>::ld(G + s) + Pop<S>::ld(G + n + s) + Pop<S>::ld(G + 2 * n + s) +
+           Pop<S>::ld(G + 3 * n + s) + Pop<S>::ld(G + 4 * n + s) + ref;
+  return Pop<S>::ld(G + s) + Pop<S>::ld(G + 3 * n + y * d.nx + xm) +
+         Pop<S>::ld(G + 4 * n + ym * d.nx + x) + Pop<S>::ld(G + n + y * d.nx + xp) +
+         Pop<S>::ld(G + 2 * n + yp * d.nx + x) + ref;
 }
 
-template <int PAR>
+// bar.sync / bar.red.or on named barrier 1 over the first `threads` threads
+__device__ __forceinline__ void sub_sync(int threads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(threads) : "memory");
+}
+__device__ __forceinline__ bool sub_sync_or(int threads, bool v) {
+  unsigned r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((unsigned)v), "r"(threads)
+      : "memory");
+  return r != 0;
+}
+
+template <int PAR, typename S>
 __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
   constexpr int LAYOUT = 1 - PAR;
   extern __shared__ float smem[];
@@ -88,26 +105,50 @@ __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
   for (int li = blockIdx.x; li < cnt; li += gridDim.x) {
     const int tile = d.list[PAR * d.ntiles + li];
     const int X0 = (tile % d.etx) * TE, Y0 = (tile / d.etx) * TE;
+    // a region (tile and halo) inside the wall ring needs no wrapping and holds
+    // no wall node: its loads go straight to their addresses
+    const bool inner = X0 - RH >= 1 && X0 + TE + RH <= d.nx - 1 && Y0 - RH >= 1 &&
+                       Y0 + TE + RH <= d.ny - 1;
+    if (inner) {
 #pragma unroll 3
-    for (int k = tid; k < RE * RE; k += EB) {
-      const int ly = k / RE, lx = k - ly * RE;
-      const int gx = wrapx(d, X0 - RH + lx), gy = wrapy(d, Y0 - RH + ly);
-      float base = 0.f, inv = 0.f, a = 0.f, fn = 0.f;
-      if (gx >= 0 && gy >= 0) {
+      for (int k = tid; k < RE * RE; k += EB) {
+        const int ly = k / RE, lx = k - ly * RE;
+        const int gx = X0 - RH + lx, gy = Y0 - RH + ly;
         const int s = gy * d.nx + gx;
-        fn = d.fl[s];
-        if (!is_wall(d, gx, gy)) {
-          a = d.phi[s] * d.lat * sigma_ratio(d, fn);   // phi dT / (sigma(f_l(n)) St)
-          base = tstar(d, gx, gy, LAYOUT) + w0 * a * fn - Ts;
-          inv = 1.f / (dTt + w0 * a);
-        }
+        const float fn = d.fl[s];
+        const float a = d.phi[s] * d.lat * sigma_ratio(d, fn);   // phi dT / (sigma(f_l(n)) St)
+        const float T = tstar_t<S>(d, s, gx - 1, gx + 1, gy - 1, gy + 1, gx, gy, LAYOUT);
+        sbase[k] = T + w0 * a * fn - Ts;
+        sinv[k] = 1.f / (dTt + w0 * a);
+        sa[k] = a;
+        sfn[k] = fn;
+        sq[k] = 0.f;
+        sf[k] = fn;
       }
-      sbase[k] = base;
-      sinv[k] = inv;
-      sa[k] = a;
-      sfn[k] = fn;
-      sq[k] = 0.f;
-      sf[k] = fn;
+    } else {
+#pragma unroll 3
+      for (int k = tid; k < RE * RE; k += EB) {
+        const int ly = k / RE, lx = k - ly * RE;
+        const int gx = wrapx(d, X0 - RH + lx), gy = wrapy(d, Y0 - RH + ly);
+        float base = 0.f, inv = 0.f, a = 0.f, fn = 0.f;
+        if (gx >= 0 && gy >= 0) {
+          const int s = gy * d.nx + gx;
+          fn = d.fl[s];
+          if (!is_wall(d, gx, gy)) {
+            a = d.phi[s] * d.lat * sigma_ratio(d, fn);   // phi dT / (sigma(f_l(n)) St)
+            const int xm = (gx == 0) ? d.nx - 1 : gx - 1, xp = (gx == d.nx - 1) ? 0 : gx + 1;
+            const int ym = (gy == 0) ? d.ny - 1 : gy - 1, yp = (gy == d.ny - 1) ? 0 : gy + 1;
+            base = tstar_t<S>(d, s, xm, xp, ym, yp, gx, gy, LAYOUT) + w0 * a * fn - Ts;
+            inv = 1.f / (dTt + w0 * a);
+          }
+        }
+        sbase[k] = base;
+        sinv[k] = inv;
+        sa[k] = a;
+        sfn[k] = fn;
+        sq[k] = 0.f;
+        sf[k] = fn;
+      }
     }
     __syncthreads();
     // Nodes whose update is clamped whatever their neighbours do are fixed now
@@ -169,9 +210,13 @@ __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
     const int ncol = sbox[1] >= lx0 ? (sbox[1] - lx0 + 2) >> 1 : 0;   // per colour and row
     const int nbox = ncol * (sbox[3] - ly0 + 1);
     const float inv_ncol = ncol ? 1.f / (float)ncol : 0.f;
+    // the sweeps run on as many whole warps as one colour of the box needs;
+    // the other warps wait at the barrier after them
+    const int sw = min(EB, (nbox + 31) & ~31);
     int it = 0;
-    bool more = true;
-    int polish = 2;   // extra sweeps after the stop test passes
+    bool more = sw > 0;   // (nothing left to sweep: solved by the fixing pass)
+    int polish = more ? 2 : 0;   // extra sweeps after the stop test passes
+    if (tid < sw)
     for (; it < d.max_inner && (more || polish > 0); ++it) {
       if (!more) --polish;
       // over-relaxed for the first sweeps, then plain Gauss-Seidel: at the last
@@ -207,11 +252,12 @@ __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
           sq[k] = a * (v - sfn[k]);
         }
         // the second colour's barrier also collects the convergence vote
-        if (color == 0) __syncthreads();
+        if (color == 0) sub_sync(sw);
       }
-      const bool c = __syncthreads_or(changed);
+      const bool c = sub_sync_or(sw, changed);
       if (more) more = c;
     }
+    __syncthreads();
     bool fchg = false, achg = false;
     for (int k = tid; k < TE * TE; k += EB) {
       const int ly = k / TE, lx = k - ly * TE;
@@ -357,16 +403,32 @@ __global__ void __launch_bounds__(CB) enthalpy_commit_kernel(Dev d) {
 
 size_t enthalpy_solve_smem() { return 6 * RE * RE * sizeof(float); }
 
+template <typename S>
+static void solve_setup_t(int bytes) {
+  cudaFuncSetAttribute(enthalpy_solve_kernel<0, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       bytes);
+  cudaFuncSetAttribute(enthalpy_solve_kernel<1, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       bytes);
+}
+
 void enthalpy_setup() {
   const int bytes = (int)enthalpy_solve_smem();
-  cudaFuncSetAttribute(enthalpy_solve_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(enthalpy_solve_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  solve_setup_t<float>(bytes);
+  solve_setup_t<__half>(bytes);
+  solve_setup_t<__nv_bfloat16>(bytes);
+}
+
+template <typename S>
+static void launch_solve_t(const Dev& d, int parity, cudaStream_t s) {
+  const size_t sm = enthalpy_solve_smem();
+  if (parity == 0) enthalpy_solve_kernel<0, S><<<d.egrid, EB, sm, s>>>(d);
+  else enthalpy_solve_kernel<1, S><<<d.egrid, EB, sm, s>>>(d);
 }
 
 void launch_enthalpy_solve(const Dev& d, int parity, cudaStream_t s) {
-  const size_t sm = enthalpy_solve_smem();
-  if (parity == 0) enthalpy_solve_kernel<0><<<d.egrid, EB, sm, s>>>(d);
-  else enthalpy_solve_kernel<1><<<d.egrid, EB, sm, s>>>(d);
+  if (d.storage == 1) launch_solve_t<__half>(d, parity, s);
+  else if (d.storage == 2) launch_solve_t<__nv_bfloat16>(d, parity, s);
+  else launch_solve_t<float>(d, parity, s);
 }
 
 void launch_enthalpy_commit(const Dev& d, int parity, cudaStream_t s) {

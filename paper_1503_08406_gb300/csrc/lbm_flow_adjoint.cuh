@@ -442,6 +442,11 @@ LBM_HD bool coupled_active(const CoupledStep<R>& A, int s) {
   const int y = s / A.geo.nx, x = s - y * A.geo.nx;
   return A.flow && !A.geo.wall(x, y) && A.fl0[s] >= A.f_act;
 }
+// the same for node s at (x, y), known already (no division)
+template <typename R>
+LBM_HD bool coupled_active_xy(const CoupledStep<R>& A, int x, int y, int s) {
+  return A.flow && !A.geo.wall(x, y) && A.fl0[s] >= A.f_act;
+}
 
 // lam_g+ of node (x, y) streamed back from lg1 (0 from outside the lattice)
 template <typename R>
@@ -460,7 +465,10 @@ LBM_HD void coupled_reverse_node(const CoupledStep<R>& A, int x, int y) {
   const long long n = A.n;
   const int s = y * G.nx + x;
   const bool wall = G.wall(x, y);
-  const bool act = coupled_active(A, s);
+  const bool act = coupled_active_xy(A, x, y, s);
+  // a node two or more nodes away from every wall is nobody's inward node
+  const bool near_wall = (!G.per_x && (x <= 1 || x >= G.nx - 2)) ||
+                         (!G.per_y && (y <= 1 || y >= G.ny - 2));
   R g[5], T = 0;
   for (int i = 0; i < 5; ++i) T += (g[i] = A.g0[i * n + s]);
   R f[9], ux = 0, uy = 0;
@@ -505,7 +513,7 @@ LBM_HD void coupled_reverse_node(const CoupledStep<R>& A, int x, int y) {
     // the extrapolation of every wall node whose inward node this is
     const int ex9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     const int ey9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-    for (int d = 1; d < 9; ++d) {
+    for (int d = 1; d < 9 && near_wall; ++d) {
       const int bx = x + ex9[d], by = y + ey9[d];
       if (bx < 0 || bx >= G.nx || by < 0 || by >= G.ny) continue;
       if (!G.wall(bx, by) || G.inward(bx, by) != s) continue;
@@ -551,7 +559,15 @@ LBM_HD void coupled_reverse_node(const CoupledStep<R>& A, int x, int y) {
     R lpost[9], lfin[9], lT, lflv, lphiv, lKv;
     for (int j = 0; j < 9; ++j) {
       const int t = G.nb(x, y, ex9[j], ey9[j]);
-      lpost[j] = (t >= 0 && coupled_active(A, t)) ? A.lf1[j * n + t] : A.lf1[op9[j] * n + s];
+      bool on = t >= 0;
+      if (on) {
+        // (x + e_j, y + e_j) wrapped, without dividing t by nx
+        int tx = x + ex9[j], ty = y + ey9[j];
+        tx = tx < 0 ? tx + G.nx : (tx >= G.nx ? tx - G.nx : tx);
+        ty = ty < 0 ? ty + G.ny : (ty >= G.ny ? ty - G.ny : ty);
+        on = coupled_active_xy(A, tx, ty, t);
+      }
+      lpost[j] = on ? A.lf1[j * n + t] : A.lf1[op9[j] * n + s];
     }
     flow_node_adjoint(A.fp, f, T, A.fl0[s], A.phi[s], A.K[s], lpost, lux, luy, lfin, &lT, &lflv,
                       &lphiv, &lKv);

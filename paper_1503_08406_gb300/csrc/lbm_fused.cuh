@@ -171,7 +171,7 @@ __device__ __forceinline__ Geo node_geo(const Dev& d, int x, int y) {
 // populations reflected at each link, used where the neighbour carries no
 // flow.  Writes the post-collision populations to their AA slots and returns
 // whether the node fails the phase-change screen.
-template <typename S, int PAR, bool FLOW>
+template <typename S, int PAR, bool FLOW, bool EDGE = true>
 __device__ __forceinline__ bool node_update(const Dev& d, int x, int y, const Geo& q,
                                             const float fln[9], const float gin[5], float f[9],
                                             const float fb[9], float phi, float K) {
@@ -338,10 +338,12 @@ __device__ __forceinline__ bool node_update(const Dev& d, int x, int y, const Ge
     cold = cold && (w <= d.wt1 * (d.T_s + d.scr_T));                              \
     hot = hot && (w >= d.wt1 * (d.T_l - d.scr_T));                                \
   }
-  LBM_WALL_POP(d.wall_l && x == 1, 1, sW, d.bc[0] == 1 ? d.wallTl[y] : T, ux)
-  LBM_WALL_POP(d.wall_r && x == nx - 2, 3, sE, d.bc[1] == 1 ? d.Tbc[1] : T, -ux)
-  LBM_WALL_POP(d.wall_b && y == 1, 2, sS, d.bc[2] == 1 ? d.Tbc[2] : T, uy)
-  LBM_WALL_POP(d.wall_t && y == ny - 2, 4, sN, d.bc[3] == 1 ? d.Tbc[3] : T, -uy)
+  if (EDGE) {   // (a node of an interior tile has no wall neighbour)
+    LBM_WALL_POP(d.wall_l && x == 1, 1, sW, d.bc[0] == 1 ? d.wallTl[y] : T, ux)
+    LBM_WALL_POP(d.wall_r && x == nx - 2, 3, sE, d.bc[1] == 1 ? d.Tbc[1] : T, -ux)
+    LBM_WALL_POP(d.wall_b && y == 1, 2, sS, d.bc[2] == 1 ? d.Tbc[2] : T, uy)
+    LBM_WALL_POP(d.wall_t && y == ny - 2, 4, sN, d.bc[3] == 1 ? d.Tbc[3] : T, -uy)
+  }
 #undef LBM_WALL_POP
 
   const bool unsafe = d.screen_off || !(cold || hot);
@@ -548,6 +550,67 @@ __device__ __forceinline__ void tma_issue(const TmaMaps& m, unsigned buf, unsign
   }
 }
 
+// The update of node (x0 + lane, y0 + ty) of a tile staged in buffer sb.
+// EDGE = false: the tile has no wall node and no neighbour of a wall node.
+template <typename S, int PAR, bool FLOW, bool EDGE>
+__device__ __forceinline__ bool tma_node(const Dev& d, const unsigned char* sb, int x0, int y0,
+                                         int lane, int ty) {
+  using L = TmaLayout<PAR, S>;
+  const int nx = d.nx, ny = d.ny;
+  const int x = x0 + lane, y = y0 + ty;
+  bool unsafe = false;
+  if (!EDGE || (x < nx && y < ny && !is_wall(d, x, y))) {
+      Geo q = node_geo_walled(d, x, y);
+      if (!EDGE)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) q.wl[i] = false;
+      const S* sF = reinterpret_cast<const S*>(sb + L::F_OFF);
+      const S* sG = reinterpret_cast<const S*>(sb + L::G_OFF);
+      const float r0 = d.wt0 * d.g_ref, r1 = d.wt1 * d.g_ref;
+      const float* sFL = reinterpret_cast<const float*>(sb + L::FL_OFF);
+      // f_l of the 3x3 neighbourhood from the halo window (origin x0 - 4, y0 - 1);
+      // all four sides are walls, so every neighbour of a non-wall node is in it
+      const int c = (ty + HY) * WX + (lane + HX);
+      float fln[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) fln[i] = q.wl[i] ? -1.f : sFL[c + ey9(i) * WX + ex9(i)];
+      constexpr int PX = L::PX, PP = L::PX * L::PY;
+      const int pc = PAR ? (ty + HY) * PX + (lane + L::HS) : ty * PX + lane;
+      float g[5];
+      if (PAR == 0) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) g[i] = gload(&sG[i * PP + pc], i ? r1 : r0);
+      } else {
+        g[0] = gload(&sG[pc], r0);
+#pragma unroll
+        for (int i = 1; i < 5; ++i) {
+          const int o = opp5(i);   // from the source node x - e_i = x + e_o, its slot o
+          g[i] = gload(&sG[o * PP + pc + ey9(o) * PX + ex9(o)], r1);
+        }
+      }
+      float f[9], fb[9];
+      float phi = 0.f, K = 1.f;
+      if (FLOW) {
+        phi = reinterpret_cast<const float*>(sb + L::PHI_OFF)[ty * TX + lane];
+        K = reinterpret_cast<const float*>(sb + L::K_OFF)[ty * TX + lane];
+        if (PAR == 0) {
+#pragma unroll
+          for (int i = 0; i < 9; ++i) f[i] = Pop<S>::ld(&sF[i * PP + pc]);
+        } else {
+          f[0] = Pop<S>::ld(&sF[pc]);
+#pragma unroll
+          for (int i = 1; i < 9; ++i) {
+            const int o = opp9(i);
+            f[i] = Pop<S>::ld(&sF[o * PP + pc + ey9(o) * PX + ex9(o)]);
+            fb[i] = Pop<S>::ld(&sF[i * PP + pc]);
+          }
+        }
+      }
+      unsafe = node_update<S, PAR, FLOW, EDGE>(d, x, y, q, fln, g, f, fb, phi, K);
+  }
+  return unsafe;
+}
+
 template <typename S, int PAR, bool FLOW, int MODE>
 __global__ void __launch_bounds__(TX* TY, TMA_MIN_CTAS)
     fused_tma_kernel(Dev d, const __grid_constant__ TmaMaps m) {
@@ -625,54 +688,12 @@ __global__ void __launch_bounds__(TX* TY, TMA_MIN_CTAS)
       }
     }
     const int x0 = ctx * TX, y0 = cty * TY;
-    const int x = x0 + lane, y = y0 + ty;
-    bool unsafe = false;
-    if (x < nx && y < ny && !is_wall(d, x, y)) {
-      const Geo q = node_geo_walled(d, x, y);
-      const S* sF = reinterpret_cast<const S*>(sb + L::F_OFF);
-      const S* sG = reinterpret_cast<const S*>(sb + L::G_OFF);
-      const float r0 = d.wt0 * d.g_ref, r1 = d.wt1 * d.g_ref;
-      const float* sFL = reinterpret_cast<const float*>(sb + L::FL_OFF);
-      // f_l of the 3x3 neighbourhood from the halo window (origin x0 - 4, y0 - 1);
-      // all four sides are walls, so every neighbour of a non-wall node is in it
-      const int c = (ty + HY) * WX + (lane + HX);
-      float fln[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) fln[i] = q.wl[i] ? -1.f : sFL[c + ey9(i) * WX + ex9(i)];
-      constexpr int PX = L::PX, PP = L::PX * L::PY;
-      const int pc = PAR ? (ty + HY) * PX + (lane + L::HS) : ty * PX + lane;
-      float g[5];
-      if (PAR == 0) {
-#pragma unroll
-        for (int i = 0; i < 5; ++i) g[i] = gload(&sG[i * PP + pc], i ? r1 : r0);
-      } else {
-        g[0] = gload(&sG[pc], r0);
-#pragma unroll
-        for (int i = 1; i < 5; ++i) {
-          const int o = opp5(i);   // from the source node x - e_i = x + e_o, its slot o
-          g[i] = gload(&sG[o * PP + pc + ey9(o) * PX + ex9(o)], r1);
-        }
-      }
-      float f[9], fb[9];
-      float phi = 0.f, K = 1.f;
-      if (FLOW) {
-        phi = reinterpret_cast<const float*>(sb + L::PHI_OFF)[ty * TX + lane];
-        K = reinterpret_cast<const float*>(sb + L::K_OFF)[ty * TX + lane];
-        if (PAR == 0) {
-#pragma unroll
-          for (int i = 0; i < 9; ++i) f[i] = Pop<S>::ld(&sF[i * PP + pc]);
-        } else {
-          f[0] = Pop<S>::ld(&sF[pc]);
-#pragma unroll
-          for (int i = 1; i < 9; ++i) {
-            const int o = opp9(i);
-            f[i] = Pop<S>::ld(&sF[o * PP + pc + ey9(o) * PX + ex9(o)]);
-            fb[i] = Pop<S>::ld(&sF[i * PP + pc]);
-          }
-        }
-      }
-      unsafe = node_update<S, PAR, FLOW>(d, x, y, q, fln, g, f, fb, phi, K);
-    }
+    const int y = y0 + ty;
+    // interior tiles (no wall node and no wall neighbour in them) take a copy
+    // of the update with the wall logic compiled out
+    const bool edge = x0 < 2 || x0 + TX > nx - 2 || y0 < 2 || y0 + TY > ny - 2;
+    const bool unsafe = edge ? tma_node<S, PAR, FLOW, true>(d, sb, x0, y0, lane, ty)
+                             : tma_node<S, PAR, FLOW, false>(d, sb, x0, y0, lane, ty);
     if (__any_sync(FULL, unsafe) && lane == 0)
       mark_tile(d, ((unsigned)y / TE) * d.etx + (unsigned)x0 / TE, PAR);
     // every thread is done with buffer b before it is refilled with the tile

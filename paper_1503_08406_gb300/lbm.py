@@ -143,6 +143,7 @@ def load():
                                     ctypes.c_int32, _VP, _VP, _DP, ctypes.c_int]
         lib.lbm_adjoint_coupled.argtypes = [_VP, ctypes.c_int, ctypes.c_int64, ctypes.c_int32,
                                             ctypes.c_int32, _VP, _VP, _VP, _DP, ctypes.c_int]
+        lib.lbm_adjoint_timing.argtypes = [_VP, _DP]
         lib.lbm_batch_create.argtypes = [ctypes.POINTER(_VP), ctypes.c_int, _VP,
                                          ctypes.POINTER(_VP)]
         lib.lbm_batch_step.argtypes = [_VP, ctypes.c_int64]
@@ -350,6 +351,12 @@ class Lattice:
                                          int(mu_sweeps), dphi.ctypes.data, dtw.ctypes.data,
                                          ctypes.byref(J), 0), "lbm_adjoint_melt")
         return J.value, dphi, dtw
+
+    def adjoint_timing(self) -> tuple[float, float]:
+        """Device ms of the last adjoint call: (forward run, reverse sweep)."""
+        ms = (ctypes.c_double * 2)()
+        _check(self.lib.lbm_adjoint_timing(self._h, ms), "lbm_adjoint_timing")
+        return ms[0], ms[1]
 
     def kernel_variant(self) -> int:
         """1: ordinary-load stream-collide kernel, 2: TMA-staged kernel."""
