@@ -85,6 +85,10 @@ def parse(argv=None):
     ap.add_argument("--objective", choices=("melt", "nusselt"), default="melt",
                     help="adjoint workload: melted fraction at the end, or the left-wall "
                          "Nusselt number averaged over the steps")
+    ap.add_argument("--trace", type=int, default=0,
+                    help="cavity workload: after the measurements, step this many more steps "
+                         "with the kernel trace on and print each launch's start, end and CTA "
+                         "count (a timeline of the overlapped graph replay)")
     ap.add_argument("--checkpoint", type=int, default=0,
                     help="adjoint workloads: keep the whole state every K steps (0: every "
                          "state when it fits in half the free memory, else sqrt(steps))")
@@ -665,6 +669,18 @@ def main(argv=None):
         line["e2e"] = e2e
         line["cpu_baseline"] = base
         print(json.dumps(line), flush=True)
+    if args.trace > 0 and rank == 0:
+        from paper_1503_08406_gb300.lbm import trace_launches
+        lat.trace(1 << 22)
+        lat.prepare(args.trace)
+        lat.step(args.trace)
+        recs = lat.trace_read()
+        lat.trace(0)
+        print("# kernel trace: %d steps, %d CTA records (times in us)" % (args.trace, len(recs)))
+        for r in trace_launches(recs):
+            print("%9.1f %9.1f %8.1f  ctas %5d  median CTA %6.1f  step %d  parity %d  %s" % (
+                r["start_us"], r["end_us"], r["end_us"] - r["start_us"], r["ctas"],
+                r["median_cta_us"], r["step"], r["parity"], r["what"]))
     lat.close()
     if dist is not None:
         dist.barrier()

@@ -321,6 +321,22 @@ int lbm_timing(lbm_ctx* c, int enable);
 int lbm_timing_read(lbm_ctx* c, double ms[4], int64_t* steps_timed, int64_t* tiles_solved,
                     int32_t* max_sweeps);
 
+/* Kernel trace, for finding where a step's time goes (graph replays run
+ * kernels side by side, which per-kernel timing cannot show).  capacity > 0:
+ * allocate a device buffer of that many records (cudaMalloc; LBM_ERR_OOM if
+ * it fails), empty it and start recording; 0: stop and free it.  While on,
+ * every CTA of the TMA-staged stream-collide kernel and of the enthalpy solve
+ * and commit kernels appends one record when it ends: kind (100 x step parity
+ * + 10 + pass for the stream-collide kernel, pass 0 all tiles, 1 tiles away
+ * from the front, 2 tiles near it; + 20 the solve; + 30 the commit), the step
+ * stamp (the same for all launches of one step), and the CTA's start and end
+ * times in ns of the GPU's global timer.  Records beyond the capacity are
+ * dropped.  Synchronises; CUDA graphs are captured again afterwards. */
+int lbm_trace(lbm_ctx* c, int64_t capacity);
+/* Copy up to max_records records (4 int64 each, in the order CTAs ended) to
+ * host memory, set *count, and empty the buffer.  Synchronises. */
+int lbm_trace_read(lbm_ctx* c, int64_t* records, int64_t max_records, int64_t* count);
+
 /* Largest lattice height (rows) lbm_reduce_state_noalloc accepts. */
 #define LBM_NOALLOC_MAX_ROWS 16384
 

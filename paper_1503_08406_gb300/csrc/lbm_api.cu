@@ -40,6 +40,7 @@ struct lbm_ctx {
   int64_t launches;                // kernels launched by lbm_step
   int64_t since_check;             // steps since the last NaN/Inf sentinel
   double adj_ms[2];                // last adjoint call: forward run, reverse sweep (device ms)
+  void* trace_buf;                 // lbm_trace records (library-allocated), or null
   lbm::TmaMaps maps;               // tensor maps of the TMA-staged fused kernel
   bool use_tma;
   bool tma_ok;                     // the lattice qualifies for the TMA-staged kernel
@@ -302,16 +303,12 @@ int lbm_create(const lbm_params* pin, void* stream, void* workspace, size_t work
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
       sms = 1;
-    // the solve runs two 512-thread CTAs per SM (they fit beside the far-tile
-    // fused pass they overlap), the commit one 1024-thread CTA per SM; a small
-    // lattice lists few tiles, so it gets at most an eighth of its tiles (at
-    // least 32) in CTAs: CTAs with nothing to do still take shared memory and
-    // slots from the lattices they run beside in a batch
-    const int cap = d.ntiles / 8 > 32 ? d.ntiles / 8 : 32;
+    // the solve and the commit walk the step's tile list with up to two CTAs
+    // per SM (CTAs without a tile exit at once); inside a batch the grids are
+    // capped (lbm_batch_create), so that idle CTAs do not take slots from the
+    // lattices beside them
     d.egrid = d.ntiles < 2 * sms ? d.ntiles : 2 * sms;
-    if (d.egrid > cap) d.egrid = cap;
-    d.cgrid = d.ntiles < sms ? d.ntiles : sms;
-    if (d.cgrid > cap) d.cgrid = cap;
+    d.cgrid = d.ntiles < 2 * sms ? d.ntiles : 2 * sms;
     lbm::enthalpy_setup();
   }
   d.max_inner = p.max_inner_iters;
@@ -364,6 +361,7 @@ void lbm_destroy(lbm_ctx* c) {
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   if (c->own_ws && c->ws) cudaFree(c->ws);
+  if (c->trace_buf) cudaFree(c->trace_buf);
   delete c;
 }
 
@@ -726,11 +724,18 @@ struct lbm_batch {
   cudaEvent_t ev_done;
   cudaGraphExec_t graph;
   std::vector<int> nl;             // kernels per context in one graph replay
+  std::vector<int> egrid, cgrid;   // the contexts' own enthalpy grids, restored at destroy
 };
 
 void lbm_batch_destroy(lbm_batch* b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
+  for (size_t i = 0; i < b->egrid.size(); ++i) {
+    lbm_ctx* c = b->ctx[i];
+    c->d.egrid = b->egrid[i];
+    c->d.cgrid = b->cgrid[i];
+    drop_graphs(c);
+  }
   if (b->graph) cudaGraphExecDestroy(b->graph);
   for (cudaEvent_t e : b->ev_in) cudaEventDestroy(e);
   for (cudaEvent_t e : b->ev_out) cudaEventDestroy(e);
@@ -751,6 +756,16 @@ int lbm_batch_create(lbm_ctx* const* ctxs, int count, void* stream, lbm_batch** 
   lbm_batch* b = new (std::nothrow) lbm_batch();
   if (!b) return LBM_ERR_OOM;
   b->ctx.assign(ctxs, ctxs + count);
+  // a small lattice lists few tiles: beside the others of the batch its
+  // enthalpy kernels get at most an eighth of its tiles (at least 32) in CTAs
+  for (lbm_ctx* c : b->ctx) {
+    b->egrid.push_back(c->d.egrid);
+    b->cgrid.push_back(c->d.cgrid);
+    const int cap = c->d.ntiles / 8 > 32 ? c->d.ntiles / 8 : 32;
+    if (c->d.egrid > cap) c->d.egrid = cap;
+    if (c->d.cgrid > cap) c->d.cgrid = cap;
+    drop_graphs(c);
+  }
   b->stream = (cudaStream_t)stream;
   b->cap = nullptr;
   b->ev_done = nullptr;
@@ -942,6 +957,48 @@ int lbm_set_state(lbm_ctx* c, const float* f, const float* g, const float* fl, i
   c->parity = 0;
   c->steps = 0;
   LBM_CUDA(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int lbm_trace(lbm_ctx* c, int64_t capacity) {
+  if (!c || capacity < 0 || capacity > (1LL << 28)) return LBM_ERR_INVALID_ARG;
+  LBM_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->trace_buf) cudaFree(c->trace_buf);
+  c->trace_buf = nullptr;
+  c->d.trace = nullptr;
+  c->d.trace_n = nullptr;
+  c->d.trace_cap = 0;
+  if (capacity > 0) {
+    if (cudaMalloc(&c->trace_buf, 256 + (size_t)capacity * 4 * sizeof(long long)) != cudaSuccess) {
+      cudaGetLastError();
+      c->trace_buf = nullptr;
+      return LBM_ERR_OOM;
+    }
+    LBM_CUDA(cudaMemsetAsync(c->trace_buf, 0, 256, c->stream));
+    c->d.trace_n = static_cast<unsigned*>(c->trace_buf);
+    c->d.trace = reinterpret_cast<long long*>(static_cast<char*>(c->trace_buf) + 256);
+    c->d.trace_cap = (unsigned)capacity;
+  }
+  drop_graphs(c);   // graphs hold the kernel parameters they were captured with
+  LBM_CUDA(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int lbm_trace_read(lbm_ctx* c, int64_t* records, int64_t max_records, int64_t* count) {
+  if (!c || !count || max_records < 0 || (max_records > 0 && !records)) return LBM_ERR_INVALID_ARG;
+  *count = 0;
+  if (!c->trace_buf) return LBM_OK;
+  unsigned n = 0;
+  LBM_CUDA(cudaMemcpyAsync(&n, c->d.trace_n, sizeof n, cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(cudaStreamSynchronize(c->stream));
+  int64_t k = n < c->d.trace_cap ? n : c->d.trace_cap;
+  if (k > max_records) k = max_records;
+  if (k > 0)
+    LBM_CUDA(cudaMemcpy(records, c->d.trace, (size_t)k * 4 * sizeof(long long),
+                        cudaMemcpyDeviceToHost));
+  LBM_CUDA(cudaMemsetAsync(c->d.trace_n, 0, sizeof n, c->stream));
+  LBM_CUDA(cudaStreamSynchronize(c->stream));
+  *count = k;
   return LBM_OK;
 }
 
@@ -1353,11 +1410,12 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
                     : checkpoint_every > 0 ? checkpoint_every
                                            : (int64_t)ceil(sqrt((double)nsteps));
   const int64_t ncp = keep_all ? 1 : nsteps / K + 1;
-  if (!keep_all && (double)(ncp + K + 2) * st * sizeof(float) > 0.8 * (double)free_b)
+  if (!keep_all && (double)(ncp + 2 * K + 3) * st * sizeof(float) > 0.8 * (double)free_b)
     return LBM_ERR_OOM;
   DevMem mem;
   // states of one segment (index m: after its m-th step; all steps when keep_all)
   float* S = mem.get((size_t)(K + 1) * st);
+  float* S2 = keep_all ? nullptr : mem.get((size_t)(K + 1) * st);   // second segment buffer
   float* cps = keep_all ? nullptr : mem.get((size_t)ncp * st);
   float* fin = keep_all ? nullptr : mem.get(st);
   float* lf[2] = {mem.get(9 * n), mem.get(9 * n)};
@@ -1375,8 +1433,8 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
   int* lists[2] = {reinterpret_cast<int*>(mem.get(n)), reinterpret_cast<int*>(mem.get(n))};
   int* counts = reinterpret_cast<int*>(mem.get(2));
   double* nu_acc = reinterpret_cast<double*>(mem.get(2));
-  unsigned* ctr = reinterpret_cast<unsigned*>(mem.get(2));
-  if (!S || (!keep_all && (!cps || !fin)) || !lf[0] || !lf[1] || !lg[0] || !lg[1] || !b.a ||
+  unsigned* ctr = reinterpret_cast<unsigned*>(mem.get(4));   // two counter pairs
+  if (!S || (!keep_all && (!cps || !fin || !S2)) || !lf[0] || !lf[1] || !lg[0] || !lg[1] || !b.a ||
       !b.lamf || !b.rhs || !b.mu0 || !b.mu1 || !b.lama || !b.lamtw || !b.pos || !lK ||
       !lists[0] || !lists[1] || !counts || !nu_acc || !ctr)
     return LBM_ERR_OOM;
@@ -1522,24 +1580,32 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
   if (keep_all) {
     reverse(c->stream, S, 0, nsteps);
   } else {
-    // One segment, its checkpoint first copied to S (index 0): the state set
-    // from it (parity 0, empty work lists), len steps forward kernel by kernel
-    // with the state after each kept at S + m st, then the len reversed steps.
-    // The launches are the same for every whole segment that starts with the
-    // same adjoint buffer, so each (len, buffer) pair is captured once.
-    auto record_segment = [&](cudaStream_t sm, int64_t len) {
-      lbm::launch_set_state(c->d, S, S + 9 * n, sm);
-      cudaMemcpyAsync(c->d.fl, S + 14 * n, n * sizeof(float), cudaMemcpyDeviceToDevice, sm);
+    // Two kinds of work per segment j, on two streams, with the segment's
+    // states in one of two buffers (S and S2, alternating):
+    //   R(j): its checkpoint copied to the buffer (index 0; a copy outside the
+    //         graph), the state set from it (parity 0, empty work lists), len
+    //         steps forward with the state after each kept at index m;
+    //   B(j): its len reversed steps from the buffer.
+    // R(j - 1) runs on a second stream beside B(j): B reads only the buffer
+    // and the adjoint arrays, R only the lattice and the other buffer; R(j - 1)
+    // waits for B(j + 1), the last reader of its buffer, and B(j) for R(j).
+    // Each (kind, len, buffer[, adjoint buffer]) is captured once and replayed.
+    float* const Sb[2] = {S, S2};
+    auto record_R = [&](cudaStream_t sm, int64_t len, int buf) {
+      float* const SS = Sb[buf];
+      unsigned* const cc = ctr + 2 * buf;
+      lbm::launch_set_state(c->d, SS, SS + 9 * n, sm);
+      cudaMemcpyAsync(c->d.fl, SS + 14 * n, n * sizeof(float), cudaMemcpyDeviceToDevice, sm);
       cudaMemsetAsync(c->d.flags, 0, 2 * sizeof(int) * c->d.ntiles, sm);
       cudaMemsetAsync(c->d.lcount, 0, 2 * sizeof(int), sm);
       if (sm == c->cap) {
         // in a capture: the step sequence of lbm_step's graphs (the next step's
         // far tiles beside each step's enthalpy kernels), the state after each
-        // step kept at S + m st through a counter reset here
-        cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), sm);
+        // step kept at SS + m st through a counter reset here
+        cudaMemsetAsync(cc, 0, 2 * sizeof(unsigned), sm);
         Hooks hk;
-        hk.st_base = S + st;
-        hk.st_ctr = ctr;
+        hk.st_base = SS + st;
+        hk.st_ctr = cc;
         capture_body(c, (int)len, 0, &hk);
       } else {
         int par = 0;
@@ -1548,14 +1614,14 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
           lbm::launch_enthalpy_solve(c->d, par, sm);
           lbm::launch_enthalpy_commit(c->d, par, sm);
           par ^= 1;
-          lbm::launch_keep_state(c->d, par, S + (size_t)m * st, nullptr, sm);
+          lbm::launch_keep_state(c->d, par, SS + (size_t)m * st, nullptr, sm);
         }
       }
-      reverse(sm, S, 0, len);
     };
     struct SegGraph {
+      int kind;   // 0 R, 1 B
       int64_t len;
-      int cur;
+      int buf, cur;
       cudaGraphExec_t ex;
     };
     struct SegGraphs {
@@ -1565,34 +1631,81 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
       }
     } seg_graphs;
     const bool can_capture = !c->graphs_off && capture_streams(c);
-    for (int64_t j = ncp - 1; j >= 0; --j) {
-      const int64_t first = j * K;
-      const int64_t len = (j == ncp - 1) ? nsteps - first : K;
-      if (len <= 0) continue;
-      LBM_CUDA(cudaMemcpyAsync(S, cps + (size_t)j * st, st * sizeof(float),
-                               cudaMemcpyDeviceToDevice, c->stream));
-      const int cur0 = cur;
-      cudaGraphExec_t ex = nullptr;
+    // a captured graph of R (after its checkpoint copy) or B, or nullptr
+    auto graph_of = [&](int kind, int64_t len, int buf) -> cudaGraphExec_t {
       for (const SegGraph& g : seg_graphs.v)
-        if (g.len == len && g.cur == cur0) ex = g.ex;
-      if (!ex && can_capture) {
-        cudaGraph_t gr = nullptr;
-        if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-          record_segment(c->cap, len);
-          if (cudaStreamEndCapture(c->cap, &gr) == cudaSuccess && gr) {
-            ex = instantiate(gr);
-            if (ex) seg_graphs.v.push_back({len, cur0, ex});
-          }
+        if (g.kind == kind && g.len == len && g.buf == buf && (kind == 0 || g.cur == cur))
+          return g.ex;
+      if (!can_capture) return nullptr;
+      cudaGraphExec_t ex = nullptr;
+      cudaGraph_t gr = nullptr;
+      const int cur0 = cur;
+      if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        if (kind == 0) record_R(c->cap, len, buf);
+        else reverse(c->cap, Sb[buf], 0, len);
+        if (cudaStreamEndCapture(c->cap, &gr) == cudaSuccess && gr) {
+          ex = instantiate(gr);
+          if (ex) seg_graphs.v.push_back({kind, len, buf, cur0, ex});
         }
-        cudaGetLastError();
-        cur = cur0;
       }
+      cudaGetLastError();
+      cur = cur0;
+      return ex;
+    };
+    struct Pipe {
+      cudaStream_t rs = nullptr;
+      cudaEvent_t evR[2] = {nullptr, nullptr}, evB[2] = {nullptr, nullptr};
+      ~Pipe() {
+        if (rs) cudaStreamDestroy(rs);
+        for (cudaEvent_t e : evR)
+          if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : evB)
+          if (e) cudaEventDestroy(e);
+      }
+    } pp;
+    bool piped = can_capture &&
+                 cudaStreamCreateWithFlags(&pp.rs, cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; piped && k < 2; ++k)
+      piped = cudaEventCreateWithFlags(&pp.evR[k], cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&pp.evB[k], cudaEventDisableTiming) == cudaSuccess;
+    cudaGetLastError();
+    const cudaStream_t rs = piped ? pp.rs : c->stream;
+    auto seg_len = [&](int64_t j) { return (j == ncp - 1) ? nsteps - j * K : K; };
+    // R runs on rs after everything queued on the context stream so far
+    if (piped) {
+      LBM_CUDA(cudaEventRecord(pp.evB[1], c->stream));
+      LBM_CUDA(cudaStreamWaitEvent(rs, pp.evB[1], 0));
+    }
+    auto run_R = [&](int64_t j, int buf) -> int {
+      const int64_t len = seg_len(j);
+      LBM_CUDA(cudaMemcpyAsync(Sb[buf], cps + (size_t)j * st, st * sizeof(float),
+                               cudaMemcpyDeviceToDevice, rs));
+      cudaGraphExec_t ex = graph_of(0, len, buf);
+      if (ex) LBM_CUDA(cudaGraphLaunch(ex, rs));
+      else record_R(rs, len, buf);
+      if (piped) LBM_CUDA(cudaEventRecord(pp.evR[buf], rs));
+      return cuda_err(cudaGetLastError());
+    };
+    int64_t j = ncp - 1;
+    while (j >= 0 && seg_len(j) <= 0) --j;
+    int buf = 0;
+    if (j >= 0) LBM_TRY(run_R(j, buf));
+    bool first = true;
+    for (; j >= 0; --j, buf ^= 1, first = false) {
+      const int64_t len = seg_len(j);
+      if (piped) LBM_CUDA(cudaStreamWaitEvent(c->stream, pp.evR[buf], 0));
+      cudaGraphExec_t ex = graph_of(1, len, buf);
       if (ex) {
-        // the graph was ordered after the copy above by the stream
         LBM_CUDA(cudaGraphLaunch(ex, c->stream));
         if (len & 1) cur ^= 1;
       } else {
-        record_segment(c->stream, len);
+        reverse(c->stream, Sb[buf], 0, len);
+      }
+      if (piped) LBM_CUDA(cudaEventRecord(pp.evB[buf], c->stream));
+      if (j > 0) {
+        // R(j - 1) into the other buffer, once B(j + 1) is done with it
+        if (piped && !first) LBM_CUDA(cudaStreamWaitEvent(rs, pp.evB[buf ^ 1], 0));
+        LBM_TRY(run_R(j - 1, buf ^ 1));
       }
       LBM_CUDA(cudaGetLastError());
     }

@@ -87,8 +87,9 @@ __device__ __forceinline__ bool sub_sync_or(int threads, bool v) {
   return r != 0;
 }
 
-template <int PAR, typename S>
+template <int PAR, typename S, int EB>
 __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
+  const long long tr0 = trace_start(d);
   constexpr int LAYOUT = 1 - PAR;
   extern __shared__ float smem[];
   float* sbase = smem;               // T* + w~0 a f_l(n) - T_s
@@ -110,20 +111,34 @@ __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
     const bool inner = X0 - RH >= 1 && X0 + TE + RH <= d.nx - 1 && Y0 - RH >= 1 &&
                        Y0 + TE + RH <= d.ny - 1;
     if (inner) {
-#pragma unroll 3
-      for (int k = tid; k < RE * RE; k += EB) {
-        const int ly = k / RE, lx = k - ly * RE;
-        const int gx = X0 - RH + lx, gy = Y0 - RH + ly;
-        const int s = gy * d.nx + gx;
-        const float fn = d.fl[s];
-        const float a = d.phi[s] * d.lat * sigma_ratio(d, fn);   // phi dT / (sigma(f_l(n)) St)
-        const float T = tstar_t<S>(d, s, gx - 1, gx + 1, gy - 1, gy + 1, gx, gy, LAYOUT);
-        sbase[k] = T + w0 * a * fn - Ts;
-        sinv[k] = 1.f / (dTt + w0 * a);
-        sa[k] = a;
-        sfn[k] = fn;
-        sq[k] = 0.f;
-        sf[k] = fn;
+      // every thread's nodes loaded in one go (all loads in flight together)
+      constexpr int NK = (RE * RE + EB - 1) / EB;
+      float fnv[NK], phv[NK], Tv[NK];
+#pragma unroll
+      for (int j = 0; j < NK; ++j) {
+        const int k = tid + j * EB;
+        if (k < RE * RE) {
+          const int ly = k / RE, lx = k - ly * RE;
+          const int gx = X0 - RH + lx, gy = Y0 - RH + ly;
+          const int s = gy * d.nx + gx;
+          fnv[j] = d.fl[s];
+          phv[j] = d.phi[s];
+          Tv[j] = tstar_t<S>(d, s, gx - 1, gx + 1, gy - 1, gy + 1, gx, gy, LAYOUT);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NK; ++j) {
+        const int k = tid + j * EB;
+        if (k < RE * RE) {
+          const float fn = fnv[j];
+          const float a = phv[j] * d.lat * sigma_ratio(d, fn);   // phi dT / (sigma(f_l(n)) St)
+          sbase[k] = Tv[j] + w0 * a * fn - Ts;
+          sinv[k] = 1.f / (dTt + w0 * a);
+          sa[k] = a;
+          sfn[k] = fn;
+          sq[k] = 0.f;
+          sf[k] = fn;
+        }
       }
     } else {
 #pragma unroll 3
@@ -216,46 +231,114 @@ __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
     int it = 0;
     bool more = sw > 0;   // (nothing left to sweep: solved by the fixing pass)
     int polish = more ? 2 : 0;   // extra sweeps after the stop test passes
-    if (tid < sw)
-    for (; it < d.max_inner && (more || polish > 0); ++it) {
-      if (!more) --polish;
-      // over-relaxed for the first sweeps, then plain Gauss-Seidel: at the last
-      // few ulps over-relaxation can cycle instead of meeting the stop test
-      const float om = (more && it < SOR_SWEEPS) ? SOR_OMEGA : 1.f;
-      bool changed = false;
+    if (nbox <= EB) {
+      // One node per colour and thread: each sweeping thread keeps its two
+      // nodes' place (packed with which neighbours lie in the region),
+      // coefficients and current value in registers, so that a sweep only
+      // exchanges q through shared memory.
+      int kk[2];
+      float cb[2], cinv[2], ca[2], cfn[2], cf[2];
 #pragma unroll
       for (int color = 0; color < 2; ++color) {
-        for (int j = tid; j < nbox; j += EB) {
+        int k = -1;
+        if (tid < nbox) {
           // (row, column pair) of the box; exact for j < 2^16 and ncol <= 24
-          const int r = (int)(((float)j + 0.5f) * inv_ncol);
+          const int r = (int)(((float)tid + 0.5f) * inv_ncol);
           const int ly = ly0 + r;
-          const int lx = lx0 + ((lx0 + ly + color) & 1) + 2 * (j - r * ncol);
-          if (lx >= RE) continue;
-          const int k = ly * RE + lx;
-          const float inv = sinv[k];
-          if (inv == 0.f) continue;   // wall, outside, or fixed above
-          const float a = sa[k];
-          float nb = 0.f;
-          if (lx > 0) nb += sq[k - 1];
-          if (lx < RE - 1) nb += sq[k + 1];
-          if (ly > 0) nb += sq[k - RE];
-          if (ly < RE - 1) nb += sq[k + RE];
-          const float b = sbase[k];
-          const float fo = sf[k];
-          const float raw = (b - w1 * nb) * inv;
-          float v = (om == 1.f) ? raw : fo + om * (raw - fo);
-          v = fminf(fmaxf(v, 0.f), 1.f);
-          // converged at about four ulps of v and of the terms that make it
-          const float tol = 4.8e-7f * (v + (fabsf(b) + w1 * fabsf(nb)) * inv);
-          if (fabsf(v - fo) > tol) changed = true;
-          sf[k] = v;
-          sq[k] = a * (v - sfn[k]);
+          const int lx = lx0 + ((lx0 + ly + color) & 1) + 2 * (tid - r * ncol);
+          if (lx < RE) {
+            k = ly * RE + lx;
+            if (sinv[k] == 0.f) k = -1;   // wall, outside, or fixed above
+            else
+              k |= ((lx > 0) | ((lx < RE - 1) << 1) | ((ly > 0) << 2) | ((ly < RE - 1) << 3)) << 16;
+          }
         }
-        // the second colour's barrier also collects the convergence vote
-        if (color == 0) sub_sync(sw);
+        const int q = k & 0xffff;
+        const float inv = k >= 0 ? sinv[q] : 0.f;
+        kk[color] = k;
+        cb[color] = k >= 0 ? sbase[q] : 0.f;
+        cinv[color] = inv;
+        ca[color] = k >= 0 ? sa[q] : 0.f;
+        cfn[color] = k >= 0 ? sfn[q] : 0.f;
+        cf[color] = k >= 0 ? sf[q] : 0.f;
       }
-      const bool c = sub_sync_or(sw, changed);
-      if (more) more = c;
+      if (tid < sw)
+        for (; it < d.max_inner && (more || polish > 0); ++it) {
+          if (!more) --polish;
+          // over-relaxed for the first sweeps, then plain Gauss-Seidel: at the last
+          // few ulps over-relaxation can cycle instead of meeting the stop test
+          const float om = (more && it < SOR_SWEEPS) ? SOR_OMEGA : 1.f;
+          bool changed = false;
+#pragma unroll
+          for (int color = 0; color < 2; ++color) {
+            const int k = kk[color];
+            if (k >= 0) {
+              const int q = k & 0xffff;
+              const int m = k >> 16;
+              float nb = 0.f;
+              if (m & 1) nb += sq[q - 1];
+              if (m & 2) nb += sq[q + 1];
+              if (m & 4) nb += sq[q - RE];
+              if (m & 8) nb += sq[q + RE];
+              const float fo = cf[color];
+              const float raw = (cb[color] - w1 * nb) * cinv[color];
+              float v = (om == 1.f) ? raw : fo + om * (raw - fo);
+              v = fminf(fmaxf(v, 0.f), 1.f);
+              // converged at about four ulps of v and of the terms that make it
+              const float tol =
+                  4.8e-7f * (v + (fabsf(cb[color]) + w1 * fabsf(nb)) * cinv[color]);
+              if (fabsf(v - fo) > tol) changed = true;
+              cf[color] = v;
+              // (a (v - f_l(n)) is exactly 0 on a node that does not move: a
+              // spurious source there would cost a rounding of its neighbours'
+              // 16-bit populations in the commit)
+              sq[q] = ca[color] * (v - cfn[color]);
+            }
+            // the second colour's barrier also collects the convergence vote
+            if (color == 0) sub_sync(sw);
+          }
+          const bool c = sub_sync_or(sw, changed);
+          if (more) more = c;
+        }
+#pragma unroll
+      for (int color = 0; color < 2; ++color)
+        if (kk[color] >= 0) sf[kk[color] & 0xffff] = cf[color];
+    } else if (tid < sw) {
+      for (; it < d.max_inner && (more || polish > 0); ++it) {
+        if (!more) --polish;
+        const float om = (more && it < SOR_SWEEPS) ? SOR_OMEGA : 1.f;
+        bool changed = false;
+#pragma unroll
+        for (int color = 0; color < 2; ++color) {
+          for (int j = tid; j < nbox; j += EB) {
+            const int r = (int)(((float)j + 0.5f) * inv_ncol);
+            const int ly = ly0 + r;
+            const int lx = lx0 + ((lx0 + ly + color) & 1) + 2 * (j - r * ncol);
+            if (lx >= RE) continue;
+            const int k = ly * RE + lx;
+            const float inv = sinv[k];
+            if (inv == 0.f) continue;   // wall, outside, or fixed above
+            const float a = sa[k];
+            float nb = 0.f;
+            if (lx > 0) nb += sq[k - 1];
+            if (lx < RE - 1) nb += sq[k + 1];
+            if (ly > 0) nb += sq[k - RE];
+            if (ly < RE - 1) nb += sq[k + RE];
+            const float b = sbase[k];
+            const float fo = sf[k];
+            const float raw = (b - w1 * nb) * inv;
+            float v = (om == 1.f) ? raw : fo + om * (raw - fo);
+            v = fminf(fmaxf(v, 0.f), 1.f);
+            const float tol = 4.8e-7f * (v + (fabsf(b) + w1 * fabsf(nb)) * inv);
+            if (fabsf(v - fo) > tol) changed = true;
+            sf[k] = v;
+            sq[k] = a * (v - sfn[k]);
+          }
+          if (color == 0) sub_sync(sw);
+        }
+        const bool c = sub_sync_or(sw, changed);
+        if (more) more = c;
+      }
     }
     __syncthreads();
     bool fchg = false, achg = false;
@@ -283,10 +366,12 @@ __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
     }
     __syncthreads();
   }
+  if (threadIdx.x == 0 && d.trace) trace_end(d, 100 * PAR + 20, d.ctr[PAR], tr0);
 }
 
 template <int PAR>
 __global__ void __launch_bounds__(CB) enthalpy_commit_kernel(Dev d) {
+  const long long tr0 = trace_start(d);
   constexpr int LAYOUT = 1 - PAR;
   constexpr int RW = TE + 2;              // tile plus a one-node ring
   __shared__ float2 sp[RW * RW];          // (f_l(n), f_l(n+1)); (-1,-1) on walls / outside
@@ -399,16 +484,21 @@ __global__ void __launch_bounds__(CB) enthalpy_commit_kernel(Dev d) {
     }
     __syncthreads();
   }
+  if (threadIdx.x == 0 && d.trace) trace_end(d, 100 * PAR + 30, d.ctr[PAR], tr0);
 }
 
 size_t enthalpy_solve_smem() { return 6 * RE * RE * sizeof(float); }
 
 template <typename S>
 static void solve_setup_t(int bytes) {
-  cudaFuncSetAttribute(enthalpy_solve_kernel<0, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       bytes);
-  cudaFuncSetAttribute(enthalpy_solve_kernel<1, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       bytes);
+  cudaFuncSetAttribute(enthalpy_solve_kernel<0, S, EB_WIDE>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(enthalpy_solve_kernel<1, S, EB_WIDE>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(enthalpy_solve_kernel<0, S, EB_NARROW>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(enthalpy_solve_kernel<1, S, EB_NARROW>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 void enthalpy_setup() {
@@ -418,11 +508,20 @@ void enthalpy_setup() {
   solve_setup_t<__nv_bfloat16>(bytes);
 }
 
+// A large lattice's solve runs beside a long far-tile pass, whose SMs it shares:
+// narrow CTAs (fewer registers held) cost that pass less.  On a small lattice
+// the far-tile pass hides under the solve, whose latency is then the step
+// time: wide CTAs finish sooner.
 template <typename S>
 static void launch_solve_t(const Dev& d, int parity, cudaStream_t s) {
   const size_t sm = enthalpy_solve_smem();
-  if (parity == 0) enthalpy_solve_kernel<0, S><<<d.egrid, EB, sm, s>>>(d);
-  else enthalpy_solve_kernel<1, S><<<d.egrid, EB, sm, s>>>(d);
+  if (d.ntiles >= SOLVE_NARROW_TILES) {
+    if (parity == 0) enthalpy_solve_kernel<0, S, EB_NARROW><<<d.egrid, EB_NARROW, sm, s>>>(d);
+    else enthalpy_solve_kernel<1, S, EB_NARROW><<<d.egrid, EB_NARROW, sm, s>>>(d);
+  } else {
+    if (parity == 0) enthalpy_solve_kernel<0, S, EB_WIDE><<<d.egrid, EB_WIDE, sm, s>>>(d);
+    else enthalpy_solve_kernel<1, S, EB_WIDE><<<d.egrid, EB_WIDE, sm, s>>>(d);
+  }
 }
 
 void launch_enthalpy_solve(const Dev& d, int parity, cudaStream_t s) {

@@ -629,6 +629,7 @@ __global__ void __launch_bounds__(TX* TY, TMA_MIN_CTAS)
   // than runs of consecutive tiles per CTA).
   const int t0 = (int)blockIdx.x, dt = (int)gridDim.x;
   const int cnt = (ntile - t0 + dt - 1) / dt;
+  const long long tr0 = trace_start(d);
   if (MODE != 1 && blockIdx.x == 0 && tid == 0) step_prologue<PAR>(d);
   constexpr int NB = L::NBUF;
   const unsigned buf0 = smem_u32(smem);
@@ -719,6 +720,8 @@ __global__ void __launch_bounds__(TX* TY, TMA_MIN_CTAS)
       mbar_wait(bar0 + 8 * bj, (phases >> bj) & 1u);
     }
   }
+  // (ctr[1 - PAR] + 1: the step this launch computes; no launch of the step changes it)
+  if (tid == 0 && d.trace) trace_end(d, 100 * PAR + 10 + MODE, d.ctr[1 - PAR] + 1, tr0);
 }
 
 // ---- launches ------------------------------------------------------------------

@@ -34,8 +34,13 @@ constexpr int TY = 8;        // fused kernel tile (threads y)
 constexpr int TE = 32;       // enthalpy tile edge
 constexpr int RH = 8;        // enthalpy halo width
 constexpr int RE = TE + 2 * RH;
-constexpr int EB = 512;      // enthalpy solve block size (two CTAs per SM fit beside the far-tile pass)
-constexpr int CB = 1024;     // enthalpy commit block size
+// enthalpy solve block sizes: narrow CTAs on large lattices (they share SMs with
+// the far-tile pass), wide ones on small lattices (the solve's latency is the step)
+constexpr int EB_NARROW = 256;
+constexpr int EB_WIDE = 512;
+constexpr int SOLVE_NARROW_TILES = 1024;   // enthalpy tiles from which the narrow form runs
+constexpr int CB = 1024;     // enthalpy commit block size (one thread per node of a tile:
+                             // narrower CTAs measured slower beside the far-tile pass)
 constexpr int RB = 256;      // reduction block size
 // default tiles per CTA of the TMA-staged kernel: few enough that CTAs retire
 // often (the enthalpy kernels overlapping the far-tile pass need SMs), enough
@@ -93,10 +98,37 @@ struct Dev {
   int* proc;                 // per enthalpy tile: (stamp << 3) | bits, bit 0 solved, bit 1
                              // some f_l changed, bit 2 some node's flow activity changed
   float2* scr;               // per node of solved tiles: (f_l(n), f_l(n+1))
+  // kernel trace (lbm_trace): per CTA, at its end, (kind, step stamp, start
+  // and end in ns of %globaltimer) appended at trace[4 k], k = trace_n[0]++,
+  // while k < trace_cap; null: off
+  long long* trace;
+  unsigned* trace_n;
+  unsigned trace_cap;
   int* stats;                // [0] inner cap hit, [1] tiles solved, [2] max sweeps,
                              // [3] last tile that hit the cap, [4] a bounded wait gave up,
                              // [5] the sentinel found a non-finite value
 };
+
+__device__ __forceinline__ long long trace_now() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// start time of a traced CTA (0 when tracing is off)
+__device__ __forceinline__ long long trace_start(const Dev& d) {
+  return d.trace ? trace_now() : 0;
+}
+// one record for the calling CTA (call from one thread, at the CTA's end)
+__device__ __forceinline__ void trace_end(const Dev& d, int kind, int stamp, long long t0) {
+  if (!d.trace) return;
+  const unsigned k = atomicAdd(d.trace_n, 1u);
+  if (k >= d.trace_cap) return;
+  long long* r = d.trace + 4ll * k;
+  r[0] = kind;
+  r[1] = stamp;
+  r[2] = t0;
+  r[3] = trace_now();
+}
 
 // Tensor maps of the TMA-staged fused kernel (passed as a __grid_constant__
 // kernel parameter): population boxes without halo for even steps and with a

@@ -144,6 +144,8 @@ def load():
         lib.lbm_adjoint_coupled.argtypes = [_VP, ctypes.c_int, ctypes.c_int64, ctypes.c_int32,
                                             ctypes.c_int32, _VP, _VP, _VP, _DP, ctypes.c_int]
         lib.lbm_adjoint_timing.argtypes = [_VP, _DP]
+        lib.lbm_trace.argtypes = [_VP, ctypes.c_int64]
+        lib.lbm_trace_read.argtypes = [_VP, _VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
         lib.lbm_batch_create.argtypes = [ctypes.POINTER(_VP), ctypes.c_int, _VP,
                                          ctypes.POINTER(_VP)]
         lib.lbm_batch_step.argtypes = [_VP, ctypes.c_int64]
@@ -352,6 +354,18 @@ class Lattice:
                                          ctypes.byref(J), 0), "lbm_adjoint_melt")
         return J.value, dphi, dtw
 
+    def trace(self, capacity: int):
+        """Start (capacity > 0 records) or stop (0) the kernel trace (lbm_trace)."""
+        _check(self.lib.lbm_trace(self._h, int(capacity)), "lbm_trace")
+
+    def trace_read(self, max_records: int = 1 << 22) -> np.ndarray:
+        """The trace records so far, int64 [n, 4]: kind, step stamp, start ns, end ns."""
+        out = np.zeros((max_records, 4), dtype=np.int64)
+        n = ctypes.c_int64()
+        _check(self.lib.lbm_trace_read(self._h, out.ctypes.data, int(max_records), ctypes.byref(n)),
+               "lbm_trace_read")
+        return out[:n.value]
+
     def adjoint_timing(self) -> tuple[float, float]:
         """Device ms of the last adjoint call: (forward run, reverse sweep)."""
         ms = (ctypes.c_double * 2)()
@@ -421,6 +435,31 @@ class Lattice:
                                         ctypes.byref(m)), "lbm_timing_read")
         return dict(fused_ms=ms[0], prep_ms=ms[1], solve_ms=ms[2], commit_ms=ms[3], steps=n.value,
                     tiles_solved=t.value, max_sweeps=m.value)
+
+
+TRACE_KINDS = {10: "stream-collide, all tiles", 11: "stream-collide, tiles away from the front",
+               12: "stream-collide, tiles near the front", 20: "enthalpy solve",
+               30: "enthalpy commit"}
+
+
+def trace_launches(records: np.ndarray) -> list[dict]:
+    """Group lbm_trace records into launches (one per kind and step stamp):
+    start of the first CTA, end of the last, CTA count and median CTA time,
+    times in us from the first record, in start order."""
+    if len(records) == 0:
+        return []
+    t0 = int(records[:, 2].min())
+    out = []
+    keys = np.unique(records[:, :2], axis=0)
+    for kind, stamp in keys:
+        m = (records[:, 0] == kind) & (records[:, 1] == stamp)
+        st, en = records[m, 2], records[m, 3]
+        out.append(dict(kind=int(kind), parity=int(kind) // 100,
+                        what=TRACE_KINDS.get(int(kind) % 100, str(kind)), step=int(stamp),
+                        start_us=(int(st.min()) - t0) / 1e3, end_us=(int(en.max()) - t0) / 1e3,
+                        ctas=int(m.sum()), median_cta_us=float(np.median(en - st)) / 1e3))
+    out.sort(key=lambda r: r["start_us"])
+    return out
 
 
 class Batch:

@@ -223,3 +223,13 @@ def test_coupled_adjoint_rejects_conduction(lbm):
     lat.set_fields(w.phi, w.K, w.T0, w.fl0)
     with pytest.raises(lbm.LBMError):
         lat.adjoint_coupled(10)
+
+
+def test_adjoint_phase_timing(lbm):
+    w = _case()
+    lat = lbm.Lattice(w.nx, w.ny, **w.params)
+    assert lat.adjoint_timing() == (0.0, 0.0)
+    lat.set_fields(w.phi, w.K, w.T0, w.fl0, w.wall_T_left)
+    lat.adjoint_coupled(20, "melt", checkpoint_every=5)
+    fwd, rev = lat.adjoint_timing()
+    assert fwd > 0 and rev > 0
