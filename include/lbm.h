@@ -240,7 +240,7 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
                 int32_t mu_sweeps, float* d_phi, float* d_wall_T_left, double* J,
                 int device_ptrs);
 
-/* Adjoint of the coupled step (flow lattice on).  Runs nsteps steps forward
+/* Adjoint of the coupled step (flow lattice on or off).  Runs nsteps steps forward
  * from the context's current state and returns the objective J (LBM_OBJ_MELT
  * or LBM_OBJ_NUSSELT, as for lbm_adjoint) with its gradients with respect to
  * the porosity field (d_phi, nx*ny), the logarithm of the permeability field
@@ -256,9 +256,10 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
  * steps, and each segment recomputed from its checkpoint and reversed from
  * one CUDA graph replay (the forward run replays graphs too).  All choices
  * give the same result bit for bit.  LBM_ERR_OOM when the kept states would
- * exceed the free memory.  Covers: FP32 storage, one thermal diffusivity, a
- * Dirichlet left wall (walls left and right, nx >= 5); LBM_ERR_INVALID_ARG
- * otherwise.  The context ends where the forward run left it.  Allocates its
+ * exceed the free memory.  Covers: FP32 storage, one heat-capacity ratio,
+ * the flow lattice on or off, one thermal diffusivity or alpha_l != alpha_s
+ * (alpha_ratio, Sec. 4.1), a Dirichlet left wall (walls left and right,
+ * nx >= 5); LBM_ERR_INVALID_ARG otherwise.  The context ends where the forward run left it.  Allocates its
  * buffers with cudaMalloc and synchronises.  device_ptrs: the three gradient
  * arrays are device (1) or host (0) pointers. */
 int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_every,

@@ -1391,8 +1391,7 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
   if (objective != LBM_OBJ_MELT && objective != LBM_OBJ_NUSSELT) return LBM_ERR_INVALID_ARG;
   const lbm_params& p = c->p;
   const lbm::Dev& d = c->d;
-  if (!p.flow || c->timing || p.storage != LBM_STORAGE_FP32 || d.alpha_var || d.sigma_var)
-    return LBM_ERR_INVALID_ARG;
+  if (c->timing || p.storage != LBM_STORAGE_FP32 || d.sigma_var) return LBM_ERR_INVALID_ARG;
   if (d.per_x || p.bc[0] != LBM_BC_DIRICHLET || d.nx < 5) return LBM_ERR_INVALID_ARG;
   const bool melt = objective == LBM_OBJ_MELT;
   const int sweeps = mu_sweeps > 0 ? mu_sweeps : 64;
@@ -1543,10 +1542,10 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
   A.nu_tw = (float)(1.5 * kN);
   A.ny0 = y0;
   A.ny1 = y1;
-  A.alpha_var = 0;   // (rejected above)
-  A.tauT_l = 0.f;
-  A.inv_aratio = 1.f;
-  A.flow = 1;
+  A.alpha_var = d.alpha_var;   // Sec. 4.1: the flux moments' rate follows f_l(n)
+  A.tauT_l = d.tauT_l;
+  A.inv_aratio = d.inv_aratio;
+  A.flow = d.flow;
   const float w9[9] = {4.f / 9, 1.f / 9, 1.f / 9, 1.f / 9, 1.f / 9,
                        1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36};
   for (int i = 0; i < 9; ++i) A.foff[i] = w9[i] * d.rho0;

@@ -215,14 +215,37 @@ def test_coupled_adjoint_matches_oracle_finite_differences(lbm, oracle_mod, obje
         assert err < TOL, (name, err, worst)
 
 
-def test_coupled_adjoint_rejects_conduction(lbm):
-    w = W.two_phase_slab(1.0, nx=40, ny=4)
-    p = dict(w.params)
-    p.pop("alpha_ratio")
-    lat = lbm.Lattice(w.nx, w.ny, **p)
-    lat.set_fields(w.phi, w.K, w.T0, w.fl0)
-    with pytest.raises(lbm.LBMError):
-        lat.adjoint_coupled(10)
+@pytest.mark.parametrize("which,objective", [("slab_alpha10", "melt"),
+                                             ("slab_alpha10", "nusselt"),
+                                             ("cavity_alpha3", "melt")])
+def test_coupled_adjoint_with_phase_dependent_diffusivity(lbm, oracle_mod, which, objective):
+    """alpha_l != alpha_s (Sec. 4.1: the flux moments' rate follows f_l(n)):
+    the Sec. 4.1 slab with alpha_l = 10 alpha_s and the flow lattice off, and
+    the melting cavity with alpha_l = 3 alpha_s, against the FP64 reference."""
+    from oracle.coupled_ref import CoupledRef
+    if which == "slab_alpha10":
+        w = W.adjoint_slab(40, 4)
+        w.params = {**w.params, "alpha_ratio": 10.0, "tau_T": 0.5 + 10 * 0.02 / 0.2}
+        steps = 200
+    else:
+        w = _case()
+        w.params = {**w.params, "alpha_ratio": 3.0}
+        steps = STEPS
+    w = _f32(w)
+    ref = CoupledRef(w.nx, w.ny, w.params).gradients(steps, w.T0, w.fl0, w.phi, w.K,
+                                                     w.wall_T_left, objective)
+    got = _gpu(lbm, w, steps, objective)
+    J, dphi, dlnK, dtw = got
+    J_ref, dphi_ref, dlnK_ref, dtw_ref = ref
+    assert abs(J - J_ref) < 1e-4 * abs(J_ref), (J, J_ref)
+    for name, g, e in (("phi", dphi, dphi_ref), ("Tw", dtw, dtw_ref)):
+        scale = np.abs(e).max()
+        assert np.abs(np.asarray(g, dtype=np.float64) - e).max() < TOL * scale, name
+    if w.params.get("flow", 1):
+        scale = np.abs(dlnK_ref).max()
+        assert np.abs(np.asarray(dlnK, dtype=np.float64) - dlnK_ref).max() < TOL * scale
+    else:
+        assert np.abs(dlnK).max() == 0   # no flow: the permeability plays no part
 
 
 def test_adjoint_phase_timing(lbm):

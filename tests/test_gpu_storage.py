@@ -153,3 +153,58 @@ def test_state_roundtrip_is_exact(lbm, storage):
     b.set_state(f, g, fl)
     for x, y in zip((f, g, fl), b.get_state()):
         assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
+
+
+# ---- the precision study on the downsampled heterogeneous cavity ----------------
+
+@pytest.fixture(scope="module")
+def downsample_oracle(oracle_mod):
+    """The heterogeneous cavity's 256^2 copy (the 2048^2 porosity draw of seed 3
+    block-averaged 8 x 8; Ra = 1e6, mean Da = 1e-4 kept), run by the FP64
+    oracle to 1,000 and 10,000 steps."""
+    w = _f32(W.heterogeneous_cavity(256, seed=3, source_n=2048))
+    o = oracle_mod.Oracle(w.nx, w.ny, **w.params)
+    o.set_fields(w.phi, w.K, w.T0, w.fl0, w.wall_T_left)
+    out, done = {}, 0
+    for steps in (1000, 10000):
+        o.step(steps - done)
+        done = steps
+        out[steps] = (o.macros(), o.reduce())
+    return w, out
+
+
+# per-field bars (normwise, and relative for the melted fraction and Nusselt
+# number) at about 3x the values measured on this workload
+DOWNSAMPLE_BARS = {
+    ("fp32", 1000): dict(u=1e-4, T=1e-4, fl=1e-4, melt=1e-5, nu=1e-5),
+    ("fp32", 10000): dict(u=1e-4, T=1e-4, fl=1e-4, melt=1e-4, nu=1e-4),
+    ("fp16", 1000): dict(u=0.1, T=5e-3, fl=2e-2, melt=1e-3, nu=2e-3),
+    ("fp16", 10000): dict(u=0.5, T=2e-2, fl=5e-2, melt=1e-3, nu=5e-3),
+    ("bf16", 1000): dict(u=0.3, T=3e-2, fl=0.1, melt=1e-3, nu=3e-2),
+    ("bf16", 10000): dict(u=0.5, T=5e-2, fl=0.2, melt=5e-3, nu=5e-2),
+}
+
+
+@pytest.mark.parametrize("storage", ("fp32", "fp16", "bf16"))
+def test_precision_study_on_downsampled_cavity(lbm, downsample_oracle, storage):
+    """FP32, FP16 and BF16 population storage against the FP64 oracle on the
+    256^2 copy of the 2048^2 heterogeneous cavity; the errors per field are
+    printed (pytest -s) and held to the bars above."""
+    w, ref = downsample_oracle
+    lat = _run(lbm, w, 0, storage)
+    done = 0
+    for steps in (1000, 10000):
+        lat.step(steps - done)
+        done = steps
+        assert lat.status() == 0
+        got, r = lat.macros(), lat.reduce()
+        exp, ro = ref[steps]
+        err = _errors(got, exp)
+        melt = abs(r["melt_frac"] / ro["melt_frac"] - 1)
+        nu = abs(r["nu_hot"] / ro["nu_hot"] - 1)
+        print("precision %s %d steps: u_x %.2e u_y %.2e T %.2e f_l %.2e melted %.2e Nu %.2e" % (
+            storage, steps, err["ux"], err["uy"], err["T"], err["fl"], melt, nu))
+        bar = DOWNSAMPLE_BARS[(storage, steps)]
+        assert max(err["ux"], err["uy"]) < bar["u"], (storage, steps, err)
+        assert err["T"] < bar["T"] and err["fl"] < bar["fl"], (storage, steps, err)
+        assert melt < bar["melt"] and nu < bar["nu"], (storage, steps, melt, nu)
