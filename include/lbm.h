@@ -103,6 +103,14 @@ typedef struct {
                                      tau_T belongs to the liquid), in n^eq of Eq. (34), in the
                                      wall extrapolation and in the latent coefficient
                                      a = phi dT / (sigma St) of Eq. (38); 0: one sigma */
+  int32_t flow_walls;             /* 1: flow walls by non-equilibrium extrapolation (Sec. 4):
+                                     a wall node whose inward node (the diagonal one at a
+                                     corner) carries flow takes f^eq(rho_f, 0) + f(x_f) -
+                                     f^eq(rho_f, u_f) before collision, collides with x_f's
+                                     T, f_l, phi and K and streams like a flow node, and links
+                                     into it stream; 0: links into wall nodes reflect halfway.
+                                     Ignored without the flow lattice; the coupled adjoint
+                                     refuses it */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;

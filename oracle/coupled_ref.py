@@ -23,7 +23,13 @@ profile:
 
 The flow nodes are chosen by f_l(n) >= f_act, a step function: its derivative
 is 0 wherever it is defined, and finite differences that do not move a node
-across f_act agree with it.  Square roots of speeds carry a 1e-300 floor so
+across f_act agree with it.  The clamp of Eq. (42) passes derivatives only
+where its output lies more than BAND_EPS = 1e-7 inside (0, 1): a solid held
+at T_s sits on the clamp's kink, where the derivative of the discrete map is
+not defined (exact arithmetic keeps f_l at 0 there, FP32 arithmetic at
+values of order 1e-8), and the mushy branch's linearisation grows without
+bound when it is applied to such nodes.  Finite differences of the oracle
+agree with this reading wherever no node is within 1e-7 of a clamp value.  Square roots of speeds carry a 1e-300 floor so
 that a node at rest has a finite derivative; the forward values are those of
 the oracle.  Scope: one sigma; one thermal diffusivity or, with
 alpha_l != alpha_s (Sec. 4.1), the rate of the flux moments following f_l(n)
@@ -65,6 +71,23 @@ N5 = torch.tensor([[1, 1, 1, 1, 1],
                    [0, 1, -1, 1, -1]], dtype=D)
 CS2 = 1.0 / 3.0
 BC = {"periodic": 0, "dirichlet": 1, "adiabatic": 2}
+BAND_EPS = 1e-7
+
+
+class _Clamp01(torch.autograd.Function):
+    """clamp(z, 0, 1) of Eq. (42), its derivative 1 only where the result lies
+    more than BAND_EPS inside (0, 1)."""
+
+    @staticmethod
+    def forward(ctx, z):
+        out = torch.clamp(z, 0.0, 1.0)
+        ctx.save_for_backward((out > BAND_EPS) & (out < 1.0 - BAND_EPS))
+        return out
+
+    @staticmethod
+    def backward(ctx, grad):
+        (open_,) = ctx.saved_tensors
+        return grad * open_
 
 
 def _inv_orthogonal_rows(M):
@@ -291,7 +314,7 @@ class CoupledRef:
         for _ in range(self.max_inner):
             src = torch.where(self.wall, zero, -a * (fk - fl))
             Tk = base + sum(self.w5[i] * self._shift(src, EX5[i], EY5[i]) for i in range(5))
-            fnext = torch.clamp((Tk + a * fk - self.T_s) / (dTt + a), 0.0, 1.0)
+            fnext = _Clamp01.apply((Tk + a * fk - self.T_s) / (dTt + a))
             fnext = torch.where(self.wall, fl, fnext)
             diff = float((fnext - fk).detach().abs().max())
             fk = fnext

@@ -63,7 +63,8 @@ __device__ __forceinline__ float wt(const Dev& d, int i) { return i == 0 ? d.wt0
 //          nodes' own populations do not reach the next step (the
 //          extrapolation rewrites them).
 // The unclamped nodes of a step are the non-wall nodes with 0 < f_l < 1 after
-// it (the solver converges to f = z there, and clamps elsewhere); the full
+// it, ADJ_BAND_EPS inside those bounds (the solver converges to f = z there,
+// and clamps elsewhere); the full
 // pass of one reversed step lists them for the next (its f(n) is the next
 // one's f(n+1)).
 
@@ -71,7 +72,7 @@ __device__ __forceinline__ bool band_node(const Dev& d, const float* f, int t) {
   if (t < 0) return false;
   const int y = t / d.nx, x = t - y * d.nx;
   const float v = f[t];
-  return !is_wall(d, x, y) && v > 0.f && v < 1.f;
+  return !is_wall(d, x, y) && adj_mushy(v);
 }
 
 // the band of the state with liquid fraction f, appended at list[*count]
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(AB) adj_full_kernel(Dev d, AdjBuffers b, Mat5 
     const float fa = f0[s], fb = f1[s];
     b.lamf[s] = __ldg(b.a + s) * S;
     if (fb != fa) b.lama[s] += -(fb - fa) * S;   // (adds 0 elsewhere)
-    if (fa > 0.f && fa < 1.f) next_list[atomicAdd(next_count, 1)] = s;
+    if (adj_mushy(fa)) next_list[atomicAdd(next_count, 1)] = s;
   }
 }
 

@@ -124,6 +124,7 @@ int check_params(const lbm_params* p) {
   if (p->storage < LBM_STORAGE_FP32 || p->storage > LBM_STORAGE_BF16) return LBM_ERR_INVALID_ARG;
   if (!(p->alpha_ratio >= 0)) return LBM_ERR_INVALID_ARG;
   if (!(p->sigma_solid >= 0)) return LBM_ERR_INVALID_ARG;
+  if (p->flow_walls < 0 || p->flow_walls > 1) return LBM_ERR_INVALID_ARG;
   return LBM_OK;
 }
 
@@ -272,6 +273,7 @@ int lbm_create(const lbm_params* pin, void* stream, void* workspace, size_t work
   d.tauT_l = (float)der[1];
   d.inv_aratio = d.alpha_var ? (float)(1.0 / p.alpha_ratio) : 1.f;
   d.sigma_var = (p.sigma_solid > 0 && p.sigma_solid != p.sigma) ? 1 : 0;
+  d.flow_walls = (p.flow && p.flow_walls) ? 1 : 0;   // walls carry flow only with a flow lattice
   d.sigma_s = d.sigma_var ? (float)p.sigma_solid : (float)p.sigma;
   d.z_e = (float)p.zeta_e;
   d.z_nu = (float)p.zeta_nu;
@@ -502,16 +504,21 @@ static int capture_body(lbm_ctx* c, int steps, int start = 0, const Hooks* hooks
   int nl = 0;
   for (int k = 0; k < steps; ++k) {
     const int par = (start + k) & 1;
+    const int fw = c->d.flow && c->d.flow_walls ? 1 : 0;   // a flow-wall pass before each pass
     if (k == 0) {
+      lbm::launch_flow_walls(c->d, par, 0, c->cap);
       lbm::launch_fused(c->d, c->tma(), par, 0, c->cap);
     } else {
+      lbm::launch_flow_walls(c->d, par, 2, c->cap);
       lbm::launch_fused(c->d, c->tma(), par, 2, c->cap);       // near tiles, after the last commit
       cudaStreamWaitEvent(c->cap, c->ev_join, 0);    // and the far tiles
     }
-    nl += 1;
+    nl += 1 + fw;
     if (k + 1 < steps) {
       cudaEventRecord(c->ev_fork, c->cap);
       cudaStreamWaitEvent(c->cap2, c->ev_fork, 0);
+      lbm::launch_flow_walls(c->d, 1 - par, 1, c->cap2);
+      nl += fw;
       lbm::launch_fused(c->d, c->tma(), 1 - par, 1, c->cap2);  // next step, far tiles
       cudaEventRecord(c->ev_join, c->cap2);
       nl += 1;
@@ -590,6 +597,7 @@ static int step_direct(lbm_ctx* c) {
     }
     cudaEventRecord(e[0], c->stream);
   }
+  lbm::launch_flow_walls(c->d, c->parity, 0, c->stream);
   lbm::launch_fused(c->d, c->tma(), c->parity, 0, c->stream);
   if (c->timing) {
     cudaEventRecord(e[1], c->stream);
@@ -601,7 +609,7 @@ static int step_direct(lbm_ctx* c) {
   if (c->timing) cudaEventRecord(e[4], c->stream);
   c->parity ^= 1;
   c->steps++;
-  c->launches += 3;
+  c->launches += 3 + (c->d.flow && c->d.flow_walls ? 1 : 0);
   return LBM_OK;
 }
 
@@ -1391,7 +1399,8 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
   if (objective != LBM_OBJ_MELT && objective != LBM_OBJ_NUSSELT) return LBM_ERR_INVALID_ARG;
   const lbm_params& p = c->p;
   const lbm::Dev& d = c->d;
-  if (c->timing || p.storage != LBM_STORAGE_FP32 || d.sigma_var) return LBM_ERR_INVALID_ARG;
+  if (c->timing || p.storage != LBM_STORAGE_FP32 || d.sigma_var || (d.flow && d.flow_walls))
+    return LBM_ERR_INVALID_ARG;
   if (d.per_x || p.bc[0] != LBM_BC_DIRICHLET || d.nx < 5) return LBM_ERR_INVALID_ARG;
   const bool melt = objective == LBM_OBJ_MELT;
   const int sweeps = mu_sweeps > 0 ? mu_sweeps : 64;
@@ -1609,6 +1618,7 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
       } else {
         int par = 0;
         for (int64_t m = 1; m <= len; ++m) {
+          lbm::launch_flow_walls(c->d, par, 0, sm);
           lbm::launch_fused(c->d, c->tma(), par, 0, sm);
           lbm::launch_enthalpy_solve(c->d, par, sm);
           lbm::launch_enthalpy_commit(c->d, par, sm);

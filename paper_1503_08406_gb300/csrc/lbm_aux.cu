@@ -7,7 +7,13 @@ namespace lbm {
 // ---- population gathers for any node, any layout --------------------------
 
 __device__ __forceinline__ bool flow_active(const Dev& d, int x, int y) {
-  return !is_wall(d, x, y) && d.fl[(long long)y * d.nx + x] >= d.f_act;
+  if (is_wall(d, x, y)) {
+    if (!d.flow_walls) return false;
+    int ix, iy;   // an extrapolated wall node carries flow with its inward node
+    inward_of(d, x, y, ix, iy);
+    return d.fl[(long long)iy * d.nx + ix] >= d.f_act;
+  }
+  return d.fl[(long long)y * d.nx + x] >= d.f_act;
 }
 
 // g_i of non-wall node (x, y) in the given layout
@@ -97,8 +103,9 @@ __global__ void macros_kernel(Dev d, int layout, float* ux, float* uy, float* rh
   if (s >= d.n) return;
   const int y = (int)(s / d.nx), x = (int)(s - (long long)y * d.nx);
   const float Tn = node_T(d, x, y, layout);
+  const bool wall = is_wall(d, x, y);
   float f[9];
-  if (is_wall(d, x, y)) {
+  if (wall) {
     for (int i = 0; i < 9; ++i) f[i] = ld_f(d, i, s);
   } else {
     gather_f(d, x, y, layout, f);
@@ -107,7 +114,7 @@ __global__ void macros_kernel(Dev d, int layout, float* ux, float* uy, float* rh
   for (int i = 0; i < 9; ++i) dr += f[i];
   const float r = d.rho0 + dr;   // stored populations are f_i - w_i rho0
   float vx = 0.f, vy = 0.f;
-  if (d.flow && flow_active(d, x, y)) {
+  if (d.flow && !wall && flow_active(d, x, y)) {   // a wall's velocity is the wall's, 0
     const float jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
     const float jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
     float Fx, Fy;
@@ -266,7 +273,7 @@ __global__ void keep_state_kernel(Dev d, int layout, float* base, unsigned* ctr)
       for (int i = 1; i < 9; ++i) {
         const int sx = wrapx(d, x - ex9(i)), sy = wrapy(d, y - ey9(i));
         const long long t = (long long)sy * d.nx + sx;
-        act[i] = !is_wall(d, sx, sy) && d.fl[t] >= d.f_act;
+        act[i] = flow_active(d, sx, sy);
         str[i] = ld_f(d, opp9(i), t);
         if (i < 5) gstr[i] = ld_g(d, opp5(i), t);
       }

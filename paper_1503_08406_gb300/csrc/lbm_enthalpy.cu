@@ -369,8 +369,39 @@ __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
   if (threadIdx.x == 0 && d.trace) trace_end(d, 100 * PAR + 20, d.ctr[PAR], tr0);
 }
 
+// x changed flow activity and is the inward node of a flow wall w next to it:
+// w's links to its other lattice neighbours x' change state with x.  Those x'
+// that kept their activity leave the link to x (a changed x' takes it itself).
 template <int PAR>
-__global__ void __launch_bounds__(CB) enthalpy_commit_kernel(Dev d) {
+__device__ __noinline__ void wall_links(const Dev& d, int x, int y, bool ao, bool an,
+                                        int stamp) {
+  const int n = (int)d.n;
+  for (int j = 1; j < 9; ++j) {
+    const int wx = wrapx(d, x + ex9(j)), wy = wrapy(d, y + ey9(j));
+    if (wx < 0 || wy < 0 || !is_wall(d, wx, wy)) continue;
+    int ix, iy;
+    inward_of(d, wx, wy, ix, iy);
+    if (ix != x || iy != y) continue;
+    for (int k = 1; k < 9; ++k) {
+      const int px = wrapx(d, wx + ex9(k)), py = wrapy(d, wy + ey9(k));
+      if (px < 0 || py < 0 || is_wall(d, px, py) || (px == x && py == y)) continue;
+      const int ps = py * d.nx + px;
+      const bool vs = solved(d, (py / TE) * d.etx + (px / TE), stamp);
+      const float fo = vs ? d.scr[ps].x : d.fl[ps], fnw = vs ? d.scr[ps].y : fo;
+      const bool xo = fo >= d.f_act, xn = fnw >= d.f_act;
+      if (xo != xn || (xo && ao) == (xn && an)) continue;
+      // the pair (x', w): population opp(k) at w, population k at x'
+      const long long A = (long long)opp9(k) * n + (wy * d.nx + wx);
+      const long long B = (long long)k * n + ps;
+      const float t = ld_pop(d, d.f, A);
+      st_pop(d, d.f, A, ld_pop(d, d.f, B));
+      st_pop(d, d.f, B, t);
+    }
+  }
+}
+
+template <int PAR, bool WALLS>
+__global__ void __launch_bounds__(CB, 2) enthalpy_commit_kernel(Dev d) {
   const long long tr0 = trace_start(d);
   constexpr int LAYOUT = 1 - PAR;
   constexpr int RW = TE + 2;              // tile plus a one-node ring
@@ -420,14 +451,21 @@ __global__ void __launch_bounds__(CB) enthalpy_commit_kernel(Dev d) {
           const int gx = wrapx(d, X0 - 1 + lx), gy = wrapy(d, Y0 - 1 + ly);
           float2 v = make_float2(-1.f, -1.f);
           unsigned char sol = 0;
-          if (gx >= 0 && gy >= 0 && !is_wall(d, gx, gy)) {
-            const int gs = gy * d.nx + gx;
-            sol = solved(d, (gy / TE) * d.etx + (gx / TE), stamp) ? 1 : 0;
-            if (sol) {
-              v = d.scr[gs];
-            } else {
-              const float f = d.fl[gs];
-              v = make_float2(f, f);
+          if (gx >= 0 && gy >= 0) {
+            const bool wall = is_wall(d, gx, gy);
+            // a flow wall node carries flow with its inward node (marked 2)
+            int vx = gx, vy = gy;
+            if (WALLS && wall) inward_of(d, gx, gy, vx, vy);
+            if (!wall || WALLS) {
+              const int gs = vy * d.nx + vx;
+              const bool vs = solved(d, (vy / TE) * d.etx + (vx / TE), stamp);
+              sol = wall ? 2 : vs ? 1 : 0;
+              if (vs) {
+                v = d.scr[gs];
+              } else {
+                const float f = d.fl[gs];
+                v = make_float2(f, f);
+              }
             }
           }
           sp[k] = v;
@@ -469,9 +507,11 @@ __global__ void __launch_bounds__(CB) enthalpy_commit_kernel(Dev d) {
             const bool po = pp.x >= d.f_act, pn = pp.y >= d.f_act;
             if ((ao && po) == (an && pn)) continue;
             // link (x, x + e_i) belongs to x for E, N, NE, NW, otherwise to the
-            // partner; a partner in a tile not solved this step cannot handle it
+            // partner; a partner in a tile not solved this step cannot handle it.
+            // A link to a flow wall belongs to x when x changed, else to the
+            // wall's inward node (below).
             const bool own = (i == 1 || i == 2 || i == 5 || i == 6);
-            if (!own && ssolved[q]) continue;
+            if (ssolved[q] == 2 ? ao == an : (!own && ssolved[q])) continue;
             const int px = wrapx(d, x + ex9(i)), py = wrapy(d, y + ey9(i));
             const long long A = (long long)i * n + (py * d.nx + px);
             const long long B = (long long)opp9(i) * n + s;
@@ -479,6 +519,27 @@ __global__ void __launch_bounds__(CB) enthalpy_commit_kernel(Dev d) {
             st_pop(d, d.f, A, ld_pop(d, d.f, B));
             st_pop(d, d.f, B, t);
           }
+        }
+      }
+      // links of flow walls whose inward node changed (tiles along the walls)
+      if (WALLS && lk &&
+          (X0 == 0 || Y0 == 0 || X0 + TE >= d.nx - 1 || Y0 + TE >= d.ny - 1)) {
+        for (int k = tid; k < TE * TE; k += CB) {
+          const int ly = k / TE, lx = k - ly * TE;
+          const int x = X0 + lx, y = Y0 + ly;
+          if (x >= d.nx || y >= d.ny || is_wall(d, x, y)) continue;
+          int ix, iy;
+          bool inw = false;
+          for (int j = 1; j < 9 && !inw; ++j) {
+            const int wx = wrapx(d, x + ex9(j)), wy = wrapy(d, y + ey9(j));
+            if (wx < 0 || wy < 0 || !is_wall(d, wx, wy)) continue;
+            inward_of(d, wx, wy, ix, iy);
+            inw = ix == x && iy == y;
+          }
+          if (!inw) continue;
+          const float2 p = d.scr[y * d.nx + x];
+          const bool ao = p.x >= d.f_act, an = p.y >= d.f_act;
+          if (ao != an) wall_links<PAR>(d, x, y, ao, an, stamp);
         }
       }
     }
@@ -531,8 +592,15 @@ void launch_enthalpy_solve(const Dev& d, int parity, cudaStream_t s) {
 }
 
 void launch_enthalpy_commit(const Dev& d, int parity, cudaStream_t s) {
-  if (parity == 0) enthalpy_commit_kernel<0><<<d.cgrid, CB, 0, s>>>(d);
-  else enthalpy_commit_kernel<1><<<d.cgrid, CB, 0, s>>>(d);
+  // flow walls add their links to the re-pairing (a variant of its own, which
+  // leaves the common one's registers alone)
+  if (d.flow && d.flow_walls) {
+    if (parity == 0) enthalpy_commit_kernel<0, true><<<d.cgrid, CB, 0, s>>>(d);
+    else enthalpy_commit_kernel<1, true><<<d.cgrid, CB, 0, s>>>(d);
+  } else {
+    if (parity == 0) enthalpy_commit_kernel<0, false><<<d.cgrid, CB, 0, s>>>(d);
+    else enthalpy_commit_kernel<1, false><<<d.cgrid, CB, 0, s>>>(d);
+  }
 }
 
 }  // namespace lbm

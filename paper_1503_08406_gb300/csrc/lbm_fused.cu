@@ -11,6 +11,16 @@ void launch_fused_f32(const Dev& d, const TmaMaps* m, int parity, int mode, cuda
 void launch_fused_f16(const Dev& d, const TmaMaps* m, int parity, int mode, cudaStream_t s);
 void launch_fused_bf16(const Dev& d, const TmaMaps* m, int parity, int mode, cudaStream_t s);
 bool tma_setup_f32(Dev& d, TmaMaps* m);
+void launch_flow_walls_f32(const Dev& d, int parity, int mode, cudaStream_t s);
+void launch_flow_walls_f16(const Dev& d, int parity, int mode, cudaStream_t s);
+void launch_flow_walls_bf16(const Dev& d, int parity, int mode, cudaStream_t s);
+
+void launch_flow_walls(const Dev& d, int parity, int mode, cudaStream_t s) {
+  if (!d.flow || !d.flow_walls) return;
+  if (d.storage == 1) launch_flow_walls_f16(d, parity, mode, s);
+  else if (d.storage == 2) launch_flow_walls_bf16(d, parity, mode, s);
+  else launch_flow_walls_f32(d, parity, mode, s);
+}
 bool tma_setup_f16(Dev& d, TmaMaps* m);
 bool tma_setup_bf16(Dev& d, TmaMaps* m);
 

@@ -165,16 +165,82 @@ __device__ __forceinline__ Geo node_geo(const Dev& d, int x, int y) {
   return q;
 }
 
+// The flow collision of one node, Eq. (16)-(28): f (nine populations as
+// deviations f_i - w_i rho0) relaxed in moment space with the porous force and
+// buoyancy at temperature T, liquid fraction flc, porosity phi and
+// permeability K; fp gets the post-collision deviations, (ux, uy) the velocity.
+__device__ __forceinline__ void flow_collide(const Dev& d, const float f[9], float T, float flc,
+                                             float phi, float K, float fp[9], float& ux,
+                                             float& uy) {
+  // populations are stored as deviations from the rest equilibrium,
+  // f_i - w_i rho0 (sum_i e_i w_i = 0, so j needs no correction)
+  const float drho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+  const float jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+  const float jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+  float Fx, Fy;
+  velocity(jx, jy, T, flc, phi, K, d, ux, uy, Fx, Fy);
+  const float varphi = phi * flc;
+  const float ivp = 1.f / varphi;
+  const float rho0 = d.rho0;
+  // moments of the deviations, M (f - w rho0); M (w rho0) = (rho0, -2 rho0, rho0, 0, ..., 0)
+  const float sa = f[1] + f[2] + f[3] + f[4];
+  const float sd = f[5] + f[6] + f[7] + f[8];
+  const float m1 = -4.f * f[0] - sa + 2.f * sd;
+  const float m2 = 4.f * f[0] - 2.f * sa + sd;
+  const float m4 = -2.f * f[1] + 2.f * f[3] + f[5] - f[6] - f[7] + f[8];
+  const float m6 = -2.f * f[2] + 2.f * f[4] + f[5] + f[6] - f[7] - f[8];
+  const float m7 = f[1] - f[2] + f[3] - f[4];
+  const float m8 = f[5] - f[6] + f[7] - f[8];
+  const float uu = ux * ux + uy * uy;
+  // non-equilibrium parts m - m^eq of e and eps, Eq. (19), with rho = rho0 + drho
+  const float ne1 = m1 + 2.f * drho - 3.f * rho0 * uu * ivp;
+  const float ne2 = m2 - drho + 3.f * rho0 * uu * ivp;
+  // forcing moments, Eq. (22)
+  const float uF = ux * Fx + uy * Fy;
+  const float S1 = 6.f * rho0 * uF * ivp;
+  const float S7 = 2.f * rho0 * (ux * Fx - uy * Fy) * ivp;
+  const float S8 = rho0 * (ux * Fy + uy * Fx) * ivp;
+  // m+ - m = -Lambda (m - m^eq) + (I - Lambda/2) S, Eq. (20); for the
+  // conserved moments this is 0 (rho) and rho0 F (momentum, with Eq. 25)
+  const float d1 = -d.s_e * ne1 + (1.f - 0.5f * d.s_e) * S1;
+  const float d2 = -d.s_eps * ne2 - (1.f - 0.5f * d.s_eps) * S1;
+  const float d3 = rho0 * Fx;
+  const float d4 = -d.s_q * (m4 + rho0 * ux) - (1.f - 0.5f * d.s_q) * rho0 * Fx;
+  const float d5 = rho0 * Fy;
+  const float d6 = -d.s_q * (m6 + rho0 * uy) - (1.f - 0.5f * d.s_q) * rho0 * Fy;
+  const float d7 = -d.s_nu * (m7 - rho0 * (ux * ux - uy * uy) * ivp) + (1.f - 0.5f * d.s_nu) * S7;
+  const float d8 = -d.s_nu * (m8 - rho0 * ux * uy * ivp) + (1.f - 0.5f * d.s_nu) * S8;
+  // f+ = f + M^-1 (m+ - m), M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
+  const float a1 = d1 * (1.f / 36.f), a2 = d2 * (1.f / 36.f);
+  const float a3 = d3 * (1.f / 6.f), a4 = d4 * (1.f / 12.f);
+  const float a5 = d5 * (1.f / 6.f), a6 = d6 * (1.f / 12.f);
+  const float a7 = d7 * 0.25f, a8 = d8 * 0.25f;
+  const float c_ax = -a1 - 2.f * a2;   // common part of the axis directions
+  const float c_dg = 2.f * a1 + a2;    // common part of the diagonals
+  fp[0] = f[0] - 4.f * a1 + 4.f * a2;
+  fp[1] = f[1] + c_ax + a3 - 2.f * a4 + a7;
+  fp[2] = f[2] + c_ax + a5 - 2.f * a6 - a7;
+  fp[3] = f[3] + c_ax - a3 + 2.f * a4 + a7;
+  fp[4] = f[4] + c_ax - a5 + 2.f * a6 - a7;
+  fp[5] = f[5] + c_dg + a3 + a4 + a5 + a6 + a8;
+  fp[6] = f[6] + c_dg - a3 - a4 + a5 + a6 - a8;
+  fp[7] = f[7] + c_dg - a3 - a4 - a5 - a6 + a8;
+  fp[8] = f[8] + c_dg + a3 + a4 - a5 - a6 - a8;
+}
+
 // The update of one non-wall node from its gathered inputs: fln = f_l of the
 // 3x3 neighbourhood (-1 on walls), gin = its five thermal populations, f = its
 // nine flow populations as streamed from the neighbours, fb = (odd steps) the
 // populations reflected at each link, used where the neighbour carries no
-// flow.  Writes the post-collision populations to their AA slots and returns
-// whether the node fails the phase-change screen.
+// flow.  wact (flow walls only): bit i set when neighbour i is a wall node that
+// carries flow (its inward node does), so that the link streams instead of
+// reflecting.  Writes the post-collision populations to their AA slots and
+// returns whether the node fails the phase-change screen.
 template <typename S, int PAR, bool FLOW, bool EDGE = true>
 __device__ __forceinline__ bool node_update(const Dev& d, int x, int y, const Geo& q,
                                             const float fln[9], const float gin[5], float f[9],
-                                            const float fb[9], float phi, float K) {
+                                            const float fb[9], float phi, float K,
+                                            unsigned wact = 0u) {
   const int nx = d.nx, ny = d.ny;
   const int n = (int)d.n;
   const int s = q.s;
@@ -197,67 +263,14 @@ __device__ __forceinline__ bool node_update(const Dev& d, int x, int y, const Ge
     // neighbour flow activity, directions 1..8 (E, N, W, S, NE, NW, SW, SE)
     bool act[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) act[i] = fln[i] >= fa;
+    for (int i = 0; i < 9; ++i) act[i] = fln[i] >= fa || ((wact >> i) & 1u);
     if (PAR == 1) {
 #pragma unroll
       for (int i = 1; i < 9; ++i)
         if (!act[opp9(i)]) f[i] = fb[i];
     }
-    // populations are stored as deviations from the rest equilibrium,
-    // f_i - w_i rho0 (sum_i e_i w_i = 0, so j needs no correction)
-    const float drho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
-    const float jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
-    const float jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
-    float Fx, Fy;
-    velocity(jx, jy, T, flc, phi, K, d, ux, uy, Fx, Fy);
-    const float varphi = phi * flc;
-    const float ivp = 1.f / varphi;
-    const float rho0 = d.rho0;
-    // moments of the deviations, M (f - w rho0); M (w rho0) = (rho0, -2 rho0, rho0, 0, ..., 0)
-    const float sa = f[1] + f[2] + f[3] + f[4];
-    const float sd = f[5] + f[6] + f[7] + f[8];
-    const float m1 = -4.f * f[0] - sa + 2.f * sd;
-    const float m2 = 4.f * f[0] - 2.f * sa + sd;
-    const float m4 = -2.f * f[1] + 2.f * f[3] + f[5] - f[6] - f[7] + f[8];
-    const float m6 = -2.f * f[2] + 2.f * f[4] + f[5] + f[6] - f[7] - f[8];
-    const float m7 = f[1] - f[2] + f[3] - f[4];
-    const float m8 = f[5] - f[6] + f[7] - f[8];
-    const float uu = ux * ux + uy * uy;
-    // non-equilibrium parts m - m^eq of e and eps, Eq. (19), with rho = rho0 + drho
-    const float ne1 = m1 + 2.f * drho - 3.f * rho0 * uu * ivp;
-    const float ne2 = m2 - drho + 3.f * rho0 * uu * ivp;
-    // forcing moments, Eq. (22)
-    const float uF = ux * Fx + uy * Fy;
-    const float S1 = 6.f * rho0 * uF * ivp;
-    const float S7 = 2.f * rho0 * (ux * Fx - uy * Fy) * ivp;
-    const float S8 = rho0 * (ux * Fy + uy * Fx) * ivp;
-    // m+ - m = -Lambda (m - m^eq) + (I - Lambda/2) S, Eq. (20); for the
-    // conserved moments this is 0 (rho) and rho0 F (momentum, with Eq. 25)
-    const float d1 = -d.s_e * ne1 + (1.f - 0.5f * d.s_e) * S1;
-    const float d2 = -d.s_eps * ne2 - (1.f - 0.5f * d.s_eps) * S1;
-    const float d3 = rho0 * Fx;
-    const float d4 = -d.s_q * (m4 + rho0 * ux) - (1.f - 0.5f * d.s_q) * rho0 * Fx;
-    const float d5 = rho0 * Fy;
-    const float d6 = -d.s_q * (m6 + rho0 * uy) - (1.f - 0.5f * d.s_q) * rho0 * Fy;
-    const float d7 = -d.s_nu * (m7 - rho0 * (ux * ux - uy * uy) * ivp) + (1.f - 0.5f * d.s_nu) * S7;
-    const float d8 = -d.s_nu * (m8 - rho0 * ux * uy * ivp) + (1.f - 0.5f * d.s_nu) * S8;
-    // f+ = f + M^-1 (m+ - m), M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
-    const float a1 = d1 * (1.f / 36.f), a2 = d2 * (1.f / 36.f);
-    const float a3 = d3 * (1.f / 6.f), a4 = d4 * (1.f / 12.f);
-    const float a5 = d5 * (1.f / 6.f), a6 = d6 * (1.f / 12.f);
-    const float a7 = d7 * 0.25f, a8 = d8 * 0.25f;
-    const float c_ax = -a1 - 2.f * a2;   // common part of the axis directions
-    const float c_dg = 2.f * a1 + a2;    // common part of the diagonals
     float fp[9];
-    fp[0] = f[0] - 4.f * a1 + 4.f * a2;
-    fp[1] = f[1] + c_ax + a3 - 2.f * a4 + a7;
-    fp[2] = f[2] + c_ax + a5 - 2.f * a6 - a7;
-    fp[3] = f[3] + c_ax - a3 + 2.f * a4 + a7;
-    fp[4] = f[4] + c_ax - a5 + 2.f * a6 - a7;
-    fp[5] = f[5] + c_dg + a3 + a4 + a5 + a6 + a8;
-    fp[6] = f[6] + c_dg - a3 - a4 + a5 + a6 - a8;
-    fp[7] = f[7] + c_dg - a3 - a4 - a5 - a6 + a8;
-    fp[8] = f[8] + c_dg + a3 + a4 - a5 - a6 - a8;
+    flow_collide(d, f, T, flc, phi, K, fp, ux, uy);
     if (PAR == 0) {
 #pragma unroll
       for (int i = 0; i < 9; ++i) fstore(&F[opp9(i) * n + s], fp[i], rnd);
@@ -362,6 +375,23 @@ __device__ __forceinline__ bool node_update(const Dev& d, int x, int y, const Ge
   return unsafe;
 }
 
+// Flow walls (Sec. 4): which wall neighbours of node (x, y) carry flow, as bits
+// 1..8 of a mask; flat(dx, dy) gives f_l of the node at offset (dx, dy), and a
+// wall neighbour's inward node is always within one node of (x, y).
+template <typename FlAt>
+__device__ __forceinline__ unsigned wall_activity(const Dev& d, int x, int y, const Geo& q,
+                                                  FlAt flat) {
+  unsigned m = 0u;
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    if (!q.wl[i]) continue;
+    int ix, iy;
+    inward_of(d, x + ex9(i), y + ey9(i), ix, iy);
+    if (flat(ix - x, iy - y) >= d.f_act) m |= 1u << i;
+  }
+  return m;
+}
+
 // Once per step (the near-tile launch runs after the previous step's enthalpy
 // kernels, the last readers of the other list): stamp the step and empty the
 // next step's list.
@@ -379,6 +409,142 @@ __device__ __forceinline__ bool takes_tile(const Dev& d, int et) {
   if (MODE == 0) return true;
   const bool nr = d.nearmap[(1 - PAR) * d.ntiles + et] == d.ctr[1 - PAR];
   return (MODE == 2) == nr;
+}
+
+// ---- flow walls (Sec. 4, non-equilibrium extrapolation) ---------------------
+//
+// With flow walls on, a wall node x_b whose inward node x_f carries flow takes,
+// before collision, f^eq(rho_f, 0) + f(x_f) - f^eq(rho_f, u_f) (rho, u and
+// varphi of x_f; the u-terms of Eq. (29) only, since f^eq's rho-term cancels),
+// collides with x_f's T, f_l, phi and K, and streams like a flow node; the
+// links from its neighbours into it stream instead of reflecting.  This kernel
+// does that for the wall nodes, one thread each, before the step's
+// stream-collide pass overwrites x_f's populations (in the AA pattern a node
+// reads and writes the same slots, and x_b only writes slots that nobody else
+// reads or writes in the step).  MODE 1 / 2 take the wall nodes whose x_f lies
+// in a far / near enthalpy tile, as the split stream-collide passes do.
+template <typename S, int PAR, int MODE>
+__global__ void __launch_bounds__(256) flow_wall_kernel(Dev d) {
+  const int nx = d.nx, ny = d.ny, n = (int)d.n;
+  const int nbot = d.wall_b ? nx : 0, ntop = d.wall_t ? nx : 0;
+  const int ylo = d.wall_b ? 1 : 0, yhi = d.wall_t ? ny - 1 : ny;
+  const int nleft = d.wall_l ? yhi - ylo : 0, nright = d.wall_r ? yhi - ylo : 0;
+  const int total = nbot + ntop + nleft + nright;
+  S* F = static_cast<S*>(d.f);
+  const S* G = static_cast<const S*>(d.g);
+  const float r0 = d.wt0 * d.g_ref, r1 = d.wt1 * d.g_ref;
+  const float w9[9] = {4.f / 9.f, 1.f / 9.f, 1.f / 9.f, 1.f / 9.f, 1.f / 9.f,
+                       1.f / 36.f, 1.f / 36.f, 1.f / 36.f, 1.f / 36.f};
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+    int x, y, kk = k;
+    if (kk < nbot) {
+      x = kk;
+      y = 0;
+    } else if ((kk -= nbot) < ntop) {
+      x = kk;
+      y = ny - 1;
+    } else if ((kk -= ntop) < nleft) {
+      x = 0;
+      y = ylo + kk;
+    } else {
+      x = nx - 1;
+      y = ylo + kk - nleft;
+    }
+    int ix, iy;
+    inward_of(d, x, y, ix, iy);
+    if (is_wall(d, ix, iy)) continue;   // a lattice too narrow to have an inward node
+    const int sf = iy * nx + ix;
+    const float flf = d.fl[sf];
+    if (flf < d.f_act) continue;   // the inward node carries no flow: the wall reflects
+    if (MODE != 0 && !takes_tile<PAR, MODE>(d, (iy / TE) * d.etx + ix / TE)) continue;
+    // x_f's populations before the step's collision, as its own update reads them
+    float f[9], g[5];
+    if (PAR == 0) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) f[i] = Pop<S>::ld(&F[i * n + sf]);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) g[i] = gload(&G[i * n + sf], i ? r1 : r0);
+    } else {
+      f[0] = Pop<S>::ld(&F[sf]);
+#pragma unroll
+      for (int i = 1; i < 9; ++i) {
+        const int sx = wrapx(d, ix - ex9(i)), sy = wrapy(d, iy - ey9(i));
+        bool a;   // does the source node carry flow?
+        if (is_wall(d, sx, sy)) {
+          int jx, jy;
+          inward_of(d, sx, sy, jx, jy);
+          a = d.fl[jy * nx + jx] >= d.f_act;
+        } else {
+          a = d.fl[sy * nx + sx] >= d.f_act;
+        }
+        f[i] = a ? Pop<S>::ld(&F[opp9(i) * n + sy * nx + sx]) : Pop<S>::ld(&F[i * n + sf]);
+      }
+      g[0] = gload(&G[sf], r0);
+#pragma unroll
+      for (int i = 1; i < 5; ++i) {
+        const int sx = wrapx(d, ix - ex9(i)), sy = wrapy(d, iy - ey9(i));
+        g[i] = gload(&G[opp5(i) * n + sy * nx + sx], r1);
+      }
+    }
+    const float T = g[0] + g[1] + g[2] + g[3] + g[4];
+    const float phi = d.phi[sf], K = d.K[sf];
+    const float jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+    const float jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+    float ux, uy, Fx, Fy;
+    velocity(jx, jy, T, flf, phi, K, d, ux, uy, Fx, Fy);
+    const float ivp = 1.f / (phi * flf);
+    const float uu = ux * ux + uy * uy;
+    float fin[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const float eu = ex9(i) * ux + ey9(i) * uy;
+      fin[i] = f[i] - w9[i] * d.rho0 * (3.f * eu + 4.5f * eu * eu * ivp - 1.5f * uu * ivp);
+    }
+    float fp[9], ub, vb;
+    flow_collide(d, fin, T, flf, phi, K, fp, ub, vb);
+    const int sb = y * nx + x;
+    unsigned rnd = 0u;
+    if constexpr (!std::is_same<S, float>::value)
+      rnd = mix32((unsigned)sb ^ mix32((unsigned)d.ctr[1 - PAR]));
+    if (PAR == 0) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) fstore(&F[opp9(i) * n + sb], fp[i], rnd);
+    } else {
+      fstore(&F[sb], fp[0], rnd);
+#pragma unroll
+      for (int i = 1; i < 9; ++i) {
+        const int zx = wrapx(d, x + ex9(i)), zy = wrapy(d, y + ey9(i));
+        bool a = false;   // does the receiving node carry flow?
+        if (zx >= 0 && zy >= 0) {
+          if (is_wall(d, zx, zy)) {
+            int jx2, jy2;
+            inward_of(d, zx, zy, jx2, jy2);
+            a = d.fl[jy2 * nx + jx2] >= d.f_act;
+          } else {
+            a = d.fl[zy * nx + zx] >= d.f_act;
+          }
+        }
+        fstore(&F[a ? i * n + zy * nx + zx : opp9(i) * n + sb], fp[i], rnd);
+      }
+    }
+  }
+}
+
+template <typename S>
+static void launch_flow_walls_t(const Dev& d, int parity, int mode, cudaStream_t s) {
+  const int total = 2 * (d.nx + d.ny);
+  const int grid = (total + 255) / 256;
+#define LBM_FW(P, M) flow_wall_kernel<S, P, M><<<grid, 256, 0, s>>>(d)
+  if (parity == 0) {
+    if (mode == 0) LBM_FW(0, 0);
+    else if (mode == 1) LBM_FW(0, 1);
+    else LBM_FW(0, 2);
+  } else {
+    if (mode == 0) LBM_FW(1, 0);
+    else if (mode == 1) LBM_FW(1, 1);
+    else LBM_FW(1, 2);
+  }
+#undef LBM_FW
 }
 
 // ---- ordinary-load kernel ----------------------------------------------------
@@ -437,7 +603,12 @@ __global__ void __launch_bounds__(TX* TY, 4) fused_step_kernel(Dev d) {
         }
       }
     }
-    unsafe = node_update<S, PAR, FLOW>(d, x, y, q, fln, g, f, fb, phi, K);
+    unsigned wact = 0u;
+    if (FLOW && d.flow_walls)
+      wact = wall_activity(d, x, y, q, [&](int dx, int dy) {
+        return d.fl[(long long)wrapy(d, y + dy) * nx + wrapx(d, x + dx)];
+      });
+    unsafe = node_update<S, PAR, FLOW>(d, x, y, q, fln, g, f, fb, phi, K, wact);
   }
   if (__any_sync(FULL, unsafe) && lane == 0)
     mark_tile(d, (y / TE) * d.etx + (blockIdx.x * TX) / TE, PAR);
@@ -606,7 +777,10 @@ __device__ __forceinline__ bool tma_node(const Dev& d, const unsigned char* sb, 
           }
         }
       }
-      unsafe = node_update<S, PAR, FLOW, EDGE>(d, x, y, q, fln, g, f, fb, phi, K);
+      unsigned wact = 0u;
+      if (FLOW && EDGE && d.flow_walls)
+        wact = wall_activity(d, x, y, q, [&](int dx, int dy) { return sFL[c + dy * WX + dx]; });
+      unsafe = node_update<S, PAR, FLOW, EDGE>(d, x, y, q, fln, g, f, fb, phi, K, wact);
   }
   return unsafe;
 }

@@ -3,6 +3,10 @@
 
 namespace lbm {
 
+void launch_flow_walls_bf16(const Dev& d, int parity, int mode, cudaStream_t s) {
+  launch_flow_walls_t<__nv_bfloat16>(d, parity, mode, s);
+}
+
 void launch_fused_bf16(const Dev& d, const TmaMaps* m, int parity, int mode, cudaStream_t s) {
   launch_fused_t<__nv_bfloat16>(d, m, parity, mode, s);
 }

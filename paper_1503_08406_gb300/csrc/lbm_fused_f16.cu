@@ -3,6 +3,10 @@
 
 namespace lbm {
 
+void launch_flow_walls_f16(const Dev& d, int parity, int mode, cudaStream_t s) {
+  launch_flow_walls_t<__half>(d, parity, mode, s);
+}
+
 void launch_fused_f16(const Dev& d, const TmaMaps* m, int parity, int mode, cudaStream_t s) {
   launch_fused_t<__half>(d, m, parity, mode, s);
 }

@@ -3,6 +3,10 @@
 
 namespace lbm {
 
+void launch_flow_walls_f32(const Dev& d, int parity, int mode, cudaStream_t s) {
+  launch_flow_walls_t<float>(d, parity, mode, s);
+}
+
 void launch_fused_f32(const Dev& d, const TmaMaps* m, int parity, int mode, cudaStream_t s) {
   launch_fused_t<float>(d, m, parity, mode, s);
 }

@@ -62,6 +62,8 @@ struct Dev {
   float z_a, z_e, z_nu;      // 1/tau_T, zeta_e, zeta_nu
   int alpha_var;             // tau_T depends on f_l (alpha_l != alpha_s)
   float tauT_l, inv_aratio;  // liquid tau_T, alpha_s / alpha_l
+  int flow_walls;            // 1: flow walls by non-equilibrium extrapolation (Sec. 4): a wall
+                             // node whose inward node carries flow collides and streams
   int sigma_var;             // sigma follows f_l, Eq. (7): sigma_s + f_l (sigma - sigma_s)
   float sigma_s;             // its solid value (sigma is the liquid one)
   float varpi, csT2, sigma;
@@ -295,6 +297,12 @@ __device__ __forceinline__ bool is_wall(const Dev& d, int x, int y) {
   return (d.wall_l && x == 0) || (d.wall_r && x == d.nx - 1) || (d.wall_b && y == 0) ||
          (d.wall_t && y == d.ny - 1);
 }
+// inward neighbour of wall node (x, y): one node into the lattice from each wall
+// it lies on (the diagonal neighbour at a corner)
+__device__ __forceinline__ void inward_of(const Dev& d, int x, int y, int& ix, int& iy) {
+  ix = (d.wall_l && x == 0) ? 1 : (d.wall_r && x == d.nx - 1) ? d.nx - 2 : x;
+  iy = (d.wall_b && y == 0) ? 1 : (d.wall_t && y == d.ny - 1) ? d.ny - 2 : y;
+}
 
 // sigma_l / sigma(f_l) with the heat-capacity ratio of Eq. (7) linear in f_l
 // (1 when sigma does not follow f_l)
@@ -365,6 +373,10 @@ void launch_nonfinite(const Dev& d, int nblocks, cudaStream_t s);
 // one CTA waiting, with a limit of limit_ns, on an mbarrier nothing completes
 // (sets stats[4] when the wait gives up, as a timed-out bulk copy does)
 void launch_wait_probe(const Dev& d, long long limit_ns, cudaStream_t s);
+// the wall nodes' flow update when flow walls are on (mode as for launch_fused,
+// by the enthalpy tile of each wall node's inward node); runs before the
+// stream-collide pass of the same step and mode
+void launch_flow_walls(const Dev& d, int parity, int mode, cudaStream_t s);
 void launch_validate(const Dev& d, const float* phi, const float* K, const float* T0,
                      const float* fl0, int* bad, cudaStream_t s);
 

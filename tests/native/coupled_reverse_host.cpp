@@ -57,14 +57,15 @@ extern "C" int coupled_reverse_step_f64(int nx, int ny, int per_x, int per_y, co
   const int ex[5] = {0, 1, 0, -1, 0};
   const int ey[5] = {0, 0, 1, 0, -1};
 
-  // the fixed point's adjoint on the band (0 < f_l(n+1) < 1, not a wall)
+  // the fixed point's adjoint on the band (f_l(n+1) inside (0, 1) by
+  // ADJ_BAND_EPS, not a wall), as the band kernel takes it
   std::vector<double> a(n), rhs(n, 0.0), mu(n, 0.0), mo(n, 0.0);
   std::vector<char> band(n);
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
       const int s = y * nx + x;
       a[s] = phi[s] * A.lat;
-      band[s] = !A.geo.wall(x, y) && fl1[s] > 0 && fl1[s] < 1;
+      band[s] = !A.geo.wall(x, y) && lbm::adj_mushy(fl1[s]);
       if (!band[s]) continue;
       double L = 0;
       for (int i = 0; i < 5; ++i) {

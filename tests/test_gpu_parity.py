@@ -254,6 +254,74 @@ def test_porous_gallium_cavity_with_solid_sigma(lbm, oracle_mod):
     assert abs(r_g["melt_frac"] / r_o["melt_frac"] - 1) < 1e-4
 
 
+def _walls_errors(lat, o):
+    """Field errors with rho on the lattice nodes only: what a wall node's
+    slots hold between steps differs by design (the extrapolation rewrites
+    them before they are used)."""
+    got, exp = lat.macros(), o.macros()
+    err = _errors(got, exp)
+    inner = (slice(1, -1), slice(1, -1))
+    err["rho"] = _errors({"rho": got["rho"][inner]}, {"rho": exp["rho"][inner]}, ("rho",))["rho"]
+    return err
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("steps", [1, 2, 3, 51])
+def test_extrapolated_flow_walls_match_oracle(lbm, oracle_mod, steps, variant):
+    """flow_walls = 1, the non-equilibrium extrapolation of Sec. 4 on the
+    no-slip walls, in the melted cavity (walls on all four sides, corners
+    included), with both stream-collide kernels and both step parities."""
+    w = _f32(W.melted_cavity(64))
+    w.params = {**w.params, "flow_walls": 1}
+    lat = _gpu(lbm, w, steps, kernel_variant=variant)
+    assert lat.kernel_variant() == variant
+    err = _walls_errors(lat, _ora(oracle_mod, w, steps))
+    assert max(err.values()) < 2e-5, err
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_extrapolated_flow_walls_with_moving_front(lbm, oracle_mod, variant):
+    """flow_walls = 1 while the front runs along the top and bottom walls:
+    wall nodes start and stop carrying flow with their inward nodes, so the
+    links into them are re-paired as the phase changes (ragged 40^2, tiles
+    of 32), 400 steps."""
+    w = _f32(W.melted_cavity(40))
+    w.params = {**w.params, "flow_walls": 1}
+    steps = 400
+    lat = _gpu(lbm, w, steps, kernel_variant=variant)
+    o = _ora(oracle_mod, w, steps)
+    err = _walls_errors(lat, o)
+    assert max(err.values()) < 5e-5, err
+    fl = o.macros()["fl"]
+    rows = [1, w.ny - 2]
+    changed = (fl[rows, 1:-1] >= 1e-3) != (w.fl0[rows, 1:-1] >= 1e-3)
+    assert changed.sum() > 0   # wall nodes did change activity in this run
+
+
+def test_extrapolated_flow_walls_brinkman_channel(lbm, oracle_mod):
+    """Body-force-driven channel between two flow walls (periodic in y, 66 x
+    4): after 6,000 steps the GPU profile is the oracle's to 1e-5 and the
+    fully developed Brinkman-Forchheimer profile with the no-slip wall on the
+    wall nodes to 1e-3."""
+    nx, ny, phi, K, G = 66, 4, 0.5, 12.5, 1e-8
+    params = dict(bc=("dirichlet", "dirichlet", "periodic", "periodic"), T_bc=(1.0, 1.0, 0, 0),
+                  flow=1, tau_nu=1.0, tau_T=1.0, g_beta=G, Pr=1.0, T_ref=0.0, flow_walls=1)
+    w = _f32(W.Workload("channel", nx, ny, params, np.full((ny, nx), phi), np.full((ny, nx), K),
+                        np.ones((ny, nx)), np.ones((ny, nx))))
+    steps = 6000
+    lat = _gpu(lbm, w, steps)
+    o = _ora(oracle_mod, w, steps)
+    got, exp = lat.macros(), o.macros()
+    uy, uy_o = got["uy"][1].astype(np.float64), exp["uy"][1]
+    assert np.abs(uy - uy_o).max() < 1e-5 * np.abs(uy_o).max()
+    d = o.derived()
+    r = np.sqrt(phi * d["nu_l"] / (d["nu_e"] * K))
+    x = np.arange(nx)
+    c = (nx - 1) / 2.0
+    u_node = G * K / d["nu_l"] * (1 - np.cosh(r * (x - c)) / np.cosh(r * c))
+    assert np.abs(uy[1:-1] - u_node[1:-1]).max() < 1e-3 * u_node.max()
+
+
 def test_full_size_cavity_matches_oracle(lbm, oracle_mod):
     """2048^2 (the benchmark size), left third melted so flow runs on a
     third of the lattice: full-field comparison after 3 steps."""

@@ -174,14 +174,15 @@ def downsample_oracle(oracle_mod):
 
 
 # per-field bars (normwise, and relative for the melted fraction and Nusselt
-# number) at about 3x the values measured on this workload
+# number) at about 3x the values measured on this workload; the velocity of
+# the thin early melt layer is small, so its 16-bit error is large normwise
 DOWNSAMPLE_BARS = {
-    ("fp32", 1000): dict(u=1e-4, T=1e-4, fl=1e-4, melt=1e-5, nu=1e-5),
-    ("fp32", 10000): dict(u=1e-4, T=1e-4, fl=1e-4, melt=1e-4, nu=1e-4),
-    ("fp16", 1000): dict(u=0.1, T=5e-3, fl=2e-2, melt=1e-3, nu=2e-3),
-    ("fp16", 10000): dict(u=0.5, T=2e-2, fl=5e-2, melt=1e-3, nu=5e-3),
-    ("bf16", 1000): dict(u=0.3, T=3e-2, fl=0.1, melt=1e-3, nu=3e-2),
-    ("bf16", 10000): dict(u=0.5, T=5e-2, fl=0.2, melt=5e-3, nu=5e-2),
+    ("fp32", 1000): dict(u=1e-5, T=2e-6, fl=1e-5, melt=1e-7, nu=1e-7),
+    ("fp32", 10000): dict(u=1e-5, T=2e-6, fl=2e-5, melt=2e-7, nu=1e-6),
+    ("fp16", 1000): dict(u=0.4, T=4e-3, fl=1.2e-2, melt=2e-5, nu=1e-4),
+    ("fp16", 10000): dict(u=1.0, T=2e-2, fl=5e-2, melt=2e-4, nu=2e-3),
+    ("bf16", 1000): dict(u=1.0, T=3e-2, fl=0.1, melt=4e-5, nu=3e-3),
+    ("bf16", 10000): dict(u=1.0, T=5e-2, fl=0.2, melt=5e-4, nu=2e-2),
 }
 
 
@@ -192,7 +193,7 @@ def test_precision_study_on_downsampled_cavity(lbm, downsample_oracle, storage):
     printed (pytest -s) and held to the bars above."""
     w, ref = downsample_oracle
     lat = _run(lbm, w, 0, storage)
-    done = 0
+    done, results = 0, []
     for steps in (1000, 10000):
         lat.step(steps - done)
         done = steps
@@ -204,6 +205,8 @@ def test_precision_study_on_downsampled_cavity(lbm, downsample_oracle, storage):
         nu = abs(r["nu_hot"] / ro["nu_hot"] - 1)
         print("precision %s %d steps: u_x %.2e u_y %.2e T %.2e f_l %.2e melted %.2e Nu %.2e" % (
             storage, steps, err["ux"], err["uy"], err["T"], err["fl"], melt, nu))
+        results.append((steps, err, melt, nu))
+    for steps, err, melt, nu in results:
         bar = DOWNSAMPLE_BARS[(storage, steps)]
         assert max(err["ux"], err["uy"]) < bar["u"], (storage, steps, err)
         assert err["T"] < bar["T"] and err["fl"] < bar["fl"], (storage, steps, err)
