@@ -298,6 +298,7 @@ def batched(args, torch):
     torch.cuda.synchronize()
     ms_seq = e0.elapsed_time(e1)
     b = Batch(lats)
+    mode = b.mode()
     b.step(args.warmup)
     torch.cuda.synchronize()
     launches0 = sum(lat.kernel_launches() for lat in lats)
@@ -329,7 +330,9 @@ def batched(args, torch):
         "data": "synthetic",
         "config": {"workload": "batched_cavities_64_seed4", "cells": cells,
                    "sides": sorted({w.nx for w in ws}), "population_storage": args.storage,
-                   "graph": "one CUDA graph per 32 steps, one branch per cavity",
+                   "graph": "one CUDA graph per 32 steps, " + (
+                       "each pass of a step one launch over all cavities" if mode == 1
+                       else "one branch per cavity"),
                    "autotuned": tuned if args.autotune else None,
                    "l2": "state ~%d MB > 129 MB L2; no flush" % (
                        (14 * (4 if args.storage == "fp32" else 2) + 12) * cells // 2**20)},
@@ -447,10 +450,10 @@ def adjoint_coupled(args, torch):
     if keep_all:
         memory = "every state kept (%.2f GB)" % ((args.steps + 1) * st_bytes / 1e9)
     else:
-        memory = ("whole state every %d steps (%d checkpoints, %.2f GB) plus one segment's "
-                  "states (%.2f GB), segments recomputed" % (
+        memory = ("whole state every %d steps (%d checkpoints, %.2f GB) plus two segments' "
+                  "states (%.2f GB: one recomputed beside the reversal of the other)" % (
                       K, args.steps // K + 1, (args.steps // K + 1) * st_bytes / 1e9,
-                      (K + 1) * st_bytes / 1e9))
+                      2 * (K + 1) * st_bytes / 1e9))
     line = {
         "metric": "coupled adjoint time / forward time, %s and its gradients" % args.objective,
         "value": ms_adj / ms_fwd, "unit": "x", "n_gpus": 1, "steps": args.steps,

@@ -294,6 +294,13 @@ int lbm_batch_create(lbm_ctx* const* ctxs, int count, void* stream, lbm_batch** 
  * Asynchronous; LBM_ERR_INVALID_ARG if a context has timing enabled or the
  * contexts' step counts differ in parity. */
 int lbm_batch_step(lbm_batch* b, int64_t nsteps);
+/* How the batch graph launches its kernels: 1 when every context runs the
+ * TMA-staged stream-collide kernel on FP32 storage with the same flow setting,
+ * no flow walls, and there are at most 64 contexts: each pass of a step (far
+ * and near stream-collide tiles, enthalpy solve, commit) is then one launch
+ * over all contexts, each context on its own range of CTAs; 0 otherwise: one
+ * graph branch per context.  The results are the same bits either way. */
+int lbm_batch_mode(const lbm_batch* b);
 void lbm_batch_destroy(lbm_batch* b);
 
 /* Macroscopic fields at the current time (each nx*ny floats, NULL to skip):

@@ -294,9 +294,13 @@ def adjoint_slab(nx: int = 2048, ny: int = 512, seed: int = 0) -> Workload:
 
 
 def adjoint_cavity(n: int = 512, seed: int = 5, source_n: int = 512, melted: float = 0.0,
-                   T_l: float = 0.05, Ra: float = 1e6, Da: float = 1e-4) -> Workload:
+                   T_l: float = 0.05, Ra: float = 1e6, Da: float = 1e-4,
+                   T_c: float = -0.05) -> Workload:
     """The inverse-problem cavity: Ra = 1e6, Pr = 1, Ste = 1, hot left wall
-    (profile 1 in `wall_T_left`, one entry per row), cold right wall at T_m = 0.
+    (profile 1 in `wall_T_left`, one entry per row), cold right wall and
+    initial solid at T_c = -0.05, below the melting range [T_s, T_l] = [0, T_l]
+    by its width: a solid at T_s itself would sit on the clamp's kink of
+    Eq. (42), where the objectives have only one-sided derivatives.
 
     Fields drawn at source_n^2 and block-averaged to n^2 when n < source_n
     (the small copies keep the large field's pattern):
@@ -305,10 +309,10 @@ def adjoint_cavity(n: int = 512, seed: int = 5, source_n: int = 512, melted: flo
       mean(K) = Da H^2;
     - porosity: clip(0.45 + 0.15 g, 0.3, 0.6) as in the heterogeneous cavity
       (16-cell smoothing, seed + 1).
-    Mushy band [T_s, T_l] = [0, T_l] above the melting point: the solid at
-    T_m stays solid, and 0 < f_l < 1 holds across a few cells at the front.
-    ``melted`` > 0 starts the left fraction of the columns liquid with T
-    falling linearly from 1 to 0 (short runs with the front already moving).
+    Mushy band [T_s, T_l] = [0, T_l] above the melting point: 0 < f_l < 1
+    holds across a few cells at the front.  ``melted`` > 0 starts the left
+    fraction of the columns liquid with T falling linearly from 1 to 0 (short
+    runs with the front already moving); the solid beyond is at T_c.
     """
     big = max(source_n, n)
     g = smoothed_gaussian(big, 32.0 / np.sqrt(2.0), seed)
@@ -320,15 +324,16 @@ def adjoint_cavity(n: int = 512, seed: int = 5, source_n: int = 512, melted: flo
     K = np.exp(lnK)
     K *= Da * n * n / K.mean()
     params = dict(bc=("dirichlet", "dirichlet", "adiabatic", "adiabatic"),
-                  T_bc=(1.0, 0.0, 0.0, 0.0), flow=1, Ra=Ra, Pr=1.0, Ma=0.1, J=1.0,
+                  T_bc=(1.0, T_c, 0.0, 0.0), flow=1, Ra=Ra, Pr=1.0, Ma=0.1, J=1.0,
                   lambda_=1.0, sigma=1.0, St=1.0, dT=1.0, H=float(n), T_ref=0.0,
                   T_s=0.0, T_l=T_l)
     phi_f, K_f, T0, fl0 = _cavity_fields(n, phi, K)
+    T0[:, 1:] = T_c
     if melted > 0:
         m = int(round(melted * n))
         x = np.arange(n)[None, :]
         fl0[:, :m] = 1.0
-        T0[:, :] = np.where(x < m, 1.0 - x / float(m), 0.0)
+        T0[:, :] = np.where(x < m, 1.0 - x / float(m), T_c)
         T0[:, 0] = 1.0
     return Workload("adjoint_cavity_%d_seed%d%s" % (n, seed, "_melted%g" % melted if melted else ""),
                     n, n, params, phi_f, K_f, T0, fl0, wall_T_left=np.ones(n),

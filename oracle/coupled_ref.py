@@ -23,15 +23,12 @@ profile:
 
 The flow nodes are chosen by f_l(n) >= f_act, a step function: its derivative
 is 0 wherever it is defined, and finite differences that do not move a node
-across f_act agree with it.  The clamp of Eq. (42) passes derivatives only
-where its output lies more than BAND_EPS = 1e-7 inside (0, 1): a solid held
-at T_s sits on the clamp's kink, where the derivative of the discrete map is
-not defined (exact arithmetic keeps f_l at 0 there, FP32 arithmetic at
-values of order 1e-8), and the mushy branch's linearisation grows without
-bound when it is applied to such nodes.  Finite differences of the oracle
-agree with this reading wherever no node is within 1e-7 of a clamp value.  Square roots of speeds carry a 1e-300 floor so
-that a node at rest has a finite derivative; the forward values are those of
-the oracle.  Scope: one sigma; one thermal diffusivity or, with
+across f_act agree with it.  The clamp of Eq. (42) passes derivatives where
+its output lies strictly inside (0, 1) (at a bound, the clamped side's
+one-sided derivative, 0), as the CUDA adjoint takes it; a node held exactly
+at T_s sits on the kink, where only one-sided derivatives exist.  Square
+roots of speeds carry a 1e-300 floor so that a node at rest has a finite
+derivative; the forward values are those of the oracle.  Scope: one sigma; one thermal diffusivity or, with
 alpha_l != alpha_s (Sec. 4.1), the rate of the flux moments following f_l(n)
 (a wall node's that of its inward node); the flow lattice on or off; any mix
 of periodic axes and wall sides the oracle accepts (left and right walls
@@ -71,17 +68,17 @@ N5 = torch.tensor([[1, 1, 1, 1, 1],
                    [0, 1, -1, 1, -1]], dtype=D)
 CS2 = 1.0 / 3.0
 BC = {"periodic": 0, "dirichlet": 1, "adiabatic": 2}
-BAND_EPS = 1e-7
 
 
 class _Clamp01(torch.autograd.Function):
-    """clamp(z, 0, 1) of Eq. (42), its derivative 1 only where the result lies
-    more than BAND_EPS inside (0, 1)."""
+    """clamp(z, 0, 1) of Eq. (42), its derivative 1 where the result lies
+    strictly inside (0, 1) and 0 elsewhere (torch.clamp's is 1 at the bounds
+    themselves)."""
 
     @staticmethod
     def forward(ctx, z):
         out = torch.clamp(z, 0.0, 1.0)
-        ctx.save_for_backward((out > BAND_EPS) & (out < 1.0 - BAND_EPS))
+        ctx.save_for_backward((out > 0.0) & (out < 1.0))
         return out
 
     @staticmethod

@@ -63,8 +63,7 @@ __device__ __forceinline__ float wt(const Dev& d, int i) { return i == 0 ? d.wt0
 //          nodes' own populations do not reach the next step (the
 //          extrapolation rewrites them).
 // The unclamped nodes of a step are the non-wall nodes with 0 < f_l < 1 after
-// it, ADJ_BAND_EPS inside those bounds (the solver converges to f = z there,
-// and clamps elsewhere); the full
+// it (the solver converges to f = z there, and clamps elsewhere); the full
 // pass of one reversed step lists them for the next (its f(n) is the next
 // one's f(n+1)).
 

@@ -45,8 +45,7 @@ void adj_mul(long long n, float* v, const float* w, cudaStream_t s);
 void adj_a(const Dev& d, float* a, cudaStream_t s);
 // J into out[0]; out holds 129 doubles (the rest: partial sums)
 void adj_objective(const Dev& d, const float* fl, double* out, cudaStream_t s);
-// the band (non-wall nodes with f inside (0, 1) by ADJ_BAND_EPS), appended at
-// list[*count]
+// the band (non-wall nodes with 0 < f < 1), appended at list[*count]
 void adj_list(const Dev& d, const float* f, int* list, int* count, cudaStream_t s);
 // d.fl to base + k n, k = ctr[0], which then advances (ctr[1]: scratch, 0)
 void adj_save(const Dev& d, float* base, unsigned* ctr, cudaStream_t s);

@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <utility>
 #include <vector>
@@ -733,11 +734,38 @@ struct lbm_batch {
   cudaGraphExec_t graph;
   std::vector<int> nl;             // kernels per context in one graph replay
   std::vector<int> egrid, cgrid;   // the contexts' own enthalpy grids, restored at destroy
+  // Batched launches: when every context runs the TMA-staged FP32 kernel with
+  // the same flow setting, each pass of a step is one launch over all of them
+  // (plans for the stream-collide, solve and commit passes; the contexts'
+  // tensor maps in device memory).
+  // The contexts are split into groups of about equal node counts, each group
+  // a branch of the graph, so that one group's enthalpy kernels (latency
+  // bound) run beside another's stream-collide pass (bandwidth bound).
+  bool fused = false;
+  struct Group {
+    std::vector<int> members;                             // context indices
+    lbm::BatchPlan* plan[3] = {nullptr, nullptr, nullptr};  // stream-collide, solve, commit
+    int maps0 = 0;                                        // first entry in dmaps
+  };
+  std::vector<Group> groups;
+  lbm::TmaMaps* dmaps = nullptr;
 };
+
+static void batch_free_plans(lbm_batch* b) {
+  for (auto& g : b->groups)
+    for (auto& p : g.plan) {
+      delete p;
+      p = nullptr;
+    }
+  b->groups.clear();
+  if (b->dmaps) cudaFree(b->dmaps);
+  b->dmaps = nullptr;
+}
 
 void lbm_batch_destroy(lbm_batch* b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
+  batch_free_plans(b);
   for (size_t i = 0; i < b->egrid.size(); ++i) {
     lbm_ctx* c = b->ctx[i];
     c->d.egrid = b->egrid[i];
@@ -793,12 +821,139 @@ int lbm_batch_create(lbm_ctx* const* ctxs, int count, void* stream, lbm_batch** 
     lbm_batch_destroy(b);
     return LBM_ERR_CUDA;
   }
+  // one launch per pass for the whole batch where the contexts allow it
+  bool fast = count <= lbm::BATCH_MAX;
+  for (lbm_ctx* c : b->ctx)
+    fast = fast && c->use_tma && c->p.storage == LBM_STORAGE_FP32 &&
+           c->d.flow == b->ctx[0]->d.flow && !c->d.flow_walls;
+  b->fused = fast;
   *out = b;
   return LBM_OK;
 }
 
+// The plans of the batched launches, from the contexts' current parameters
+// (taken by value into the graph, as a single context's capture does).
+static constexpr int BATCH_GROUPS = 4;
+
+static int batch_plans(lbm_batch* b) {
+  batch_free_plans(b);
+  const int n = (int)b->ctx.size();
+  // Stream-collide: a context's own grid spreads its tiles over every SM (one
+  // or two tiles per CTA for a small lattice, too few to keep its ring of bulk
+  // copies busy).  In a batch the lattices share the GPU: about two waves of
+  // CTAs in all, each taking the same number of tiles.
+  long long tiles = 0;
+  std::vector<long long> nt(n);
+  for (int i = 0; i < n; ++i) {
+    const lbm::Dev& d = b->ctx[i]->d;
+    nt[i] = (long long)((d.nx + lbm::TX - 1) / lbm::TX) * ((d.ny + lbm::TY - 1) / lbm::TY);
+    tiles += nt[i];
+  }
+  const long long slots = b->ctx[0]->d.tslots > 0 ? b->ctx[0]->d.tslots : 1;
+  long long tpc = (tiles + 2 * slots - 1) / (2 * slots);
+  tpc = tpc < 1 ? 1 : tpc > 32 ? 32 : tpc;
+  // groups: largest lattices first, each to the group with the fewest nodes
+  const int ng = n < BATCH_GROUPS ? n : BATCH_GROUPS;
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int c) {
+    return b->ctx[a]->d.n != b->ctx[c]->d.n ? b->ctx[a]->d.n > b->ctx[c]->d.n : a < c;
+  });
+  b->groups.assign(ng, lbm_batch::Group());
+  std::vector<long long> load(ng, 0);
+  for (int i : order) {
+    int g = 0;
+    for (int k = 1; k < ng; ++k)
+      if (load[k] < load[g]) g = k;
+    b->groups[g].members.push_back(i);
+    load[g] += b->ctx[i]->d.n;
+  }
+  std::vector<lbm::TmaMaps> maps;
+  for (auto& G : b->groups) {
+    G.maps0 = (int)maps.size();
+    for (int k = 0; k < 3; ++k) {
+      G.plan[k] = new (std::nothrow) lbm::BatchPlan();
+      if (!G.plan[k]) return LBM_ERR_OOM;
+      lbm::BatchPlan& P = *G.plan[k];
+      P.count = (int)G.members.size();
+      P.start[0] = 0;
+      for (int j = 0; j < P.count; ++j) {
+        const int i = G.members[j];
+        const lbm::Dev& d = b->ctx[i]->d;
+        P.d[j] = d;
+        const int grid = k == 0 ? (int)((nt[i] + tpc - 1) / tpc) : k == 1 ? d.egrid : d.cgrid;
+        P.start[j + 1] = P.start[j] + grid;
+      }
+    }
+    for (int i : G.members) maps.push_back(b->ctx[i]->maps);
+  }
+  if (cudaMalloc(&b->dmaps, n * sizeof(lbm::TmaMaps)) != cudaSuccess) {
+    cudaGetLastError();
+    b->dmaps = nullptr;
+    return LBM_ERR_OOM;
+  }
+  LBM_CUDA(cudaMemcpy(b->dmaps, maps.data(), n * sizeof(lbm::TmaMaps), cudaMemcpyHostToDevice));
+  return LBM_OK;
+}
+
+// LBM_BATCH_STEPS steps of the whole batch: per group, four launches a step on
+// the same schedule as one context's capture (the far tiles of step k + 1 on
+// the group's second stream beside the enthalpy kernels of step k), each
+// launch over every context of the group; the groups are branches forked from
+// the capture's start and joined at its end.
+static int batch_capture_fused(lbm_batch* b) {
+  LBM_TRY(batch_plans(b));
+  lbm::batch_setup();
+  const bool flow = b->ctx[0]->d.flow != 0;
+  cudaGraph_t gr = nullptr;
+  if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return LBM_ERR_CUDA;
+  }
+  cudaEventRecord(b->ev_done, b->cap);
+  int nl = 0;
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    const auto& G = b->groups[gi];
+    lbm_ctx* c0 = b->ctx[G.members[0]];
+    const lbm::BatchPlan &PF = *G.plan[0], &PS = *G.plan[1], &PC = *G.plan[2];
+    const lbm::TmaMaps* maps = b->dmaps + G.maps0;
+    cudaStreamWaitEvent(c0->cap, b->ev_done, 0);
+    for (int k = 0; k < LBM_BATCH_STEPS; ++k) {
+      const int par = k & 1;
+      if (k == 0) {
+        lbm::launch_fused_batch(PF, maps, par, 0, flow, c0->cap);
+      } else {
+        lbm::launch_fused_batch(PF, maps, par, 2, flow, c0->cap);
+        cudaStreamWaitEvent(c0->cap, c0->ev_join, 0);
+      }
+      if (k + 1 < LBM_BATCH_STEPS) {
+        cudaEventRecord(c0->ev_fork, c0->cap);
+        cudaStreamWaitEvent(c0->cap2, c0->ev_fork, 0);
+        lbm::launch_fused_batch(PF, maps, 1 - par, 1, flow, c0->cap2);
+        cudaEventRecord(c0->ev_join, c0->cap2);
+        ++nl;
+      }
+      lbm::launch_enthalpy_solve_batch(PS, par, c0->cap);
+      lbm::launch_enthalpy_commit_batch(PC, par, c0->cap);
+      nl += 3;
+    }
+    cudaEventRecord(b->ev_out[gi], c0->cap);
+  }
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) cudaStreamWaitEvent(b->cap, b->ev_out[gi], 0);
+  if (cudaStreamEndCapture(b->cap, &gr) != cudaSuccess || !gr) {
+    cudaGetLastError();
+    return LBM_ERR_CUDA;
+  }
+  b->graph = instantiate(gr);
+  // the launches are shared: each group's first context is charged its group's
+  b->nl.assign(b->ctx.size(), 0);
+  for (const auto& G : b->groups) b->nl[G.members[0]] = nl / (int)b->groups.size();
+  return b->graph ? LBM_OK : LBM_ERR_CUDA;
+}
+
 // one graph: LBM_BATCH_STEPS steps of every context, one branch per context
 static int batch_capture(lbm_batch* b) {
+  if (b->fused) return batch_capture_fused(b);
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
@@ -821,6 +976,11 @@ static int batch_capture(lbm_batch* b) {
   }
   b->graph = instantiate(g);
   return b->graph ? LBM_OK : LBM_ERR_CUDA;
+}
+
+int lbm_batch_mode(const lbm_batch* b) {
+  if (!b) return LBM_ERR_INVALID_ARG;
+  return b->fused ? 1 : 0;
 }
 
 int lbm_batch_step(lbm_batch* b, int64_t nsteps) {

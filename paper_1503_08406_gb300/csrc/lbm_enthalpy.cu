@@ -87,8 +87,10 @@ __device__ __forceinline__ bool sub_sync_or(int threads, bool v) {
   return r != 0;
 }
 
+// CTA bid of nblk (the whole grid of a single lattice's launch, a range of a
+// batched one) takes listed tiles bid, bid + nblk, ...
 template <int PAR, typename S, int EB>
-__global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
+__device__ __forceinline__ void enthalpy_solve_body(const Dev& d, int bid, int nblk) {
   const long long tr0 = trace_start(d);
   constexpr int LAYOUT = 1 - PAR;
   extern __shared__ float smem[];
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
   const int cnt = d.lcount[PAR];
   const int stamp = stamp_of(d, PAR);
   const float w0 = d.wt0, w1 = d.wt1, Ts = d.T_s, dTt = d.dTt;
-  for (int li = blockIdx.x; li < cnt; li += gridDim.x) {
+  for (int li = bid; li < cnt; li += nblk) {
     const int tile = d.list[PAR * d.ntiles + li];
     const int X0 = (tile % d.etx) * TE, Y0 = (tile / d.etx) * TE;
     // a region (tile and halo) inside the wall ring needs no wrapping and holds
@@ -369,6 +371,17 @@ __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
   if (threadIdx.x == 0 && d.trace) trace_end(d, 100 * PAR + 20, d.ctr[PAR], tr0);
 }
 
+template <int PAR, typename S, int EB>
+__global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
+  enthalpy_solve_body<PAR, S, EB>(d, (int)blockIdx.x, (int)gridDim.x);
+}
+
+template <int PAR, typename S, int EB>
+__global__ void __launch_bounds__(EB) enthalpy_solve_batch_kernel(const __grid_constant__ BatchPlan P) {
+  const int c = plan_lattice(P, (int)blockIdx.x);
+  enthalpy_solve_body<PAR, S, EB>(P.d[c], (int)blockIdx.x - P.start[c], P.start[c + 1] - P.start[c]);
+}
+
 // x changed flow activity and is the inward node of a flow wall w next to it:
 // w's links to its other lattice neighbours x' change state with x.  Those x'
 // that kept their activity leave the link to x (a changed x' takes it itself).
@@ -401,7 +414,7 @@ __device__ __noinline__ void wall_links(const Dev& d, int x, int y, bool ao, boo
 }
 
 template <int PAR, bool WALLS>
-__global__ void __launch_bounds__(CB, 2) enthalpy_commit_kernel(Dev d) {
+__device__ __forceinline__ void enthalpy_commit_body(const Dev& d, int bid, int nblk) {
   const long long tr0 = trace_start(d);
   constexpr int LAYOUT = 1 - PAR;
   constexpr int RW = TE + 2;              // tile plus a one-node ring
@@ -412,7 +425,7 @@ __global__ void __launch_bounds__(CB, 2) enthalpy_commit_kernel(Dev d) {
   const int cnt = d.lcount[PAR];
   const int stamp = stamp_of(d, PAR);
   const int n = (int)d.n;
-  for (int li = blockIdx.x; li < cnt; li += gridDim.x) {
+  for (int li = bid; li < cnt; li += nblk) {
     const int tile = d.list[PAR * d.ntiles + li];
     const int tx0 = tile % d.etx, ty0 = tile / d.etx;
     const int X0 = tx0 * TE, Y0 = ty0 * TE;
@@ -548,6 +561,17 @@ __global__ void __launch_bounds__(CB, 2) enthalpy_commit_kernel(Dev d) {
   if (threadIdx.x == 0 && d.trace) trace_end(d, 100 * PAR + 30, d.ctr[PAR], tr0);
 }
 
+template <int PAR, bool WALLS>
+__global__ void __launch_bounds__(CB, 2) enthalpy_commit_kernel(Dev d) {
+  enthalpy_commit_body<PAR, WALLS>(d, (int)blockIdx.x, (int)gridDim.x);
+}
+
+template <int PAR>
+__global__ void __launch_bounds__(CB, 2) enthalpy_commit_batch_kernel(const __grid_constant__ BatchPlan P) {
+  const int c = plan_lattice(P, (int)blockIdx.x);
+  enthalpy_commit_body<PAR, false>(P.d[c], (int)blockIdx.x - P.start[c], P.start[c + 1] - P.start[c]);
+}
+
 size_t enthalpy_solve_smem() { return 6 * RE * RE * sizeof(float); }
 
 template <typename S>
@@ -589,6 +613,33 @@ void launch_enthalpy_solve(const Dev& d, int parity, cudaStream_t s) {
   if (d.storage == 1) launch_solve_t<__half>(d, parity, s);
   else if (d.storage == 2) launch_solve_t<__nv_bfloat16>(d, parity, s);
   else launch_solve_t<float>(d, parity, s);
+}
+
+void fused_batch_setup();   // lbm_fused_f32.cu
+
+void batch_setup() {
+  fused_batch_setup();
+  const int bytes = (int)enthalpy_solve_smem();
+  cudaFuncSetAttribute(enthalpy_solve_batch_kernel<0, float, EB_WIDE>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(enthalpy_solve_batch_kernel<1, float, EB_WIDE>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+// the lattices of a batch are small: the wide CTAs, which finish a tile sooner
+void launch_enthalpy_solve_batch(const BatchPlan& P, int parity, cudaStream_t s) {
+  const size_t sm = enthalpy_solve_smem();
+  const int grid = P.start[P.count];
+  if (grid <= 0) return;
+  if (parity == 0) enthalpy_solve_batch_kernel<0, float, EB_WIDE><<<grid, EB_WIDE, sm, s>>>(P);
+  else enthalpy_solve_batch_kernel<1, float, EB_WIDE><<<grid, EB_WIDE, sm, s>>>(P);
+}
+
+void launch_enthalpy_commit_batch(const BatchPlan& P, int parity, cudaStream_t s) {
+  const int grid = P.start[P.count];
+  if (grid <= 0) return;
+  if (parity == 0) enthalpy_commit_batch_kernel<0><<<grid, CB, 0, s>>>(P);
+  else enthalpy_commit_batch_kernel<1><<<grid, CB, 0, s>>>(P);
 }
 
 void launch_enthalpy_commit(const Dev& d, int parity, cudaStream_t s) {

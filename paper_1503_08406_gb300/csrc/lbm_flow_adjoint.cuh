@@ -34,23 +34,12 @@
 namespace lbm {
 
 // The reverse sweeps take the clamp of Eq. (42) as open at a node (the node
-// mushy, its f_l a function of the step's temperature) only where f_l after
-// the step lies at least ADJ_BAND_EPS inside (0, 1).  A solid held at T_s
-// sits on the clamp's kink: exact arithmetic keeps its f_l at 0, while FP32
-// rounding in the enthalpy solve leaves values of order 1e-8 there.  Taken as
-// mushy, such nodes make the linearised step grow without bound: a mushy
-// node passes a temperature change on to its four neighbours as latent heat
-// amplified by 4 w~_1 a / (T_l - T_s + w~_0 a), which exceeds 1 when the
-// mushy range T_l - T_s is narrow against a (the forward step never sees
-// the growth, since f_l cannot fall below 0).  Nodes within ADJ_BAND_EPS of
-// a clamp value count as clamped; the exact gradient moves by far less than
-// the FP32 path's own rounding (the FP64 reference's, by 1e-7 relative on a
-// 128^2 melting cavity over 200 steps).
-constexpr double ADJ_BAND_EPS = 1e-7;
-
+// mushy, its f_l a function of the step's temperature) where f_l after the
+// step lies strictly inside (0, 1); at the bounds the one-sided derivative of
+// the clamped side, 0, is taken.
 template <typename R>
 LBM_HD bool adj_mushy(R f) {
-  return f > R(ADJ_BAND_EPS) && f < R(1) - R(ADJ_BAND_EPS);
+  return f > R(0) && f < R(1);
 }
 
 template <typename R>

@@ -785,9 +785,11 @@ __device__ __forceinline__ bool tma_node(const Dev& d, const unsigned char* sb, 
   return unsafe;
 }
 
+// One CTA's share of the pass over one lattice: CTA bid of nblk (blockIdx.x
+// and gridDim.x of a single lattice's launch; its range in a batched launch).
 template <typename S, int PAR, bool FLOW, int MODE>
-__global__ void __launch_bounds__(TX* TY, TMA_MIN_CTAS)
-    fused_tma_kernel(Dev d, const __grid_constant__ TmaMaps m) {
+__device__ __forceinline__ void fused_tma_body(const Dev& d, const TmaMaps& m, int bid,
+                                               int nblk) {
   using L = TmaLayout<PAR, S>;
   constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -801,10 +803,10 @@ __global__ void __launch_bounds__(TX* TY, TMA_MIN_CTAS)
   // it).  The CTAs resident at any moment so work on one band of tiles, which keeps
   // the DRAM traffic of a moment within a few rows of each plane (measured 4% faster
   // than runs of consecutive tiles per CTA).
-  const int t0 = (int)blockIdx.x, dt = (int)gridDim.x;
+  const int t0 = bid, dt = nblk;
   const int cnt = (ntile - t0 + dt - 1) / dt;
   const long long tr0 = trace_start(d);
-  if (MODE != 1 && blockIdx.x == 0 && tid == 0) step_prologue<PAR>(d);
+  if (MODE != 1 && bid == 0 && tid == 0) step_prologue<PAR>(d);
   constexpr int NB = L::NBUF;
   const unsigned buf0 = smem_u32(smem);
   const unsigned bar0 = buf0 + L::BAR_OFF;   // mbarrier of buffer j: bar0 + 8 j
@@ -896,6 +898,23 @@ __global__ void __launch_bounds__(TX* TY, TMA_MIN_CTAS)
   }
   // (ctr[1 - PAR] + 1: the step this launch computes; no launch of the step changes it)
   if (tid == 0 && d.trace) trace_end(d, 100 * PAR + 10 + MODE, d.ctr[1 - PAR] + 1, tr0);
+}
+
+template <typename S, int PAR, bool FLOW, int MODE>
+__global__ void __launch_bounds__(TX* TY, TMA_MIN_CTAS)
+    fused_tma_kernel(Dev d, const __grid_constant__ TmaMaps m) {
+  fused_tma_body<S, PAR, FLOW, MODE>(d, m, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// The same pass over every lattice of a batch in one launch: each lattice's
+// CTAs are a range of the grid, its parameters one entry of the plan, its
+// tensor maps one entry of a device array.
+template <typename S, int PAR, bool FLOW, int MODE>
+__global__ void __launch_bounds__(TX* TY, TMA_MIN_CTAS)
+    fused_tma_batch_kernel(const __grid_constant__ BatchPlan P, const TmaMaps* __restrict__ maps) {
+  const int c = plan_lattice(P, (int)blockIdx.x);
+  fused_tma_body<S, PAR, FLOW, MODE>(P.d[c], maps[c], (int)blockIdx.x - P.start[c],
+                                     P.start[c + 1] - P.start[c]);
 }
 
 // ---- launches ------------------------------------------------------------------

@@ -13,6 +13,42 @@ void launch_fused_f32(const Dev& d, const TmaMaps* m, int parity, int mode, cuda
 
 bool tma_setup_f32(Dev& d, TmaMaps* m) { return tma_setup_t<float>(d, m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32); }
 
+void fused_batch_setup() {
+  const int s0 = TmaLayout<0, float>::SMEM, s1 = TmaLayout<1, float>::SMEM;
+#define LBM_SMEM(P, FL, MO, SM)                                                      \
+  cudaFuncSetAttribute(fused_tma_batch_kernel<float, P, FL, MO>,                     \
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, SM)
+  LBM_SMEM(0, true, 0, s0); LBM_SMEM(0, true, 1, s0); LBM_SMEM(0, true, 2, s0);
+  LBM_SMEM(0, false, 0, s0); LBM_SMEM(0, false, 1, s0); LBM_SMEM(0, false, 2, s0);
+  LBM_SMEM(1, true, 0, s1); LBM_SMEM(1, true, 1, s1); LBM_SMEM(1, true, 2, s1);
+  LBM_SMEM(1, false, 0, s1); LBM_SMEM(1, false, 1, s1); LBM_SMEM(1, false, 2, s1);
+#undef LBM_SMEM
+}
+
+template <int PAR, bool FL, int MO>
+static void fused_batch_one(const BatchPlan& P, const TmaMaps* maps, cudaStream_t s) {
+  fused_tma_batch_kernel<float, PAR, FL, MO>
+      <<<P.start[P.count], dim3(TX, TY), TmaLayout<PAR, float>::SMEM, s>>>(P, maps);
+}
+
+template <int PAR, bool FL>
+static void fused_batch_mode(const BatchPlan& P, const TmaMaps* maps, int mode, cudaStream_t s) {
+  if (mode == 0) fused_batch_one<PAR, FL, 0>(P, maps, s);
+  else if (mode == 1) fused_batch_one<PAR, FL, 1>(P, maps, s);
+  else fused_batch_one<PAR, FL, 2>(P, maps, s);
+}
+
+void launch_fused_batch(const BatchPlan& P, const TmaMaps* maps, int parity, int mode, bool flow,
+                        cudaStream_t s) {
+  if (parity == 0) {
+    if (flow) fused_batch_mode<0, true>(P, maps, mode, s);
+    else fused_batch_mode<0, false>(P, maps, mode, s);
+  } else {
+    if (flow) fused_batch_mode<1, true>(P, maps, mode, s);
+    else fused_batch_mode<1, false>(P, maps, mode, s);
+  }
+}
+
 // Self-check of the bounded wait: one CTA initialises an mbarrier that no copy
 // and no thread ever completes, waits on it with mbar_wait's limit, and on
 // giving up sets the same timeout flag the stream-collide kernel sets.  Nothing

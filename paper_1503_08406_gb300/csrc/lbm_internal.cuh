@@ -139,6 +139,28 @@ struct TmaMaps {
   CUtensorMap f_even, f_odd, g_even, g_odd, fl, phi, K;
 };
 
+// A batched launch runs one kernel over several lattices: lattice i takes the
+// CTAs [start[i], start[i + 1]) of the grid, with its own parameters d[i].
+// Passed as a __grid_constant__ kernel parameter (25 KB, within the 32 KB
+// parameter limit), so a CTA reads its lattice's fields from the constant
+// bank as a single lattice's launch does.
+constexpr int BATCH_MAX = 64;
+struct BatchPlan {
+  int count;
+  int start[BATCH_MAX + 1];
+  Dev d[BATCH_MAX];
+};
+// the lattice whose range holds CTA b (binary search over the starts)
+__device__ __forceinline__ int plan_lattice(const BatchPlan& P, int b) {
+  int lo = 0, hi = P.count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (P.start[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // conversions between a stored population and FP32 (round to nearest on store)
 template <typename S>
 struct Pop;
@@ -355,6 +377,16 @@ bool tma_setup(Dev& d, TmaMaps* m);
 int tma_grid(const Dev& d, int tpc);
 void launch_enthalpy_solve(const Dev& d, int parity, cudaStream_t s);
 void launch_enthalpy_commit(const Dev& d, int parity, cudaStream_t s);
+// Batched launches (FP32 storage, TMA-staged stream-collide, no flow walls):
+// one launch runs the pass for every lattice of the plan, lattice i on the
+// CTAs [P.start[i], P.start[i + 1]); maps: device array of the lattices'
+// tensor maps.  batch_setup sets the kernels' shared-memory limits (call it
+// before capturing them).
+void batch_setup();
+void launch_fused_batch(const BatchPlan& P, const TmaMaps* maps, int parity, int mode, bool flow,
+                        cudaStream_t s);
+void launch_enthalpy_solve_batch(const BatchPlan& P, int parity, cudaStream_t s);
+void launch_enthalpy_commit_batch(const BatchPlan& P, int parity, cudaStream_t s);
 void enthalpy_setup();
 size_t enthalpy_solve_smem();
 void launch_init(const Dev& d, const float* T0, cudaStream_t s);

@@ -150,6 +150,8 @@ def load():
         lib.lbm_batch_create.argtypes = [ctypes.POINTER(_VP), ctypes.c_int, _VP,
                                          ctypes.POINTER(_VP)]
         lib.lbm_batch_step.argtypes = [_VP, ctypes.c_int64]
+        lib.lbm_batch_mode.argtypes = [_VP]
+        lib.lbm_batch_mode.restype = ctypes.c_int
         lib.lbm_batch_destroy.argtypes = [_VP]
         lib.lbm_batch_destroy.restype = None
         lib.lbm_get_macros.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int]
@@ -480,6 +482,12 @@ class Batch:
 
     def step(self, nsteps: int):
         _check(self.lib.lbm_batch_step(self._h, int(nsteps)), "lbm_batch_step")
+
+    def mode(self) -> int:
+        """1: one launch per pass over every lattice; 0: one graph branch per lattice."""
+        rc = int(self.lib.lbm_batch_mode(self._h))
+        _check(rc if rc < 0 else 0, "lbm_batch_mode")
+        return rc
 
     def close(self):
         if getattr(self, "_h", None):

@@ -57,8 +57,7 @@ extern "C" int coupled_reverse_step_f64(int nx, int ny, int per_x, int per_y, co
   const int ex[5] = {0, 1, 0, -1, 0};
   const int ey[5] = {0, 0, 1, 0, -1};
 
-  // the fixed point's adjoint on the band (f_l(n+1) inside (0, 1) by
-  // ADJ_BAND_EPS, not a wall), as the band kernel takes it
+  // the fixed point's adjoint on the band (0 < f_l(n+1) < 1, not a wall)
   std::vector<double> a(n), rhs(n, 0.0), mu(n, 0.0), mo(n, 0.0);
   std::vector<char> band(n);
   for (int y = 0; y < ny; ++y)
