@@ -130,8 +130,8 @@ int check_params(const lbm_params* p) {
 }
 
 struct Layout {
-  size_t f, g, fl, phi, K, wallTl, flags, list, lcount, ctr, nearmap, proc, scr, stats, tmp,
-      partials, sums, bad, total;
+  size_t f, g, fl, phi, K, wallTl, flags, list, lcount, ctr, nearmap, proc, tact, scr, stats,
+      tmp, partials, sums, bad, total;
 };
 
 size_t up(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -154,6 +154,7 @@ Layout layout_of(const lbm_params* p, int nred) {
   L.ctr = o; o += up(2 * sizeof(int));
   L.nearmap = o; o += up(2 * tiles * sizeof(int));
   L.proc = o; o += up(tiles * sizeof(int));
+  L.tact = o; o += up(tiles);
   L.scr = o; o += up(n * sizeof(float2));
   L.stats = o; o += up(8 * sizeof(int));
   L.tmp = o; o += up(9 * n * sizeof(float));
@@ -333,6 +334,8 @@ int lbm_create(const lbm_params* pin, void* stream, void* workspace, size_t work
   d.ctr = (int*)(b + L.ctr);
   d.nearmap = (int*)(b + L.nearmap);
   d.proc = (int*)(b + L.proc);
+  d.tact = (unsigned char*)(b + L.tact);
+  d.tskip = 0;
   d.scr = (float2*)(b + L.scr);
   d.stats = (int*)(b + L.stats);
   c->tmp = (float*)(b + L.tmp);
@@ -383,8 +386,9 @@ static int reset_lists(lbm_ctx* c) {
   LBM_CUDA(cudaMemsetAsync(d.flags, 0, 2 * sizeof(int) * d.ntiles, c->stream));
   LBM_CUDA(cudaMemsetAsync(d.lcount, 0, 2 * sizeof(int), c->stream));
   LBM_CUDA(cudaMemsetAsync(d.stats + 5, 0, sizeof(int), c->stream));
+  lbm::launch_tile_activity(d, c->stream);   // f_l was just loaded
   c->since_check = 0;
-  return LBM_OK;
+  return cuda_err(cudaGetLastError());
 }
 
 static int copy_in(lbm_ctx* c, float* dst, const float* src, size_t count, int device_ptrs) {
@@ -881,6 +885,7 @@ static int batch_plans(lbm_batch* b) {
         const int i = G.members[j];
         const lbm::Dev& d = b->ctx[i]->d;
         P.d[j] = d;
+        P.d[j].tskip = 1;   // batch members are mostly solid early on
         const int grid = k == 0 ? (int)((nt[i] + tpc - 1) / tpc) : k == 1 ? d.egrid : d.cgrid;
         P.start[j + 1] = P.start[j] + grid;
       }
@@ -1764,6 +1769,7 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
       unsigned* const cc = ctr + 2 * buf;
       lbm::launch_set_state(c->d, SS, SS + 9 * n, sm);
       cudaMemcpyAsync(c->d.fl, SS + 14 * n, n * sizeof(float), cudaMemcpyDeviceToDevice, sm);
+      lbm::launch_tile_activity(c->d, sm);
       cudaMemsetAsync(c->d.flags, 0, 2 * sizeof(int) * c->d.ntiles, sm);
       cudaMemsetAsync(c->d.lcount, 0, 2 * sizeof(int), sm);
       if (sm == c->cap) {

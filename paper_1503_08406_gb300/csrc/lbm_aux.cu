@@ -319,6 +319,24 @@ static unsigned grid1(long long n, int b) { return (unsigned)((n + b - 1) / b); 
 void launch_init(const Dev& d, const float* T0, cudaStream_t s) {
   init_kernel<<<grid1(d.n, 256), 256, 0, s>>>(d, T0);
 }
+// one CTA per enthalpy tile: does a non-wall node of it carry flow?
+__global__ void __launch_bounds__(256) tile_activity_kernel(Dev d) {
+  const int tile = blockIdx.x;
+  const int X0 = (tile % d.etx) * TE, Y0 = (tile / d.etx) * TE;
+  int any = 0;
+  for (int k = threadIdx.x; k < TE * TE; k += blockDim.x) {
+    const int x = X0 + k % TE, y = Y0 + k / TE;
+    if (x < d.nx && y < d.ny && !is_wall(d, x, y) && d.fl[(long long)y * d.nx + x] >= d.f_act)
+      any = 1;
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) d.tact[tile] = (unsigned char)(any ? 1 : 0);
+}
+
+void launch_tile_activity(const Dev& d, cudaStream_t s) {
+  if (d.ntiles > 0) tile_activity_kernel<<<d.ntiles, 256, 0, s>>>(d);
+}
+
 void launch_macros(const Dev& d, int layout, float* ux, float* uy, float* rho, float* T,
                    float* fl, cudaStream_t s) {
   macros_kernel<<<grid1(d.n, 256), 256, 0, s>>>(d, layout, ux, uy, rho, T, fl);

@@ -486,6 +486,7 @@ __device__ __forceinline__ void enthalpy_commit_body(const Dev& d, int bid, int 
         }
         __syncthreads();
       }
+      int flows = 0;   // a node of the tile carries flow after the step
 #pragma unroll 4
       for (int k = tid; k < TE * TE; k += CB) {
         const int ly = k / TE, lx = k - ly * TE;
@@ -494,6 +495,7 @@ __device__ __forceinline__ void enthalpy_commit_body(const Dev& d, int bid, int 
         const int s = y * d.nx + x;
         const float2 p = d.scr[s];
         const float fn = p.x, fnew = p.y;
+        flows |= fnew >= d.f_act;
         if (fnew != fn) {
           d.fl[s] = fnew;
           const float S0 = -d.phi[s] * d.lat * sigma_ratio(d, fn) * (fnew - fn);
@@ -554,6 +556,12 @@ __device__ __forceinline__ void enthalpy_commit_body(const Dev& d, int bid, int 
           const bool ao = p.x >= d.f_act, an = p.y >= d.f_act;
           if (ao != an) wall_links<PAR>(d, x, y, ao, an, stamp);
         }
+      }
+      // (the stream-collide pass copies a tile's flow populations only when
+      // this is set; no fused pass reads it while the commit runs on its tile)
+      if (pb & 2) {
+        flows = __syncthreads_or(flows);
+        if (tid == 0) d.tact[tile] = (unsigned char)(flows ? 1 : 0);
       }
     }
     __syncthreads();

@@ -701,21 +701,23 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity,
   }
 }
 
-// issue the copies of the tile at (x0, y0) into buffer `buf`, completing on `bar`
+// issue the copies of the tile at (x0, y0) into buffer `buf`, completing on `bar`;
+// flows: some node of the tile carries flow (else its nodes read neither their
+// flow populations nor phi and K, and those are not copied)
 template <typename S, int PAR, bool FLOW>
 __device__ __forceinline__ void tma_issue(const TmaMaps& m, unsigned buf, unsigned bar, int x0,
-                                          int y0) {
+                                          int y0, bool flows) {
   using L = TmaLayout<PAR, S>;
-  constexpr int bytes =
-      (FLOW ? L::F_BYTES : 0) + L::G_BYTES + L::FL_BYTES + (FLOW ? 2 * L::M_BYTES : 0);
+  const bool fc = FLOW && flows;
+  const int bytes = (fc ? L::F_BYTES + 2 * L::M_BYTES : 0) + L::G_BYTES + L::FL_BYTES;
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
   // x0 is a multiple of 32 and HX of 4: every box starts on a 16-byte boundary
   const int px = PAR ? x0 - L::HS : x0, py = PAR ? y0 - HY : y0;
-  if (FLOW) tma_load_3d(buf + L::F_OFF, PAR ? &m.f_odd : &m.f_even, px, py, 0, bar);
+  if (fc) tma_load_3d(buf + L::F_OFF, PAR ? &m.f_odd : &m.f_even, px, py, 0, bar);
   tma_load_3d(buf + L::G_OFF, PAR ? &m.g_odd : &m.g_even, px, py, 0, bar);
   tma_load_2d(buf + L::FL_OFF, &m.fl, x0 - HX, y0 - HY, bar);
-  if (FLOW) {
+  if (fc) {
     tma_load_2d(buf + L::PHI_OFF, &m.phi, x0, y0, bar);
     tma_load_2d(buf + L::K_OFF, &m.K, x0, y0, bar);
   }
@@ -814,17 +816,22 @@ __device__ __forceinline__ void fused_tma_body(const Dev& d, const TmaMaps& m, i
     if (tid == 0) atomicExch(&d.stats[4], 2);
     return;
   }
+  // bit k: this CTA's tile k needs its flow populations (with d.tskip: it has a
+  // node that carries flow, read once, one lane per tile, by the thread that
+  // issues every copy)
+  unsigned fmask = 0u;
   auto issue = [&](int k, int j) {   // tile k of this CTA into buffer j
     const int t = t0 + k * dt;
     tma_issue<S, PAR, FLOW>(m, buf0 + j * L::BYTES, bar0 + 8 * j, (t % tiles_x) * TX,
-                         (t / tiles_x) * TY);
+                            (t / tiles_x) * TY, (fmask >> k) & 1u);
   };
   if (ty == 0) {
     // which of this CTA's tiles this launch takes, one lane per tile
     const int t = t0 + lane * dt;
+    const int et = ((t / tiles_x) * TY / TE) * d.etx + (t % tiles_x) * TX / TE;
     bool take = lane < cnt;
-    if (take && MODE != 0) take = takes_tile<PAR, MODE>(d, ((t / tiles_x) * TY / TE) * d.etx +
-                                                              (t % tiles_x) * TX / TE);
+    if (take && MODE != 0) take = takes_tile<PAR, MODE>(d, et);
+    fmask = !FLOW ? 0u : d.tskip ? __ballot_sync(FULL, take && d.tact[et]) : ~0u;
     const unsigned mask = __ballot_sync(FULL, take);
     if (lane == 0) {
       *s_mask = mask;

@@ -100,6 +100,12 @@ struct Dev {
   int* proc;                 // per enthalpy tile: (stamp << 3) | bits, bit 0 solved, bit 1
                              // some f_l changed, bit 2 some node's flow activity changed
   float2* scr;               // per node of solved tiles: (f_l(n), f_l(n+1))
+  int tskip;                 // 1: the TMA-staged pass copies flow populations, phi and K
+                             // only for tiles with tact set (batch members: mostly solid
+                             // lattices); 0: for every tile
+  unsigned char* tact;       // per enthalpy tile: 1 if a non-wall node of it carries flow
+                             // (f_l >= f_act); kept by the commit kernel and by
+                             // launch_tile_activity wherever f_l is loaded
   // kernel trace (lbm_trace): per CTA, at its end, (kind, step stamp, start
   // and end in ns of %globaltimer) appended at trace[4 k], k = trace_n[0]++,
   // while k < trace_cap; null: off
@@ -400,6 +406,8 @@ void launch_set_state(const Dev& d, const float* f, const float* g, cudaStream_t
 // the whole state (f, g, f_l: 15 n floats, natural layout) into base, or into
 // base + ctr[0] 15 n and then ctr[0]++ when ctr is non-null (ctr[1] must be 0)
 void launch_keep_state(const Dev& d, int layout, float* base, unsigned* ctr, cudaStream_t s);
+// d.tact from d.fl, every tile (after f_l is loaded from outside the step)
+void launch_tile_activity(const Dev& d, cudaStream_t s);
 // NaN/Inf sentinel over the whole state (sets stats[5])
 void launch_nonfinite(const Dev& d, int nblocks, cudaStream_t s);
 // one CTA waiting, with a limit of limit_ns, on an mbarrier nothing completes
