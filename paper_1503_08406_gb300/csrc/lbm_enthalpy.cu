@@ -376,8 +376,9 @@ __global__ void __launch_bounds__(EB) enthalpy_solve_kernel(Dev d) {
   enthalpy_solve_body<PAR, S, EB>(d, (int)blockIdx.x, (int)gridDim.x);
 }
 
+// (three CTAs a SM: a batch lists many small tiles at once)
 template <int PAR, typename S, int EB>
-__global__ void __launch_bounds__(EB) enthalpy_solve_batch_kernel(const __grid_constant__ BatchPlan P) {
+__global__ void __launch_bounds__(EB, 3) enthalpy_solve_batch_kernel(const __grid_constant__ BatchPlan P) {
   const int c = plan_lattice(P, (int)blockIdx.x);
   enthalpy_solve_body<PAR, S, EB>(P.d[c], (int)blockIdx.x - P.start[c], P.start[c + 1] - P.start[c]);
 }
