@@ -19,10 +19,12 @@ LIB = os.path.join(OUT, "liblbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
          "--expt-relaxed-constexpr"]
-# The fused stream-collide is issue-bound: its divisions and square roots use
-# the hardware-approximate forms (about 2 ulp; denormals are still kept).
+# The fused stream-collide is issue-bound, and the reverse sweep of the coupled
+# adjoint compute-bound: their divisions and square roots use the
+# hardware-approximate forms (about 2 ulp; denormals are still kept).
 APPROX = ["-prec-div=false", "-prec-sqrt=false"]
-PER_FILE = {"lbm_fused_f32.cu": APPROX, "lbm_fused_f16.cu": APPROX, "lbm_fused_bf16.cu": APPROX}
+PER_FILE = {"lbm_fused_f32.cu": APPROX, "lbm_fused_f16.cu": APPROX, "lbm_fused_bf16.cu": APPROX,
+            "lbm_adjoint.cu": APPROX}
 
 
 def _nvcc() -> str:

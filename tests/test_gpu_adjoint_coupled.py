@@ -218,8 +218,8 @@ def _oracle_objective(oracle_mod, w, steps, objective, phi=None, K=None, tw=None
 @pytest.mark.parametrize("objective", ["melt", "nusselt"])
 def test_coupled_adjoint_matches_oracle_finite_differences(lbm, oracle_mod, objective):
     """Central differences of the FP64 oracle's objective, h = 1e-4 (in phi,
-    ln K and the wall profile), at 16 seeded cells whose f_l after the run
-    lies in (0.05, 0.95) (the front, away from the clamps) and whose gradient
+    ln K and the wall profile), at 16 seeded cells away from the clamps (f_l
+    after the run in (0.05, 0.95), or liquid at least 0.05 above T_l) whose gradient
     is at least 5% of the field's largest (an FP32 gradient carries an
     absolute error of ~1e-5 of the largest entry, so smaller entries cannot be
     held to 1e-3 of themselves), and at 4 wall rows, after 400 steps.  Each
@@ -233,7 +233,12 @@ def test_coupled_adjoint_matches_oracle_finite_differences(lbm, oracle_mod, obje
     o = oracle_mod.Oracle(w.nx, w.ny, **w.params)
     o.set_fields(w.phi, w.K, w.T0, w.fl0, w.wall_T_left)
     o.step(steps)
-    fl_end = o.macros()["fl"]
+    mac = o.macros()
+    fl_end = mac["fl"]
+    # away from the clamp kinks: the front (0.05 < f_l < 0.95) and the liquid
+    # well above T_l (where the Nusselt number's gradient sits)
+    smooth = ((fl_end > 0.05) & (fl_end < 0.95)) | \
+        ((fl_end == 1.0) & (mac["T"] >= w.params["T_l"] + 0.05))
     rng = np.random.default_rng(12)
     h = 1e-4
 
@@ -257,7 +262,7 @@ def test_coupled_adjoint_matches_oracle_finite_differences(lbm, oracle_mod, obje
     worst, checked = {}, {}
     for name, grad in (("phi", dphi), ("lnK", dlnK)):
         big = np.abs(grad) >= 0.05 * np.abs(grad).max()
-        cand = np.argwhere((fl_end > 0.05) & (fl_end < 0.95) & big)
+        cand = np.argwhere(smooth & big)
         assert len(cand) >= 8, (name, len(cand))
         cells = cand[rng.choice(len(cand), size=min(16, len(cand)), replace=False)]
         for (y, x) in cells:
