@@ -111,6 +111,15 @@ typedef struct {
                                      into it stream; 0: links into wall nodes reflect halfway.
                                      Ignored without the flow lattice; the coupled adjoint
                                      refuses it */
+  int32_t flow_front;             /* 1: no-slip on the moving solid-liquid interface by the
+                                     same extrapolation (Sec. 4): a link from a flow node x
+                                     into a lattice node without flow returns, in place of x's
+                                     reflected population, the one that node would stream
+                                     back as a boundary node extrapolated from x
+                                     (f^eq(rho_x, 0) + f(x) - f^eq(rho_x, u_x) collided with
+                                     x's T, f_l, phi and K); 0: halfway bounce-back.  Links
+                                     into wall nodes follow flow_walls.  Ignored without the
+                                     flow lattice; the coupled adjoint refuses it */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;

@@ -65,7 +65,7 @@ class _Params(ctypes.Structure):
         ("f_act", ctypes.c_double),
         ("max_inner_iters", ctypes.c_int32), ("inner_tol", ctypes.c_double),
         ("alpha_ratio", ctypes.c_double), ("sigma_solid", ctypes.c_double),
-        ("flow_walls", ctypes.c_int32),
+        ("flow_walls", ctypes.c_int32), ("flow_front", ctypes.c_int32),
     ]
 
 
@@ -125,7 +125,7 @@ DEFAULTS = dict(
     T_ref=0.0, T_s=0.0, T_l=0.0, varpi=-2.0, rho0=1.0, tau_nu=-1.0, tau_T=-1.0, g_beta=-1.0,
     s_e=0.0, s_eps=0.0, s_q=0.0, zeta_e=0.0, zeta_nu=0.0, f_act=1e-3,
     max_inner_iters=1000, inner_tol=1e-13, alpha_ratio=0.0, sigma_solid=0.0,
-    flow_walls=0,
+    flow_walls=0, flow_front=0,
 )
 
 

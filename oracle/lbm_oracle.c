@@ -39,6 +39,13 @@
  *    the inward node x_f; it then collides with x_f's T, f_l, phi and K and
  *    streams like a flow node; links into it are no longer reflected.  (The
  *    default, flow_walls = 0, reflects them halfway.)
+ *  - flow front (flow_front = 1): the same extrapolation for the no-slip condition on
+ *    the moving solid-liquid interface (Sec. 4).  A link from a flow node x into a
+ *    non-flow lattice node x_s (not a wall) returns, instead of x's own reflected
+ *    population, the one x_s would stream back as a boundary node extrapolated from x:
+ *    f^eq(rho_x, 0) + f(x) - f^eq(rho_x, u_x) collided with x's T, f_l, phi and K.
+ *    Each link takes its own flow node, so no choice among a solid node's neighbours
+ *    is needed; x_s keeps its populations (flow only in the liquid).
  *  - with sigma_solid set, sigma follows Eq. (7), linear in f_l:
  *    sigma(f_l) = sigma_s + f_l (sigma_l - sigma_s), evaluated at f_l(n) per
  *    node for the step, in tau_T, in n^eq of Eq. (34) and in the latent
@@ -99,6 +106,7 @@ struct ora_ctx {
   /* fields */
   double *phi, *K, *wallTl;
   double *f, *fpost, *fnew; /* [9][n] */
+  double *fext;             /* [9][n]: post-collision extrapolated boundary state (flow_front) */
   double *g, *gpre, *gpost, *gstar, *gtmp; /* [5][n] */
   double *fl, *fk, *fk1, *ux, *uy, *T, *Tk, *a; /* a: of the step under way */
   unsigned char *wall, *active;
@@ -451,6 +459,7 @@ int ora_create(const ora_params* p, ora_ctx** out) {
   c->f = calloc(9 * n, sizeof(double));
   c->fpost = calloc(9 * n, sizeof(double));
   c->fnew = calloc(9 * n, sizeof(double));
+  c->fext = calloc(9 * n, sizeof(double));
   c->g = calloc(5 * n, sizeof(double));
   c->gpre = calloc(5 * n, sizeof(double));
   c->gpost = calloc(5 * n, sizeof(double));
@@ -466,7 +475,8 @@ int ora_create(const ora_params* p, ora_ctx** out) {
   c->a = calloc(n, sizeof(double));
   c->wall = calloc(n, 1);
   c->active = calloc(n, 1);
-  if (!c->phi || !c->K || !c->wallTl || !c->f || !c->fpost || !c->fnew || !c->g || !c->gpre ||
+  if (!c->phi || !c->K || !c->wallTl || !c->f || !c->fpost || !c->fnew || !c->fext || !c->g ||
+      !c->gpre ||
       !c->gpost || !c->gstar || !c->gtmp || !c->fl || !c->fk || !c->fk1 || !c->ux || !c->uy ||
       !c->T || !c->Tk || !c->a || !c->wall || !c->active) {
     ora_destroy(c);
@@ -483,7 +493,7 @@ int ora_create(const ora_params* p, ora_ctx** out) {
 void ora_destroy(ora_ctx* c) {
   if (!c) return;
   free(c->phi); free(c->K); free(c->wallTl);
-  free(c->f); free(c->fpost); free(c->fnew);
+  free(c->f); free(c->fpost); free(c->fnew); free(c->fext);
   free(c->g); free(c->gpre); free(c->gpost); free(c->gstar); free(c->gtmp);
   free(c->fl); free(c->fk); free(c->fk1); free(c->ux); free(c->uy); free(c->T); free(c->Tk);
   free(c->a); free(c->wall); free(c->active);
@@ -600,6 +610,17 @@ static void flow_step(ora_ctx* c) {
       for (int i = 0; i < 9; ++i) fin[i] = c->f[i * n + s];
       if (c->active[s] == 1) {
         collide_flow(c, fin, c->T[s], c->fl[s], c->phi[s], c->K[s], fout, &c->ux[s], &c->uy[s]);
+        if (c->p.flow_front == 1) {
+          /* the boundary state a non-flow neighbour extrapolates from this node */
+          double rho, ufx, ufy, Fx, Fy, eqw[9], eqf[9], fb[9], fe[9], tx, ty;
+          macro_flow(c, fin, c->T[s], c->fl[s], c->phi[s], c->K[s], &rho, &ufx, &ufy, &Fx, &Fy);
+          const double vphi = c->phi[s] * c->fl[s];
+          ora_feq(c, rho, 0, 0, vphi, eqw);
+          ora_feq(c, rho, ufx, ufy, vphi, eqf);
+          for (int i = 0; i < 9; ++i) fb[i] = eqw[i] + fin[i] - eqf[i];
+          collide_flow(c, fb, c->T[s], c->fl[s], c->phi[s], c->K[s], fe, &tx, &ty);
+          for (int i = 0; i < 9; ++i) c->fext[i * n + s] = fe[i];
+        }
       } else if (c->active[s] == 2) {
         /* Sec. 4: equilibrium at the wall velocity (0) with the fluid node's
          * density plus the fluid node's non-equilibrium part */
@@ -637,6 +658,8 @@ static void flow_step(ora_ctx* c) {
         int src = neighbour(c, x, y, -EX9[i], -EY9[i]);
         if (src >= 0 && c->active[src])
           c->fnew[i * n + s] = c->fpost[i * n + src];
+        else if (c->p.flow_front == 1 && c->active[s] == 1 && src >= 0 && !c->wall[src])
+          c->fnew[i * n + s] = c->fext[i * n + s];   /* from the front's boundary node */
         else
           c->fnew[i * n + s] = c->fpost[OPP9[i] * n + s];
       }

@@ -54,6 +54,9 @@ typedef struct {
                            f_l = 1); 0: sigma everywhere */
   int32_t flow_walls;   /* 0: halfway bounce-back on links into wall nodes;
                            1: non-equilibrium extrapolation on wall nodes (Sec. 4) */
+  int32_t flow_front;   /* 0: halfway bounce-back on links into non-flow lattice nodes;
+                           1: non-equilibrium extrapolation at the moving solid-liquid
+                           interface (Sec. 4), from the flow node of each link */
 } ora_params;
 
 typedef struct ora_ctx ora_ctx;

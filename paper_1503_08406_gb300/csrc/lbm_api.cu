@@ -126,6 +126,7 @@ int check_params(const lbm_params* p) {
   if (!(p->alpha_ratio >= 0)) return LBM_ERR_INVALID_ARG;
   if (!(p->sigma_solid >= 0)) return LBM_ERR_INVALID_ARG;
   if (p->flow_walls < 0 || p->flow_walls > 1) return LBM_ERR_INVALID_ARG;
+  if (p->flow_front < 0 || p->flow_front > 1) return LBM_ERR_INVALID_ARG;
   return LBM_OK;
 }
 
@@ -276,6 +277,7 @@ int lbm_create(const lbm_params* pin, void* stream, void* workspace, size_t work
   d.inv_aratio = d.alpha_var ? (float)(1.0 / p.alpha_ratio) : 1.f;
   d.sigma_var = (p.sigma_solid > 0 && p.sigma_solid != p.sigma) ? 1 : 0;
   d.flow_walls = (p.flow && p.flow_walls) ? 1 : 0;   // walls carry flow only with a flow lattice
+  d.flow_front = (p.flow && p.flow_front) ? 1 : 0;
   d.sigma_s = d.sigma_var ? (float)p.sigma_solid : (float)p.sigma;
   d.z_e = (float)p.zeta_e;
   d.z_nu = (float)p.zeta_nu;
@@ -829,7 +831,7 @@ int lbm_batch_create(lbm_ctx* const* ctxs, int count, void* stream, lbm_batch** 
   bool fast = count <= lbm::BATCH_MAX;
   for (lbm_ctx* c : b->ctx)
     fast = fast && c->use_tma && c->p.storage == LBM_STORAGE_FP32 &&
-           c->d.flow == b->ctx[0]->d.flow && !c->d.flow_walls;
+           c->d.flow == b->ctx[0]->d.flow && !c->d.flow_walls && !c->d.flow_front;
   b->fused = fast;
   *out = b;
   return LBM_OK;
@@ -1564,7 +1566,7 @@ int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t check
   if (objective != LBM_OBJ_MELT && objective != LBM_OBJ_NUSSELT) return LBM_ERR_INVALID_ARG;
   const lbm_params& p = c->p;
   const lbm::Dev& d = c->d;
-  if (c->timing || p.storage != LBM_STORAGE_FP32 || d.sigma_var || (d.flow && d.flow_walls))
+  if (c->timing || p.storage != LBM_STORAGE_FP32 || d.sigma_var || d.flow_walls || d.flow_front)
     return LBM_ERR_INVALID_ARG;
   if (d.per_x || p.bc[0] != LBM_BC_DIRICHLET || d.nx < 5) return LBM_ERR_INVALID_ARG;
   const bool melt = objective == LBM_OBJ_MELT;

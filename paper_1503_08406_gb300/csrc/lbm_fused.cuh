@@ -228,6 +228,27 @@ __device__ __forceinline__ void flow_collide(const Dev& d, const float f[9], flo
   fp[8] = f[8] + c_dg + a3 + a4 - a5 - a6 - a8;
 }
 
+// Non-equilibrium extrapolation of Sec. 4 from a flow node: the boundary
+// node's state f^eq(rho, 0) + f - f^eq(rho, u) (deviations: f minus the
+// velocity part of f^eq at the node's rho and u), collided with the flow
+// node's T, f_l, phi and K, into fe
+static __device__ __noinline__ void extrapolated_post(const Dev& d, const float f[9], float T, float fl,
+                                               float phi, float K, float ux, float uy,
+                                               float fe[9]) {
+  const float w9[9] = {4.f / 9.f, 1.f / 9.f, 1.f / 9.f, 1.f / 9.f, 1.f / 9.f,
+                       1.f / 36.f, 1.f / 36.f, 1.f / 36.f, 1.f / 36.f};
+  const float ivp = 1.f / (phi * fl);
+  const float uu = ux * ux + uy * uy;
+  float fb[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const float eu = ex9(i) * ux + ey9(i) * uy;
+    fb[i] = f[i] - w9[i] * d.rho0 * (3.f * eu + 4.5f * eu * eu * ivp - 1.5f * uu * ivp);
+  }
+  float ub, vb;
+  flow_collide(d, fb, T, fl, phi, K, fe, ub, vb);
+}
+
 // The update of one non-wall node from its gathered inputs: fln = f_l of the
 // 3x3 neighbourhood (-1 on walls), gin = its five thermal populations, f = its
 // nine flow populations as streamed from the neighbours, fb = (odd steps) the
@@ -236,7 +257,7 @@ __device__ __forceinline__ void flow_collide(const Dev& d, const float f[9], flo
 // carries flow (its inward node does), so that the link streams instead of
 // reflecting.  Writes the post-collision populations to their AA slots and
 // returns whether the node fails the phase-change screen.
-template <typename S, int PAR, bool FLOW, bool EDGE = true>
+template <typename S, int PAR, int FLOW, bool EDGE = true>
 __device__ __forceinline__ bool node_update(const Dev& d, int x, int y, const Geo& q,
                                             const float fln[9], const float gin[5], float f[9],
                                             const float fb[9], float phi, float K,
@@ -271,6 +292,22 @@ __device__ __forceinline__ bool node_update(const Dev& d, int x, int y, const Ge
     }
     float fp[9];
     flow_collide(d, f, T, flc, phi, K, fp, ux, uy);
+    if (FLOW == 2) {
+      // links into non-flow lattice nodes (the front; walls keep their own
+      // rule): what arrives from the solid node is its extrapolated population
+      // in place of our reflected one, in the same slot
+      unsigned fm = 0u;
+#pragma unroll
+      for (int i = 1; i < 9; ++i)
+        if (!act[i] && !(EDGE && q.wl[i])) fm |= 1u << i;
+      if (fm) {
+        float fe[9];
+        extrapolated_post(d, f, T, flc, phi, K, ux, uy, fe);
+#pragma unroll
+        for (int i = 1; i < 9; ++i)
+          if ((fm >> i) & 1u) fp[i] = fe[opp9(i)];
+      }
+    }
     if (PAR == 0) {
 #pragma unroll
       for (int i = 0; i < 9; ++i) fstore(&F[opp9(i) * n + s], fp[i], rnd);
@@ -433,8 +470,6 @@ __global__ void __launch_bounds__(256) flow_wall_kernel(Dev d) {
   S* F = static_cast<S*>(d.f);
   const S* G = static_cast<const S*>(d.g);
   const float r0 = d.wt0 * d.g_ref, r1 = d.wt1 * d.g_ref;
-  const float w9[9] = {4.f / 9.f, 1.f / 9.f, 1.f / 9.f, 1.f / 9.f, 1.f / 9.f,
-                       1.f / 36.f, 1.f / 36.f, 1.f / 36.f, 1.f / 36.f};
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
     int x, y, kk = k;
     if (kk < nbot) {
@@ -492,16 +527,8 @@ __global__ void __launch_bounds__(256) flow_wall_kernel(Dev d) {
     const float jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
     float ux, uy, Fx, Fy;
     velocity(jx, jy, T, flf, phi, K, d, ux, uy, Fx, Fy);
-    const float ivp = 1.f / (phi * flf);
-    const float uu = ux * ux + uy * uy;
-    float fin[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const float eu = ex9(i) * ux + ey9(i) * uy;
-      fin[i] = f[i] - w9[i] * d.rho0 * (3.f * eu + 4.5f * eu * eu * ivp - 1.5f * uu * ivp);
-    }
-    float fp[9], ub, vb;
-    flow_collide(d, fin, T, flf, phi, K, fp, ub, vb);
+    float fp[9];
+    extrapolated_post(d, f, T, flf, phi, K, ux, uy, fp);
     const int sb = y * nx + x;
     unsigned rnd = 0u;
     if constexpr (!std::is_same<S, float>::value)
@@ -549,7 +576,7 @@ static void launch_flow_walls_t(const Dev& d, int parity, int mode, cudaStream_t
 
 // ---- ordinary-load kernel ----------------------------------------------------
 
-template <typename S, int PAR, bool FLOW, int MODE>
+template <typename S, int PAR, int FLOW, int MODE>
 __global__ void __launch_bounds__(TX* TY, 4) fused_step_kernel(Dev d) {
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x;
@@ -704,7 +731,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity,
 // issue the copies of the tile at (x0, y0) into buffer `buf`, completing on `bar`;
 // flows: some node of the tile carries flow (else its nodes read neither their
 // flow populations nor phi and K, and those are not copied)
-template <typename S, int PAR, bool FLOW>
+template <typename S, int PAR, int FLOW>
 __device__ __forceinline__ void tma_issue(const TmaMaps& m, unsigned buf, unsigned bar, int x0,
                                           int y0, bool flows) {
   using L = TmaLayout<PAR, S>;
@@ -725,7 +752,7 @@ __device__ __forceinline__ void tma_issue(const TmaMaps& m, unsigned buf, unsign
 
 // The update of node (x0 + lane, y0 + ty) of a tile staged in buffer sb.
 // EDGE = false: the tile has no wall node and no neighbour of a wall node.
-template <typename S, int PAR, bool FLOW, bool EDGE>
+template <typename S, int PAR, int FLOW, bool EDGE>
 __device__ __forceinline__ bool tma_node(const Dev& d, const unsigned char* sb, int x0, int y0,
                                          int lane, int ty) {
   using L = TmaLayout<PAR, S>;
@@ -789,7 +816,7 @@ __device__ __forceinline__ bool tma_node(const Dev& d, const unsigned char* sb, 
 
 // One CTA's share of the pass over one lattice: CTA bid of nblk (blockIdx.x
 // and gridDim.x of a single lattice's launch; its range in a batched launch).
-template <typename S, int PAR, bool FLOW, int MODE>
+template <typename S, int PAR, int FLOW, int MODE>
 __device__ __forceinline__ void fused_tma_body(const Dev& d, const TmaMaps& m, int bid,
                                                int nblk) {
   using L = TmaLayout<PAR, S>;
@@ -907,7 +934,7 @@ __device__ __forceinline__ void fused_tma_body(const Dev& d, const TmaMaps& m, i
   if (tid == 0 && d.trace) trace_end(d, 100 * PAR + 10 + MODE, d.ctr[1 - PAR] + 1, tr0);
 }
 
-template <typename S, int PAR, bool FLOW, int MODE>
+template <typename S, int PAR, int FLOW, int MODE>
 __global__ void __launch_bounds__(TX* TY, TMA_MIN_CTAS)
     fused_tma_kernel(Dev d, const __grid_constant__ TmaMaps m) {
   fused_tma_body<S, PAR, FLOW, MODE>(d, m, (int)blockIdx.x, (int)gridDim.x);
@@ -916,7 +943,7 @@ __global__ void __launch_bounds__(TX* TY, TMA_MIN_CTAS)
 // The same pass over every lattice of a batch in one launch: each lattice's
 // CTAs are a range of the grid, its parameters one entry of the plan, its
 // tensor maps one entry of a device array.
-template <typename S, int PAR, bool FLOW, int MODE>
+template <typename S, int PAR, int FLOW, int MODE>
 __global__ void __launch_bounds__(TX* TY, TMA_MIN_CTAS)
     fused_tma_batch_kernel(const __grid_constant__ BatchPlan P, const TmaMaps* __restrict__ maps) {
   const int c = plan_lattice(P, (int)blockIdx.x);
@@ -926,18 +953,22 @@ __global__ void __launch_bounds__(TX* TY, TMA_MIN_CTAS)
 
 // ---- launches ------------------------------------------------------------------
 
+// FLOW: 0 no flow lattice, 1 flow, 2 flow with the front extrapolation
 template <typename S, int MODE>
 static void launch_mode(const Dev& d, int parity, dim3 grid, dim3 block, cudaStream_t s) {
-  if (d.flow) {
-    if (parity == 0) fused_step_kernel<S, 0, true, MODE><<<grid, block, 0, s>>>(d);
-    else fused_step_kernel<S, 1, true, MODE><<<grid, block, 0, s>>>(d);
+  if (d.flow && d.flow_front) {
+    if (parity == 0) fused_step_kernel<S, 0, 2, MODE><<<grid, block, 0, s>>>(d);
+    else fused_step_kernel<S, 1, 2, MODE><<<grid, block, 0, s>>>(d);
+  } else if (d.flow) {
+    if (parity == 0) fused_step_kernel<S, 0, 1, MODE><<<grid, block, 0, s>>>(d);
+    else fused_step_kernel<S, 1, 1, MODE><<<grid, block, 0, s>>>(d);
   } else {
-    if (parity == 0) fused_step_kernel<S, 0, false, MODE><<<grid, block, 0, s>>>(d);
-    else fused_step_kernel<S, 1, false, MODE><<<grid, block, 0, s>>>(d);
+    if (parity == 0) fused_step_kernel<S, 0, 0, MODE><<<grid, block, 0, s>>>(d);
+    else fused_step_kernel<S, 1, 0, MODE><<<grid, block, 0, s>>>(d);
   }
 }
 
-template <typename S, int PAR, bool FLOW, int MODE>
+template <typename S, int PAR, int FLOW, int MODE>
 static void launch_tma_one(const Dev& d, const TmaMaps& m, cudaStream_t s) {
   const size_t sm = TmaLayout<PAR, S>::SMEM;
   fused_tma_kernel<S, PAR, FLOW, MODE><<<d.tgrid, dim3(TX, TY), sm, s>>>(d, m);
@@ -945,12 +976,15 @@ static void launch_tma_one(const Dev& d, const TmaMaps& m, cudaStream_t s) {
 
 template <typename S, int MODE>
 static void launch_tma_mode(const Dev& d, const TmaMaps& m, int parity, cudaStream_t s) {
-  if (d.flow) {
-    if (parity == 0) launch_tma_one<S, 0, true, MODE>(d, m, s);
-    else launch_tma_one<S, 1, true, MODE>(d, m, s);
+  if (d.flow && d.flow_front) {
+    if (parity == 0) launch_tma_one<S, 0, 2, MODE>(d, m, s);
+    else launch_tma_one<S, 1, 2, MODE>(d, m, s);
+  } else if (d.flow) {
+    if (parity == 0) launch_tma_one<S, 0, 1, MODE>(d, m, s);
+    else launch_tma_one<S, 1, 1, MODE>(d, m, s);
   } else {
-    if (parity == 0) launch_tma_one<S, 0, false, MODE>(d, m, s);
-    else launch_tma_one<S, 1, false, MODE>(d, m, s);
+    if (parity == 0) launch_tma_one<S, 0, 0, MODE>(d, m, s);
+    else launch_tma_one<S, 1, 0, MODE>(d, m, s);
   }
 }
 
@@ -998,15 +1032,17 @@ static bool tma_setup_t(Dev& d, TmaMaps* m, CUtensorMapDataType dt) {
 #define LBM_SMEM(P, FL, MO, SM)                                                      \
   cudaFuncSetAttribute(fused_tma_kernel<S, P, FL, MO>,                               \
                        cudaFuncAttributeMaxDynamicSharedMemorySize, SM)
-  LBM_SMEM(0, true, 0, s0); LBM_SMEM(0, true, 1, s0); LBM_SMEM(0, true, 2, s0);
-  LBM_SMEM(0, false, 0, s0); LBM_SMEM(0, false, 1, s0); LBM_SMEM(0, false, 2, s0);
-  LBM_SMEM(1, true, 0, s1); LBM_SMEM(1, true, 1, s1); LBM_SMEM(1, true, 2, s1);
-  LBM_SMEM(1, false, 0, s1); LBM_SMEM(1, false, 1, s1); LBM_SMEM(1, false, 2, s1);
+  LBM_SMEM(0, 2, 0, s0); LBM_SMEM(0, 2, 1, s0); LBM_SMEM(0, 2, 2, s0);
+  LBM_SMEM(0, 1, 0, s0); LBM_SMEM(0, 1, 1, s0); LBM_SMEM(0, 1, 2, s0);
+  LBM_SMEM(0, 0, 0, s0); LBM_SMEM(0, 0, 1, s0); LBM_SMEM(0, 0, 2, s0);
+  LBM_SMEM(1, 2, 0, s1); LBM_SMEM(1, 2, 1, s1); LBM_SMEM(1, 2, 2, s1);
+  LBM_SMEM(1, 1, 0, s1); LBM_SMEM(1, 1, 1, s1); LBM_SMEM(1, 1, 2, s1);
+  LBM_SMEM(1, 0, 0, s1); LBM_SMEM(1, 0, 1, s1); LBM_SMEM(1, 0, 2, s1);
 #undef LBM_SMEM
   int per0 = 0, per1 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per0, fused_tma_kernel<S, 0, true, 0>, TX * TY,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per0, fused_tma_kernel<S, 0, 1, 0>, TX * TY,
                                                 s0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, fused_tma_kernel<S, 1, true, 0>, TX * TY,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, fused_tma_kernel<S, 1, 1, 0>, TX * TY,
                                                 s1);
   if (cudaGetLastError() != cudaSuccess || per0 <= 0 || per1 <= 0) return false;
   int dev = 0, sms = 0;

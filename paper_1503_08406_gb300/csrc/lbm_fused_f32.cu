@@ -18,20 +18,20 @@ void fused_batch_setup() {
 #define LBM_SMEM(P, FL, MO, SM)                                                      \
   cudaFuncSetAttribute(fused_tma_batch_kernel<float, P, FL, MO>,                     \
                        cudaFuncAttributeMaxDynamicSharedMemorySize, SM)
-  LBM_SMEM(0, true, 0, s0); LBM_SMEM(0, true, 1, s0); LBM_SMEM(0, true, 2, s0);
-  LBM_SMEM(0, false, 0, s0); LBM_SMEM(0, false, 1, s0); LBM_SMEM(0, false, 2, s0);
-  LBM_SMEM(1, true, 0, s1); LBM_SMEM(1, true, 1, s1); LBM_SMEM(1, true, 2, s1);
-  LBM_SMEM(1, false, 0, s1); LBM_SMEM(1, false, 1, s1); LBM_SMEM(1, false, 2, s1);
+  LBM_SMEM(0, 1, 0, s0); LBM_SMEM(0, 1, 1, s0); LBM_SMEM(0, 1, 2, s0);
+  LBM_SMEM(0, 0, 0, s0); LBM_SMEM(0, 0, 1, s0); LBM_SMEM(0, 0, 2, s0);
+  LBM_SMEM(1, 1, 0, s1); LBM_SMEM(1, 1, 1, s1); LBM_SMEM(1, 1, 2, s1);
+  LBM_SMEM(1, 0, 0, s1); LBM_SMEM(1, 0, 1, s1); LBM_SMEM(1, 0, 2, s1);
 #undef LBM_SMEM
 }
 
-template <int PAR, bool FL, int MO>
+template <int PAR, int FL, int MO>
 static void fused_batch_one(const BatchPlan& P, const TmaMaps* maps, cudaStream_t s) {
   fused_tma_batch_kernel<float, PAR, FL, MO>
       <<<P.start[P.count], dim3(TX, TY), TmaLayout<PAR, float>::SMEM, s>>>(P, maps);
 }
 
-template <int PAR, bool FL>
+template <int PAR, int FL>
 static void fused_batch_mode(const BatchPlan& P, const TmaMaps* maps, int mode, cudaStream_t s) {
   if (mode == 0) fused_batch_one<PAR, FL, 0>(P, maps, s);
   else if (mode == 1) fused_batch_one<PAR, FL, 1>(P, maps, s);
@@ -41,11 +41,11 @@ static void fused_batch_mode(const BatchPlan& P, const TmaMaps* maps, int mode, 
 void launch_fused_batch(const BatchPlan& P, const TmaMaps* maps, int parity, int mode, bool flow,
                         cudaStream_t s) {
   if (parity == 0) {
-    if (flow) fused_batch_mode<0, true>(P, maps, mode, s);
-    else fused_batch_mode<0, false>(P, maps, mode, s);
+    if (flow) fused_batch_mode<0, 1>(P, maps, mode, s);
+    else fused_batch_mode<0, 0>(P, maps, mode, s);
   } else {
-    if (flow) fused_batch_mode<1, true>(P, maps, mode, s);
-    else fused_batch_mode<1, false>(P, maps, mode, s);
+    if (flow) fused_batch_mode<1, 1>(P, maps, mode, s);
+    else fused_batch_mode<1, 0>(P, maps, mode, s);
   }
 }
 

@@ -100,6 +100,8 @@ struct Dev {
   int* proc;                 // per enthalpy tile: (stamp << 3) | bits, bit 0 solved, bit 1
                              // some f_l changed, bit 2 some node's flow activity changed
   float2* scr;               // per node of solved tiles: (f_l(n), f_l(n+1))
+  int flow_front;            // 1: links from a flow node into a non-flow lattice node take
+                             // the extrapolated boundary population (Sec. 4, moving front)
   int tskip;                 // 1: the TMA-staged pass copies flow populations, phi and K
                              // only for tiles with tact set (batch members: mostly solid
                              // lattices); 0: for every tile

@@ -59,6 +59,7 @@ class lbm_params(ctypes.Structure):
         ("check_every", ctypes.c_int32),
         ("sigma_solid", ctypes.c_double),
         ("flow_walls", ctypes.c_int32),
+        ("flow_front", ctypes.c_int32),
     ]
 
 
@@ -68,7 +69,7 @@ PARAM_DEFAULTS = dict(
     T_ref=0.0, T_s=0.0, T_l=0.0, varpi=-2.0, rho0=1.0, tau_nu=-1.0, tau_T=-1.0, g_beta=-1.0,
     s_e=0.0, s_eps=0.0, s_q=0.0, zeta_e=0.0, zeta_nu=0.0, f_act=1e-3,
     max_inner_iters=1000, inner_tol=1e-6, screen_tol=0.0, kernel_variant=0, storage=0, alpha_ratio=0.0,
-    check_every=0, sigma_solid=0.0, flow_walls=0,
+    check_every=0, sigma_solid=0.0, flow_walls=0, flow_front=0,
 )
 
 

@@ -322,6 +322,60 @@ def test_extrapolated_flow_walls_brinkman_channel(lbm, oracle_mod):
     assert np.abs(uy[1:-1] - u_node[1:-1]).max() < 1e-3 * u_node.max()
 
 
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("steps,walls", [(1, 0), (2, 0), (51, 0), (51, 1)])
+def test_front_extrapolation_matches_oracle(lbm, oracle_mod, steps, walls, variant):
+    """flow_front = 1 (no-slip on the moving solid-liquid interface by the
+    extrapolation of Sec. 4) in the melted cavity, both stream-collide kernels,
+    with halfway bounce-back or extrapolated flow walls."""
+    w = _f32(W.melted_cavity(64))
+    w.params = {**w.params, "flow_front": 1, "flow_walls": walls}
+    lat = _gpu(lbm, w, steps, kernel_variant=variant)
+    assert lat.kernel_variant() == variant
+    err = _walls_errors(lat, _ora(oracle_mod, w, steps))
+    assert max(err.values()) < 2e-5, err
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_front_extrapolation_with_moving_front(lbm, oracle_mod, variant):
+    """flow_front = 1 while the front moves (ragged 40^2, 400 steps): links
+    turn from extrapolated to streaming as nodes melt."""
+    w = _f32(W.melted_cavity(40))
+    w.params = {**w.params, "flow_front": 1}
+    steps = 400
+    lat = _gpu(lbm, w, steps, kernel_variant=variant)
+    o = _ora(oracle_mod, w, steps)
+    err = _walls_errors(lat, o)
+    assert max(err.values()) < 5e-5, err
+    fl = o.macros()["fl"]
+    assert ((fl >= 1e-3) != (w.fl0 >= 1e-3)).sum() > 0   # the flow mask moved
+
+
+def test_front_extrapolation_channel_between_solid_columns(lbm, oracle_mod):
+    """The solid-column channel (periodic both ways, no wall nodes, uniform
+    buoyancy): after 6,000 steps the GPU profile is the oracle's to 1e-5 and
+    the Brinkman-Forchheimer profile with the no-slip on the solid nodes to
+    1e-3."""
+    nx, ny, phi, K, G = 66, 4, 0.5, 12.5, 1e-8
+    params = dict(bc=("periodic",) * 4, T_bc=(0.0, 0.0, 0.0, 0.0), flow=1, tau_nu=1.0,
+                  tau_T=1.0, g_beta=G, Pr=1.0, T_ref=-1.0, T_s=0.0, T_l=0.0, flow_front=1)
+    fl0 = np.ones((ny, nx))
+    fl0[:, 0] = fl0[:, -1] = 0.0
+    w = _f32(W.Workload("solid_channel", nx, ny, params, np.full((ny, nx), phi),
+                        np.full((ny, nx), K), np.zeros((ny, nx)), fl0))
+    steps = 6000
+    lat = _gpu(lbm, w, steps)
+    o = _ora(oracle_mod, w, steps)
+    uy, uy_o = lat.macros()["uy"][1].astype(np.float64), o.macros()["uy"][1]
+    assert np.abs(uy - uy_o).max() < 1e-5 * np.abs(uy_o).max()
+    d = o.derived()
+    r = np.sqrt(phi * d["nu_l"] / (d["nu_e"] * K))
+    x = np.arange(nx)
+    c = (nx - 1) / 2.0
+    u_node = G * K / d["nu_l"] * (1 - np.cosh(r * (x - c)) / np.cosh(r * c))
+    assert np.abs(uy[1:-1] - u_node[1:-1]).max() < 1e-3 * u_node.max()
+
+
 def test_full_size_cavity_matches_oracle(lbm, oracle_mod):
     """2048^2 (the benchmark size), left third melted so flow runs on a
     third of the lattice: full-field comparison after 3 steps."""

@@ -90,6 +90,42 @@ def test_brinkman_channel_with_extrapolated_walls(oracle_mod):
     assert np.abs(o.macros()["ux"]).max() < 1e-15
 
 
+def test_brinkman_channel_between_solid_columns_with_front_extrapolation(oracle_mod):
+    """flow_front = 1 (Sec. 4's non-equilibrium extrapolation for the no-slip
+    condition on the solid-liquid interface): a channel, periodic both ways, no
+    wall nodes, bounded by two solid columns (f_l = 0, held at T_m with the
+    isothermal melting point, so that neither phase changes) and driven by a
+    uniform buoyancy (T - T_ref = 1).  The no-slip sits on the solid nodes: the
+    developed profile is the flow-wall one, within 1e-3 of
+    (G K / nu_l) [1 - cosh(r (x - c)) / cosh(r c)], c = (nx - 1)/2, and next to
+    the solid 90% above the halfway bounce-back profile."""
+    nx, ny, phi, K, G = 66, 4, 0.5, 12.5, 1e-8
+    params = dict(bc=("periodic",) * 4, T_bc=(0.0, 0.0, 0.0, 0.0), flow=1, tau_nu=1.0,
+                  tau_T=1.0, g_beta=G, Pr=1.0, T_ref=-1.0, T_s=0.0, T_l=0.0, flow_front=1)
+    fl0 = np.ones((ny, nx))
+    fl0[:, 0] = fl0[:, -1] = 0.0
+    w = W.Workload("solid_channel", nx, ny, params, np.full((ny, nx), phi), np.full((ny, nx), K),
+                   np.zeros((ny, nx)), fl0)
+    o = _run(oracle_mod, w, 6000)
+    m = o.macros()
+    uy = m["uy"][1]
+    assert np.array_equal(m["fl"], fl0)   # no phase change
+    d = o.derived()
+    r = np.sqrt(phi * d["nu_l"] / (d["nu_e"] * K))
+    x = np.arange(nx)
+    c = (nx - 1) / 2.0
+    u_node = G * K / d["nu_l"] * (1 - np.cosh(r * (x - c)) / np.cosh(r * c))
+    u_half = G * K / d["nu_l"] * (1 - np.cosh(r * (x - c)) / np.cosh(r * (nx - 2) / 2))
+    assert np.abs(uy[1:-1] - u_node[1:-1]).max() < 1e-3 * u_node.max()
+    assert uy[1] > 1.9 * u_half[1]
+    assert np.abs(m["ux"]).max() < 1e-15
+    # halfway bounce-back on the same columns puts the wall half a node further in
+    o2 = _run(oracle_mod, W.Workload("solid_channel_bb", nx, ny, {**params, "flow_front": 0},
+                                     w.phi, w.K, w.T0, fl0), 6000)
+    uy2 = o2.macros()["uy"][1]
+    assert np.abs(uy2[1:-1] - u_half[1:-1]).max() < 2e-3 * u_half.max()
+
+
 # ---- conservation on closed domains -----------------------------------------
 
 @pytest.mark.parametrize("flow,T_s,T_l", [(1, 0.0, 0.0), (0, -0.05, 0.05)])
