@@ -389,7 +389,7 @@ void adj_objective(const Dev& d, const float* fl, double* out, cudaStream_t s) {
 
 // One reversed coupled step (flow on): lbm::coupled_reverse_node per node,
 // rows along blockIdx.y.
-__global__ void __launch_bounds__(128, 6) adj_coupled_kernel(CoupledStep<float> A) {
+__global__ void __launch_bounds__(128, 8) adj_coupled_kernel(CoupledStep<float> A) {
   const int x = blockIdx.x * 128 + threadIdx.x;
   if (x >= A.geo.nx) return;
   for (int y = blockIdx.y; y < A.geo.ny; y += gridDim.y) coupled_reverse_node(A, x, y);
