@@ -261,7 +261,7 @@ template <typename S, int PAR, int FLOW, bool EDGE = true>
 __device__ __forceinline__ bool node_update(const Dev& d, int x, int y, const Geo& q,
                                             const float fln[9], const float gin[5], float f[9],
                                             const float fb[9], float phi, float K,
-                                            unsigned wact = 0u) {
+                                            unsigned wact = 0u, unsigned seed = 0u) {
   const int nx = d.nx, ny = d.ny;
   const int n = (int)d.n;
   const int s = q.s;
@@ -272,7 +272,7 @@ __device__ __forceinline__ bool node_update(const Dev& d, int x, int y, const Ge
   // rounding bits of this node and step (16-bit storage only)
   unsigned rnd = 0u;
   if constexpr (!std::is_same<S, float>::value)
-    rnd = mix32((unsigned)s ^ mix32((unsigned)d.ctr[1 - PAR]));
+    rnd = mix32((unsigned)s ^ seed);
   const float flc = fln[0];
   const float g0 = gin[0], g1 = gin[1], g2 = gin[2], g3 = gin[3], g4 = gin[4];
   const float T = g0 + g1 + g2 + g3 + g4;
@@ -635,7 +635,8 @@ __global__ void __launch_bounds__(TX* TY, 4) fused_step_kernel(Dev d) {
       wact = wall_activity(d, x, y, q, [&](int dx, int dy) {
         return d.fl[(long long)wrapy(d, y + dy) * nx + wrapx(d, x + dx)];
       });
-    unsafe = node_update<S, PAR, FLOW>(d, x, y, q, fln, g, f, fb, phi, K, wact);
+    const unsigned seed = std::is_same<S, float>::value ? 0u : mix32((unsigned)d.ctr[1 - PAR]);
+    unsafe = node_update<S, PAR, FLOW>(d, x, y, q, fln, g, f, fb, phi, K, wact, seed);
   }
   if (__any_sync(FULL, unsafe) && lane == 0)
     mark_tile(d, (y / TE) * d.etx + (blockIdx.x * TX) / TE, PAR);
@@ -754,7 +755,7 @@ __device__ __forceinline__ void tma_issue(const TmaMaps& m, unsigned buf, unsign
 // EDGE = false: the tile has no wall node and no neighbour of a wall node.
 template <typename S, int PAR, int FLOW, bool EDGE>
 __device__ __forceinline__ bool tma_node(const Dev& d, const unsigned char* sb, int x0, int y0,
-                                         int lane, int ty) {
+                                         int lane, int ty, unsigned seed) {
   using L = TmaLayout<PAR, S>;
   const int nx = d.nx, ny = d.ny;
   const int x = x0 + lane, y = y0 + ty;
@@ -809,7 +810,7 @@ __device__ __forceinline__ bool tma_node(const Dev& d, const unsigned char* sb, 
       unsigned wact = 0u;
       if (FLOW && EDGE && d.flow_walls)
         wact = wall_activity(d, x, y, q, [&](int dx, int dy) { return sFL[c + dy * WX + dx]; });
-      unsafe = node_update<S, PAR, FLOW, EDGE>(d, x, y, q, fln, g, f, fb, phi, K, wact);
+      unsafe = node_update<S, PAR, FLOW, EDGE>(d, x, y, q, fln, g, f, fb, phi, K, wact, seed);
   }
   return unsafe;
 }
@@ -835,6 +836,9 @@ __device__ __forceinline__ void fused_tma_body(const Dev& d, const TmaMaps& m, i
   const int t0 = bid, dt = nblk;
   const int cnt = (ntile - t0 + dt - 1) / dt;
   const long long tr0 = trace_start(d);
+  // 16-bit storage: the step's part of every node's rounding seed (this
+  // launch does not change ctr[1 - PAR])
+  const unsigned seed = std::is_same<S, float>::value ? 0u : mix32((unsigned)d.ctr[1 - PAR]);
   if (MODE != 1 && bid == 0 && tid == 0) step_prologue<PAR>(d);
   constexpr int NB = L::NBUF;
   const unsigned buf0 = smem_u32(smem);
@@ -903,8 +907,8 @@ __device__ __forceinline__ void fused_tma_body(const Dev& d, const TmaMaps& m, i
     // interior tiles (no wall node and no wall neighbour in them) take a copy
     // of the update with the wall logic compiled out
     const bool edge = x0 < 2 || x0 + TX > nx - 2 || y0 < 2 || y0 + TY > ny - 2;
-    const bool unsafe = edge ? tma_node<S, PAR, FLOW, true>(d, sb, x0, y0, lane, ty)
-                             : tma_node<S, PAR, FLOW, false>(d, sb, x0, y0, lane, ty);
+    const bool unsafe = edge ? tma_node<S, PAR, FLOW, true>(d, sb, x0, y0, lane, ty, seed)
+                             : tma_node<S, PAR, FLOW, false>(d, sb, x0, y0, lane, ty, seed);
     if (__any_sync(FULL, unsafe) && lane == 0)
       mark_tile(d, ((unsigned)y / TE) * d.etx + (unsigned)x0 / TE, PAR);
     // every thread is done with buffer b before it is refilled with the tile
