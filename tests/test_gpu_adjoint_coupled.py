@@ -6,7 +6,7 @@ Nusselt number averaged over the steps, with respect to porosity, ln K and
 the left wall profile; oracle/coupled_ref.py differentiates the same map by
 autograd and is pinned to finite differences of the C oracle.  The GPU runs
 in FP32: its gradients are held to 1e-3 of the largest entry of the FP64
-reference's (normwise, the benchmark spec bar), and, at sampled cells, to central
+reference's (normwise), and, at sampled cells, to central
 differences of the oracle's objective with h = 1e-4.
 
 Memory schedules: keeping every state, and keeping one every K steps with
