@@ -276,8 +276,10 @@ int lbm_adjoint(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_ev
  * exceed the free memory.  Covers: FP32 storage, one heat-capacity ratio,
  * the flow lattice on or off, one thermal diffusivity or alpha_l != alpha_s
  * (alpha_ratio, Sec. 4.1), a Dirichlet left wall (walls left and right,
- * nx >= 5); LBM_ERR_INVALID_ARG otherwise.  The context ends where the forward run left it.  Allocates its
- * buffers with cudaMalloc and synchronises.  device_ptrs: the three gradient
+ * nx >= 5), halfway bounce-back on walls and front (flow_walls = flow_front =
+ * 0), no timing; LBM_ERR_INVALID_ARG otherwise.  The context ends where the
+ * forward run left it.  Allocates its buffers with cudaMalloc and
+ * synchronises.  device_ptrs: the three gradient
  * arrays are device (1) or host (0) pointers. */
 int lbm_adjoint_coupled(lbm_ctx* c, int objective, int64_t nsteps, int32_t checkpoint_every,
                         int32_t mu_sweeps, float* d_phi, float* d_lnK, float* d_wall_T_left,
